@@ -1,0 +1,285 @@
+"""FP64 CPU oracle for keyframe surface correction (arXiv 1709.03763).
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check and by
+the benchmark's CPU-baseline leg, never by the product path.  It shares no code
+with the CUDA library and takes no value the CUDA path produced.
+
+`build()` compiles surfcorr_oracle.cpp into liboracle.so (g++ -O2, FP64, IEEE
+semantics, OpenMP over the blocks of one keyframe operation).  The thin ctypes
+wrappers below only marshal arrays; every computation is in the C++ file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "surfcorr_oracle.cpp")
+LIB = os.path.join(HERE, "liboracle.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", "-o", LIB + ".tmp", SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(LIB + ".tmp", LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_l = ctypes.c_long
+_p = ctypes.c_void_p
+
+
+def _declare(L):
+    L.or_fuse.argtypes = [_p, _p, _i, _p, _d, _d, _d, _d, _i, _i, _d, _p, _p, _p]
+    L.or_fuse.restype = _i
+    L.or_set_margins.argtypes = [_d, _d, _d]
+    L.or_set_threads.argtypes = [_i]
+    L.or_get_threads.restype = _i
+    L.or_vol_create.argtypes = [_d, _d, _i]
+    L.or_vol_create.restype = _p
+    L.or_vol_destroy.argtypes = [_p]
+    L.or_vol_clone.argtypes = [_p]
+    L.or_vol_clone.restype = _p
+    L.or_integrate.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p]
+    L.or_integrate.restype = _i
+    L.or_deintegrate.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p]
+    L.or_deintegrate.restype = _i
+    L.or_reintegrate_batch.argtypes = [_p, _i, _p, _p, _p, _p, _p, _d, _d, _d, _d, _i, _i]
+    L.or_reintegrate_batch.restype = _i
+    L.or_vol_num_blocks.argtypes = [_p]
+    L.or_vol_num_blocks.restype = _l
+    L.or_vol_export.argtypes = [_p, _p, _p, _p, _p, _p, _p]
+    L.or_vol_ghosts.argtypes = [_p, _p]
+    L.or_vol_ghosts.restype = _l
+    L.or_vol_touched.argtypes = [_p, _i, _p, _p]
+    L.or_vol_touched.restype = _l
+    L.or_allocation_set.argtypes = [_d, _d, _p, _d, _d, _d, _d, _i, _i, _p, _p, _p]
+    L.or_allocation_set.restype = _l
+    L.or_pose_distance.argtypes = [_p, _p]
+    L.or_pose_distance.restype = _d
+    L.or_select_topm.argtypes = [_p, _i, _i, _p]
+    L.or_select_consecutive.argtypes = [_p, _i, _i, _p]
+    L.or_select_consecutive.restype = _i
+    L.or_loss.argtypes = [_p, _p, _l, _d, _p, _p]
+    L.or_loss.restype = _d
+    L.or_grad.argtypes = [_p, _i, _p, _p, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _p]
+    L.or_grad.restype = _i
+    L.or_loss_perturbed.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _l, _d]
+    L.or_loss_perturbed.restype = _d
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(np.asarray(a), dtype=np.float32)
+
+
+def _u8(a):
+    return None if a is None else np.ascontiguousarray(np.asarray(a), dtype=np.uint8)
+
+
+def _np(t):
+    """torch tensor or array -> numpy (host)."""
+    if hasattr(t, "detach"):
+        return t.detach().cpu().numpy()
+    return np.asarray(t)
+
+
+def set_margins(tau_px=1e-3, tau_m=1e-5, tau_rel=1e-6):
+    lib().or_set_margins(tau_px, tau_m, tau_rel)
+
+
+def set_threads(n: int):
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().or_get_threads()
+
+
+def fuse(depths, poses, kf_pose, intr, disc_rel=0.1):
+    """Eq. 1 keyframe depth fusion.  depths [n,H,W] f32, poses [n,3,4], kf_pose [3,4].
+    Returns (Z* [H,W] f64, W* [H,W] f64, flag [H,W] u8)."""
+    d = _f32(_np(depths))
+    n, H, W = d.shape
+    p = _f32(_np(poses)).reshape(n, 12)
+    k = _f32(_np(kf_pose)).reshape(12)
+    Zs = np.zeros((H, W), np.float64)
+    Ws = np.zeros((H, W), np.float64)
+    fl = np.zeros((H, W), np.uint8)
+    fx, fy, cx, cy = intr[:4]
+    lib().or_fuse(_ptr(d), _ptr(p), n, _ptr(k), fx, fy, cx, cy, W, H, disc_rel, _ptr(Zs), _ptr(Ws), _ptr(fl))
+    return Zs, Ws, fl
+
+
+def allocation_set(depth, pose, intr, voxel_size, trunc):
+    """A(k, T) -> (coords [n,3] int32, marginal [n] u8: 0 robust, 1 marginal member,
+    2 marginal non-member)."""
+    d = _f32(_np(depth))
+    H, W = d.shape
+    p = _f32(_np(pose)).reshape(12)
+    fx, fy, cx, cy = intr[:4]
+    n = lib().or_allocation_set(voxel_size, trunc, _ptr(d), fx, fy, cx, cy, W, H, _ptr(p), None, None)
+    c = np.zeros((n, 3), np.int32)
+    m = np.zeros(n, np.uint8)
+    lib().or_allocation_set(voxel_size, trunc, _ptr(d), fx, fy, cx, cy, W, H, _ptr(p), _ptr(c), _ptr(m))
+    return c, m
+
+
+@dataclass
+class Export:
+    coords: np.ndarray   # [n,3] int32 block coordinates, ascending key order
+    D: np.ndarray        # [n,512] f64
+    W: np.ndarray        # [n,512] f64
+    C: np.ndarray        # [n,512,3] f64
+    bflag: np.ndarray    # [n] u8
+    vflag: np.ndarray    # [n,512] u8
+    ghosts: np.ndarray   # [g,3] int32 blocks reached only marginally, not allocated here
+
+
+class Volume:
+    """Voxel-hashed TSDF in FP64.  rgba8=True stores colour as 8-bit integers."""
+
+    def __init__(self, voxel_size, trunc, rgba8=False, _handle=None):
+        self.voxel_size = voxel_size
+        self.trunc = trunc
+        self.rgba8 = rgba8
+        self.h = _handle if _handle is not None else lib().or_vol_create(voxel_size, trunc, int(rgba8))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().or_vol_destroy(self.h)
+            self.h = None
+
+    def clone(self):
+        return Volume(self.voxel_size, self.trunc, self.rgba8, _handle=lib().or_vol_clone(self.h))
+
+    def integrate(self, kf_id, depth, rgba, intr, pose):
+        d = _f32(_np(depth))
+        H, W = d.shape
+        c = _u8(_np(rgba)) if rgba is not None else None
+        p = _f32(_np(pose)).reshape(12)
+        fx, fy, cx, cy = intr[:4]
+        rc = lib().or_integrate(self.h, kf_id, _ptr(d), _ptr(c), fx, fy, cx, cy, W, H, _ptr(p))
+        if rc:
+            raise ValueError(f"keyframe {kf_id} already integrated")
+
+    def deintegrate(self, kf_id, depth, rgba, intr, pose):
+        d = _f32(_np(depth))
+        H, W = d.shape
+        c = _u8(_np(rgba)) if rgba is not None else None
+        p = _f32(_np(pose)).reshape(12)
+        fx, fy, cx, cy = intr[:4]
+        rc = lib().or_deintegrate(self.h, kf_id, _ptr(d), _ptr(c), fx, fy, cx, cy, W, H, _ptr(p))
+        if rc:
+            raise ValueError(f"keyframe {kf_id} not integrated")
+
+    def reintegrate_batch(self, kf_ids, depths, rgbas, old_poses, new_poses, intr):
+        ids = np.ascontiguousarray(kf_ids, np.int32)
+        d = _f32(_np(depths))
+        n, H, W = d.shape
+        c = _u8(_np(rgbas)) if rgbas is not None else None
+        op = _f32(_np(old_poses)).reshape(n, 12)
+        np_ = _f32(_np(new_poses)).reshape(n, 12)
+        fx, fy, cx, cy = intr[:4]
+        rc = lib().or_reintegrate_batch(self.h, n, _ptr(ids), _ptr(d), _ptr(c), _ptr(op), _ptr(np_),
+                                        fx, fy, cx, cy, W, H)
+        if rc:
+            raise ValueError("batch item not integrated / already integrated")
+
+    def num_blocks(self):
+        return lib().or_vol_num_blocks(self.h)
+
+    def export(self) -> Export:
+        n = self.num_blocks()
+        coords = np.zeros((n, 3), np.int32)
+        D = np.zeros((n, 512))
+        W = np.zeros((n, 512))
+        C = np.zeros((n, 512, 3))
+        bf = np.zeros(n, np.uint8)
+        vf = np.zeros((n, 512), np.uint8)
+        lib().or_vol_export(self.h, _ptr(coords), _ptr(D), _ptr(W), _ptr(C), _ptr(bf), _ptr(vf))
+        g = lib().or_vol_ghosts(self.h, None)
+        gh = np.zeros((g, 3), np.int32)
+        lib().or_vol_ghosts(self.h, _ptr(gh))
+        return Export(coords, D, W, C, bf, vf, gh)
+
+    def touched(self, kf_id):
+        n = lib().or_vol_touched(self.h, kf_id, None, None)
+        if n < 0:
+            return None, None
+        c = np.zeros((n, 3), np.int32)
+        m = np.zeros(n, np.uint8)
+        lib().or_vol_touched(self.h, kf_id, _ptr(c), _ptr(m))
+        return c, m
+
+    def loss(self, points, lam=0.1):
+        pts = np.ascontiguousarray(points, np.float64)
+        nv = ctypes.c_long(0)
+        pf = np.zeros(len(pts), np.uint8)
+        L = lib().or_loss(self.h, _ptr(pts), len(pts), lam, ctypes.byref(nv), _ptr(pf))
+        return L, nv.value, pf
+
+    def grad(self, kf_ids, depths, poses, intr, points, lam=0.1, with_depth=True):
+        ids = np.ascontiguousarray(kf_ids, np.int32)
+        d = _f32(_np(depths))
+        K, H, W = d.shape
+        p = _f32(_np(poses)).reshape(K, 12)
+        pts = np.ascontiguousarray(points, np.float64)
+        gx = np.zeros((K, 6))
+        gd = np.zeros((K, H, W)) if with_depth else None
+        fx, fy, cx, cy = intr[:4]
+        rc = lib().or_grad(self.h, K, _ptr(ids), _ptr(d), None, _ptr(p), fx, fy, cx, cy, W, H,
+                           _ptr(pts), len(pts), lam, _ptr(gx), _ptr(gd))
+        if rc:
+            raise ValueError("keyframe not integrated")
+        return gx, gd
+
+    def loss_perturbed(self, kf_id, depth, pose, intr, xi, points, lam=0.1, pix=-1, dz=0.0):
+        d = _f32(_np(depth))
+        H, W = d.shape
+        p = _f32(_np(pose)).reshape(12)
+        x = np.ascontiguousarray(xi, np.float64).reshape(6)
+        pts = np.ascontiguousarray(points, np.float64)
+        fx, fy, cx, cy = intr[:4]
+        return lib().or_loss_perturbed(self.h, kf_id, _ptr(d), _ptr(p), fx, fy, cx, cy, W, H, _ptr(x),
+                                       int(pix), float(dz), _ptr(pts), len(pts), lam)
+
+
+def pose_distance(T0, T1) -> float:
+    a = _f32(T0).reshape(12)
+    b = _f32(T1).reshape(12)
+    return lib().or_pose_distance(_ptr(a), _ptr(b))
+
+
+def select_topm(dist, m):
+    d = np.ascontiguousarray(dist, np.float64)
+    out = np.zeros(m, np.int32)
+    lib().or_select_topm(_ptr(d), len(d), m, _ptr(out))
+    return out
+
+
+def select_consecutive(dist, m):
+    d = np.ascontiguousarray(dist, np.float64)
+    sums = np.zeros(max(len(d) - m + 1, 0))
+    j = lib().or_select_consecutive(_ptr(d), len(d), m, _ptr(sums))
+    return j, sums

@@ -1,0 +1,970 @@
+// FP64 CPU oracle for keyframe surface correction (Maier, Schaller, Cremers,
+// "Efficient Online Surface Correction for Real-time Large-Scale 3D
+// Reconstruction", arXiv 1709.03763).
+//
+// TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+// benchmark's CPU-baseline leg load this library.  It shares no code, header,
+// table or constant with the CUDA path, and it never reads a value the CUDA
+// path produced.  It is deliberately plain and slow: one voxel, one pixel, one
+// decision at a time, in double precision, in the order the paper states the
+// steps.  Inputs are the same float32 depth / uint8 colour / float32 poses the
+// GPU gets, promoted to double.
+//
+// Functions and what pins them (the pins live in tests/test_oracle_*.py):
+//   or_fuse                  Eq. 1 keyframe depth fusion (Section 3 "Keyframe Fusion").
+//                            Pinned: identical frames at one pose give Z* = Z and
+//                            W* = sum of cos(theta)/Z^2; a fronto-parallel plane has
+//                            cos(theta) = 1; x-translated views of a plane fuse to z0;
+//                            Eq. 1 applied in any frame order gives the same ratio.
+//   or_vol_*                 Voxel-hashed TSDF (Section 3 "SDF volume"): block
+//                            allocation, running-average integration, Eq. 2
+//                            de-integration, sequential re-integration batches
+//                            (Section 4.3).  Pinned: closed-form truncated distance
+//                            for a fronto-parallel plane and for a sphere, weights
+//                            equal a brute-force observation count, integrate then
+//                            de-integrate restores the volume, allocation equals a
+//                            dense point-sampling of each band segment.
+//   or_pose_distance,        Keyframe selection (Section 4.3, Eq. 3, Fig. 4).
+//   or_select_topm,          Pinned: the Fig. 4 worked example.
+//   or_select_consecutive
+//   or_loss, or_grad,        Loss on the fused SDF and its analytic gradient with
+//   or_loss_perturbed        respect to keyframe se(3) poses and depth pixels (this
+//                            extension has no counterpart in the paper).  Pinned: a
+//                            plane moved along the optical axis (closed form), zero
+//                            roll gradient for a fronto-parallel plane, and central
+//                            finite differences of or_loss_perturbed.
+//
+// Readings of points the paper leaves open (pixel convention, normal estimate,
+// discontinuity test, sampling weight, truncation band, the voxel set an
+// integration touches, W' = 0 in Eq. 2, se(3) parameterisation) are stated
+// where they are used below.
+//
+// Decision margins: float32 arithmetic on the GPU cannot reproduce every
+// threshold decision of this double-precision reference exactly.  Each
+// decision below therefore records its margin; an item whose margin is below
+// tau (tau_px pixels for rounding, tau_m metres for distances) is flagged and
+// the parity tests leave flagged items out of exact comparisons.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+double g_tau_px = 1e-3;   // pixel-rounding margin (pixels)
+double g_tau_m = 1e-5;    // distance margin (metres)
+double g_tau_rel = 1e-6;  // relative margin for the discontinuity test
+
+struct Intr {
+    double fx, fy, cx, cy;
+    int W, H;
+};
+
+// Pose T = (R, t) in SE(3), world_from_camera: g(T, p) = R p + t (Section 3
+// "Preliminaries").  Stored as a row-major 3x4 matrix [R | t].
+struct Pose {
+    double R[3][3];
+    double t[3];
+};
+
+Pose pose_from(const float* m) {
+    Pose P;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) P.R[r][c] = (double)m[r * 4 + c];
+        P.t[r] = (double)m[r * 4 + 3];
+    }
+    return P;
+}
+
+// g(T, p) = R p + t
+void apply(const Pose& T, const double p[3], double out[3]) {
+    for (int r = 0; r < 3; ++r) out[r] = T.R[r][0] * p[0] + T.R[r][1] * p[1] + T.R[r][2] * p[2] + T.t[r];
+}
+
+// g(T^-1, p) = R^T (p - t)
+void apply_inv(const Pose& T, const double p[3], double out[3]) {
+    double q[3] = {p[0] - T.t[0], p[1] - T.t[1], p[2] - T.t[2]};
+    for (int r = 0; r < 3; ++r) out[r] = T.R[0][r] * q[0] + T.R[1][r] * q[1] + T.R[2][r] * q[2];
+}
+
+// pi^-1(x, Z): pixel centres at integer coordinates, Z is z-depth.
+void backproject(const Intr& K, double u, double v, double Z, double out[3]) {
+    out[0] = (u - K.cx) / K.fx * Z;
+    out[1] = (v - K.cy) / K.fy * Z;
+    out[2] = Z;
+}
+
+// Nearest pixel of a continuous image coordinate, halves rounded up:
+// floor(a + 1/2).  Returns the margin: distance of a + 1/2 to the nearest
+// integer (how far the coordinate is from a rounding tie).
+long round_half_up(double a, double* margin) {
+    double b = a + 0.5;
+    double f = std::floor(b);
+    double fr = b - f;
+    *margin = std::min(fr, 1.0 - fr);
+    return (long)f;
+}
+
+}  // namespace
+
+// ============================================================================
+// Keyframe depth fusion, Eq. 1 (Section 3 "Keyframe Fusion")
+// ============================================================================
+//
+// For each frame i of the keyframe's group (in the given order) and each pixel
+// x of Z_i (row-major):
+//   * skip invalid depth (Z <= 0) and pixels close to depth discontinuities.
+//     Reading: a pixel is kept only if all four 4-neighbours are valid and
+//     |Z(n) - Z(x)| <= disc_rel * Z(x) for each; border pixels have no full
+//     neighbourhood and are skipped.
+//   * w_z(x) = cos(theta) * Z(x)^-2, theta the angle between the depth normal
+//     and the camera axis.  Reading: normal = (P(u+1,v) - P(u-1,v)) x
+//     (P(u,v+1) - P(u,v-1)) with P = pi^-1 in camera coordinates, and
+//     cos(theta) = |n_z| / |n|.
+//   * p* = g(T*^-1, g(T_i, pi^-1(x, Z_i(x)))); x* = pi(p*) rounded to the
+//     nearest pixel (same rounding as the volume update); skip if Z*_p <= 0 or
+//     x* falls outside the image.
+//   * Eq. 1: Z*(x*) <- (W*(x*) Z*(x*) + w_z Z*_p) / (W*(x*) + w_z);
+//            W*(x*) <- W*(x*) + w_z.
+//     Reading: no z-test; every warped sample is averaged into its pixel.
+// Z* and W* start at zero.  flag[x*] marks target pixels that a source pixel
+// with a marginal decision may land in (3x3 neighbourhood of its x*).
+extern "C" int or_fuse(const float* depths, const float* poses, int n, const float* kf_pose,
+                       double fx, double fy, double cx, double cy, int W, int H, double disc_rel,
+                       double* Zs, double* Ws, uint8_t* flag) {
+    const Intr K{fx, fy, cx, cy, W, H};
+    const Pose Tk = pose_from(kf_pose);
+    for (long p = 0; p < (long)W * H; ++p) {
+        Zs[p] = 0.0;
+        Ws[p] = 0.0;
+        flag[p] = 0;
+    }
+    for (int f = 0; f < n; ++f) {
+        const float* Z = depths + (long)f * W * H;
+        const Pose Tf = pose_from(poses + 12 * f);
+        for (int v = 0; v < H; ++v) {
+            for (int u = 0; u < W; ++u) {
+                double z = Z[(long)v * W + u];
+                if (!(z > 0.0)) continue;
+                if (u == 0 || v == 0 || u == W - 1 || v == H - 1) continue;
+                double zn[4] = {Z[(long)v * W + u - 1], Z[(long)v * W + u + 1],
+                                Z[(long)(v - 1) * W + u], Z[(long)(v + 1) * W + u]};
+                if (!(zn[0] > 0.0 && zn[1] > 0.0 && zn[2] > 0.0 && zn[3] > 0.0)) continue;
+                // discontinuity test (exact decision + its margin)
+                bool keep = true, marginal = false;
+                for (int k = 0; k < 4; ++k) {
+                    double gap = std::fabs(zn[k] - z) - disc_rel * z;
+                    if (std::fabs(gap) < g_tau_rel * z) marginal = true;
+                    if (gap > 0.0) keep = false;
+                }
+                if (!keep && !marginal) continue;
+                // warp into the keyframe: p* = g(T*^-1, g(T_i, pi^-1(x, Z_i(x))))
+                double P[3], pw[3], ps[3];
+                backproject(K, u, v, z, P);
+                apply(Tf, P, pw);
+                apply_inv(Tk, pw, ps);
+                if (std::fabs(ps[2]) < g_tau_m) marginal = true;
+                if (!(ps[2] > 0.0)) continue;
+                double mu_, mv_;
+                long xs = round_half_up(K.fx * ps[0] / ps[2] + K.cx, &mu_);
+                long ys = round_half_up(K.fy * ps[1] / ps[2] + K.cy, &mv_);
+                if (mu_ < g_tau_px || mv_ < g_tau_px) marginal = true;
+                if (marginal) {
+                    for (long dy = -1; dy <= 1; ++dy)
+                        for (long dx = -1; dx <= 1; ++dx) {
+                            long yy = ys + dy, xx = xs + dx;
+                            if (yy >= 0 && yy < H && xx >= 0 && xx < W) flag[yy * W + xx] = 1;
+                        }
+                }
+                if (!keep) continue;
+                if (xs < 0 || xs >= W || ys < 0 || ys >= H) continue;
+                // w_z = cos(theta) / Z^2 from the central-difference depth normal
+                double Pl[3], Pr[3], Pu[3], Pd[3];
+                backproject(K, u - 1, v, zn[0], Pl);
+                backproject(K, u + 1, v, zn[1], Pr);
+                backproject(K, u, v - 1, zn[2], Pu);
+                backproject(K, u, v + 1, zn[3], Pd);
+                double a[3] = {Pr[0] - Pl[0], Pr[1] - Pl[1], Pr[2] - Pl[2]};
+                double b[3] = {Pd[0] - Pu[0], Pd[1] - Pu[1], Pd[2] - Pu[2]};
+                double nrm[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+                double nn = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+                if (!(nn > 0.0)) continue;
+                double cos_theta = std::fabs(nrm[2]) / nn;
+                double wz = cos_theta / (z * z);
+                long q = ys * W + xs;
+                // Eq. 1
+                Zs[q] = (Ws[q] * Zs[q] + wz * ps[2]) / (Ws[q] + wz);
+                Ws[q] = Ws[q] + wz;
+            }
+        }
+    }
+    return 0;
+}
+
+// ============================================================================
+// Voxel-hashed TSDF volume (Section 3 "SDF volume"; Section 4.3)
+// ============================================================================
+//
+// Voxel i (integer 3-vector) sits at world position i * s.  Voxel blocks hold
+// 8^3 voxels; block b covers voxel indices 8b .. 8b+7 on each axis and the
+// closed world box [8 b s, 8 (b+1) s]^3.  Each voxel stores D (signed
+// distance, metres), C (colour, RGB in 0..255) and W (integration weight).
+// The block map is keyed by block coordinate; storage order is irrelevant.
+
+namespace {
+
+constexpr int BS = 8;
+constexpr int NV = BS * BS * BS;
+
+struct Block {
+    double D[NV];
+    double W[NV];
+    double C[NV][3];
+    uint8_t vflag[NV];
+    uint8_t bflag;
+    Block() {
+        std::memset(D, 0, sizeof(D));
+        std::memset(W, 0, sizeof(W));
+        std::memset(C, 0, sizeof(C));
+        std::memset(vflag, 0, sizeof(vflag));
+        bflag = 0;
+    }
+};
+
+int64_t pack(long x, long y, long z) {
+    const long O = 1L << 20;
+    return (int64_t)((x + O) | ((y + O) << 21) | ((z + O) << 42));
+}
+void unpack(int64_t k, long* x, long* y, long* z) {
+    const long O = 1L << 20, M = (1L << 21) - 1;
+    *x = (long)(k & M) - O;
+    *y = (long)((k >> 21) & M) - O;
+    *z = (long)((k >> 42) & M) - O;
+}
+
+long floor_div(long a, long b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
+
+struct Touched {
+    std::vector<int64_t> blocks;         // A(k, T): this keyframe's blocks, sorted
+    std::vector<uint8_t> marginal;       // allocation decision uncertain for that block
+};
+
+struct Vol {
+    double s, mu;
+    int rgba8;  // 1: colour is stored as 8-bit integers (rounded after each update)
+    std::unordered_map<int64_t, Block> blocks;
+    std::map<int, Touched> touched;
+    // blocks some integration reached only marginally (a float32 implementation
+    // may allocate or update them where this reference does not)
+    std::unordered_map<int64_t, uint8_t> ghosts;
+};
+
+// Closed segment [q0, q1] against the closed box [lo, hi]^3 (slab test).
+bool seg_box(const double q0[3], const double q1[3], const double lo[3], const double hi[3]) {
+    double tmin = 0.0, tmax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double d = q1[a] - q0[a];
+        if (d == 0.0) {
+            if (q0[a] < lo[a] || q0[a] > hi[a]) return false;
+            continue;
+        }
+        double t0 = (lo[a] - q0[a]) / d, t1 = (hi[a] - q0[a]) / d;
+        if (t0 > t1) std::swap(t0, t1);
+        tmin = std::max(tmin, t0);
+        tmax = std::min(tmax, t1);
+        if (tmin > tmax) return false;
+    }
+    return true;
+}
+
+// A(k, T): allocation / visibility (Section 3 "SDF volume": blocks are first
+// allocated, then voxels are updated).  Reading: for every valid pixel x the
+// centre ray's band segment, camera z in [Z(x) - mu, Z(x) + mu], is taken to
+// world coordinates; every block whose closed box meets that segment belongs to
+// A(k, T).  Candidates are all blocks in the segment's bounding box (brute force).
+// A block is "marginal" when the segment meets the box grown by tau_m but not the
+// box shrunk by tau_m, for every pixel that reaches it.
+void allocation_set(const Vol& V, const float* depth, const Intr& K, const Pose& T,
+                    std::vector<int64_t>& out, std::vector<uint8_t>& marg) {
+    const double B = BS * V.s;
+    // per block: bit 0 = some pixel meets the exact box, bit 1 = some pixel meets the
+    // shrunk box (robust member), bit 2 = some pixel meets the grown box
+    std::map<int64_t, int> state;
+    for (int v = 0; v < K.H; ++v) {
+        for (int u = 0; u < K.W; ++u) {
+            double z = depth[(long)v * K.W + u];
+            if (!(z > 0.0)) continue;
+            double c0[3], c1[3], q0[3], q1[3];
+            backproject(K, u, v, z - V.mu, c0);
+            backproject(K, u, v, z + V.mu, c1);
+            apply(T, c0, q0);
+            apply(T, c1, q1);
+            long blo[3], bhi[3];
+            for (int a = 0; a < 3; ++a) {
+                double lo = std::min(q0[a], q1[a]), hi = std::max(q0[a], q1[a]);
+                blo[a] = (long)std::ceil((lo - g_tau_m) / B) - 1;
+                bhi[a] = (long)std::floor((hi + g_tau_m) / B);
+            }
+            for (long bz = blo[2]; bz <= bhi[2]; ++bz)
+                for (long by = blo[1]; by <= bhi[1]; ++by)
+                    for (long bx = blo[0]; bx <= bhi[0]; ++bx) {
+                        double lo[3] = {bx * B, by * B, bz * B};
+                        double hi[3] = {(bx + 1) * B, (by + 1) * B, (bz + 1) * B};
+                        double lo_s[3], hi_s[3], lo_g[3], hi_g[3];
+                        for (int a = 0; a < 3; ++a) {
+                            lo_s[a] = lo[a] + g_tau_m;
+                            hi_s[a] = hi[a] - g_tau_m;
+                            lo_g[a] = lo[a] - g_tau_m;
+                            hi_g[a] = hi[a] + g_tau_m;
+                        }
+                        int bits = (seg_box(q0, q1, lo, hi) ? 1 : 0) | (seg_box(q0, q1, lo_s, hi_s) ? 2 : 0) |
+                                   (seg_box(q0, q1, lo_g, hi_g) ? 4 : 0);
+                        if (bits) state[pack(bx, by, bz)] |= bits;
+                    }
+        }
+    }
+    out.clear();
+    marg.clear();
+    for (auto& kv : state) {
+        out.push_back(kv.first);
+        if (kv.second & 2) marg.push_back(0);        // robust member
+        else if (kv.second & 1) marg.push_back(1);   // member by the exact test, marginal
+        else marg.push_back(2);                      // marginal non-member
+    }
+}
+
+// Per-voxel projective sample of keyframe (depth, colour) at pose T.
+// Returns true when the voxel is updated; fills d, c and the decision margins.
+struct Sample {
+    bool upd;
+    bool marginal;
+    bool clamped;
+    long pix;
+    double d;
+    double c[3];
+    double pv[3];
+    double zc;
+};
+
+Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const Intr& K, const Pose& T,
+                    long ix, long iy, long iz) {
+    Sample S{};
+    S.upd = false;
+    S.marginal = false;
+    S.pv[0] = ix * V.s;
+    S.pv[1] = iy * V.s;
+    S.pv[2] = iz * V.s;
+    double pc[3];
+    apply_inv(T, S.pv, pc);
+    S.zc = pc[2];
+    if (std::fabs(pc[2]) < g_tau_m) S.marginal = true;
+    if (!(pc[2] > 0.0)) return S;
+    double mu_, mv_;
+    long px = round_half_up(K.fx * pc[0] / pc[2] + K.cx, &mu_);
+    long py = round_half_up(K.fy * pc[1] / pc[2] + K.cy, &mv_);
+    if (mu_ < g_tau_px || mv_ < g_tau_px) S.marginal = true;
+    if (px < 0 || px >= K.W || py < 0 || py >= K.H) return S;
+    long q = py * K.W + px;
+    double Z = depth[q];
+    if (!(Z > 0.0)) return S;
+    // projective distance along the camera z axis (Section 4.3): eta = Z(x) - z_c
+    double eta = Z - pc[2];
+    if (std::fabs(eta + V.mu) < g_tau_m) S.marginal = true;
+    if (eta < -V.mu) return S;  // far behind the observed surface: not updated
+    S.upd = true;
+    S.pix = q;
+    S.clamped = !(eta < V.mu);
+    if (std::fabs(eta - V.mu) < g_tau_m) S.marginal = true;  // clamp kink (matters for gradients)
+    S.d = std::min(eta, V.mu);
+    if (rgba) {
+        for (int ch = 0; ch < 3; ++ch) S.c[ch] = (double)rgba[4 * q + ch];
+    } else {
+        S.c[0] = S.c[1] = S.c[2] = 0.0;
+    }
+    return S;
+}
+
+double to_u8(double x) {
+    // 8-bit storage: round half to even, saturate.
+    double r = std::nearbyint(x);
+    return std::min(255.0, std::max(0.0, r));
+}
+
+// Running weighted average (Section 3) with sign +1, or its inverse Eq. 2
+// (Section 4.3) with sign -1.  Sampling weight w = 1 per keyframe observation
+// (reading: the paper names w_i without giving its value).  When Eq. 2 brings W
+// to zero the division is undefined; reading: the voxel returns to its empty
+// state D = C = 0, W = 0 (the block stays allocated).
+void update_blocks(Vol& V, const std::vector<int64_t>& blocks, const std::vector<uint8_t>& marg,
+                   const float* depth, const uint8_t* rgba, const Intr& K, const Pose& T, int sign) {
+    std::vector<Block*> ptrs(blocks.size(), nullptr);
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        auto it = V.blocks.find(blocks[b]);
+        if (it != V.blocks.end()) ptrs[b] = &it->second;
+    }
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long b = 0; b < (long)blocks.size(); ++b) {
+        Block* blk = ptrs[b];
+        if (!blk) continue;
+        if (marg[b]) blk->bflag = 1;
+        if (marg[b] == 2) continue;  // marginal non-member: not part of A(k, T)
+        long bx, by, bz;
+        unpack(blocks[b], &bx, &by, &bz);
+        for (int lz = 0; lz < BS; ++lz)
+            for (int ly = 0; ly < BS; ++ly)
+                for (int lx = 0; lx < BS; ++lx) {
+                    int vi = lx + BS * ly + BS * BS * lz;
+                    Sample S = sample_voxel(V, depth, rgba, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
+                    if (S.marginal) blk->vflag[vi] = 1;
+                    if (!S.upd) continue;
+                    const double w = 1.0;
+                    double Wv = blk->W[vi];
+                    if (sign > 0) {
+                        blk->D[vi] = (blk->D[vi] * Wv + S.d * w) / (Wv + w);
+                        for (int ch = 0; ch < 3; ++ch) {
+                            double c = (blk->C[vi][ch] * Wv + S.c[ch] * w) / (Wv + w);
+                            blk->C[vi][ch] = V.rgba8 ? to_u8(c) : c;
+                        }
+                        blk->W[vi] = Wv + w;
+                    } else {
+                        double Wn = Wv - w;  // Eq. 2
+                        if (Wn == 0.0) {
+                            blk->D[vi] = 0.0;
+                            for (int ch = 0; ch < 3; ++ch) blk->C[vi][ch] = 0.0;
+                        } else {
+                            blk->D[vi] = (blk->D[vi] * Wv - S.d * w) / Wn;
+                            for (int ch = 0; ch < 3; ++ch) {
+                                double c = (blk->C[vi][ch] * Wv - S.c[ch] * w) / Wn;
+                                blk->C[vi][ch] = V.rgba8 ? to_u8(c) : c;
+                            }
+                        }
+                        blk->W[vi] = Wn;
+                    }
+                }
+    }
+}
+
+}  // namespace
+
+extern "C" void or_set_margins(double tau_px, double tau_m, double tau_rel) {
+    g_tau_px = tau_px;
+    g_tau_m = tau_m;
+    g_tau_rel = tau_rel;
+}
+
+extern "C" void or_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+extern "C" int or_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+extern "C" void* or_vol_create(double voxel_size, double trunc, int rgba8) {
+    Vol* V = new Vol();
+    V->s = voxel_size;
+    V->mu = trunc;
+    V->rgba8 = rgba8;
+    return V;
+}
+
+extern "C" void or_vol_destroy(void* vol) { delete (Vol*)vol; }
+
+extern "C" void* or_vol_clone(void* vol) { return new Vol(*(Vol*)vol); }
+
+// Integrate keyframe kf_id at pose T: first allocate A(k, T), then update the
+// voxels of exactly those blocks (reading: an integration touches only the
+// blocks its own band segments reach, so that Eq. 2 run on the same block list
+// is its exact inverse).  Returns -1 if kf_id is already integrated.
+extern "C" int or_integrate(void* vol, int kf_id, const float* depth, const uint8_t* rgba,
+                            double fx, double fy, double cx, double cy, int W, int H, const float* pose) {
+    Vol& V = *(Vol*)vol;
+    if (V.touched.count(kf_id)) return -1;
+    const Intr K{fx, fy, cx, cy, W, H};
+    const Pose T = pose_from(pose);
+    Touched tl;
+    allocation_set(V, depth, K, T, tl.blocks, tl.marginal);
+    for (size_t b = 0; b < tl.blocks.size(); ++b) {
+        if (tl.marginal[b] != 2) V.blocks.try_emplace(tl.blocks[b]);
+        if (tl.marginal[b] != 0) V.ghosts[tl.blocks[b]] = 1;
+    }
+    update_blocks(V, tl.blocks, tl.marginal, depth, rgba, K, T, +1);
+    V.touched[kf_id] = std::move(tl);
+    return 0;
+}
+
+// De-integrate keyframe kf_id, Eq. 2, with the depth, colour and pose it was
+// integrated with, over its stored block list.  Returns -1 if not integrated.
+extern "C" int or_deintegrate(void* vol, int kf_id, const float* depth, const uint8_t* rgba,
+                              double fx, double fy, double cx, double cy, int W, int H, const float* pose) {
+    Vol& V = *(Vol*)vol;
+    auto it = V.touched.find(kf_id);
+    if (it == V.touched.end()) return -1;
+    const Intr K{fx, fy, cx, cy, W, H};
+    const Pose T = pose_from(pose);
+    update_blocks(V, it->second.blocks, it->second.marginal, depth, rgba, K, T, -1);
+    V.touched.erase(it);
+    return 0;
+}
+
+// One pose-graph update (Section 4.3 "Re-integration strategy"): de-integrate
+// every item at its former pose, in item order, then integrate every item at
+// its updated pose, in item order.  depths [n][H][W], rgba [n][H][W][4],
+// poses [n][12].
+extern "C" int or_reintegrate_batch(void* vol, int n, const int* kf_ids, const float* depths, const uint8_t* rgba,
+                                    const float* old_poses, const float* new_poses,
+                                    double fx, double fy, double cx, double cy, int W, int H) {
+    long img = (long)W * H;
+    for (int i = 0; i < n; ++i) {
+        int rc = or_deintegrate(vol, kf_ids[i], depths + i * img, rgba ? rgba + 4 * i * img : nullptr,
+                                fx, fy, cx, cy, W, H, old_poses + 12 * i);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        int rc = or_integrate(vol, kf_ids[i], depths + i * img, rgba ? rgba + 4 * i * img : nullptr,
+                              fx, fy, cx, cy, W, H, new_poses + 12 * i);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+extern "C" long or_vol_num_blocks(void* vol) { return (long)((Vol*)vol)->blocks.size(); }
+
+// Export blocks in ascending key order: coords [n][3], D/W [n][512], C [n][512][3],
+// bflag [n], vflag [n][512].
+extern "C" void or_vol_export(void* vol, int32_t* coords, double* D, double* Wt, double* C, uint8_t* bflag,
+                              uint8_t* vflag) {
+    Vol& V = *(Vol*)vol;
+    std::vector<int64_t> keys;
+    keys.reserve(V.blocks.size());
+    for (auto& kv : V.blocks) keys.push_back(kv.first);
+    std::sort(keys.begin(), keys.end());
+    for (size_t i = 0; i < keys.size(); ++i) {
+        long x, y, z;
+        unpack(keys[i], &x, &y, &z);
+        coords[3 * i] = (int32_t)x;
+        coords[3 * i + 1] = (int32_t)y;
+        coords[3 * i + 2] = (int32_t)z;
+        const Block& b = V.blocks[keys[i]];
+        if (D) std::memcpy(D + i * NV, b.D, sizeof(b.D));
+        if (Wt) std::memcpy(Wt + i * NV, b.W, sizeof(b.W));
+        if (C) std::memcpy(C + i * NV * 3, b.C, sizeof(b.C));
+        if (bflag) bflag[i] = b.bflag | (V.ghosts.count(keys[i]) ? 1 : 0);
+        if (vflag) std::memcpy(vflag + i * NV, b.vflag, NV);
+    }
+}
+
+// Blocks that some integration reached only marginally and that this reference
+// did not allocate: count, or fills coords [n][3].
+extern "C" long or_vol_ghosts(void* vol, int32_t* coords) {
+    Vol& V = *(Vol*)vol;
+    std::vector<int64_t> keys;
+    for (auto& kv : V.ghosts)
+        if (!V.blocks.count(kv.first)) keys.push_back(kv.first);
+    std::sort(keys.begin(), keys.end());
+    if (coords) {
+        for (size_t i = 0; i < keys.size(); ++i) {
+            long x, y, z;
+            unpack(keys[i], &x, &y, &z);
+            coords[3 * i] = (int32_t)x;
+            coords[3 * i + 1] = (int32_t)y;
+            coords[3 * i + 2] = (int32_t)z;
+        }
+    }
+    return (long)keys.size();
+}
+
+// The stored block list of kf_id: count, or fills coords [n][3] and marginal [n]
+// (0 robust member, 1 marginal member, 2 marginal non-member).
+extern "C" long or_vol_touched(void* vol, int kf_id, int32_t* coords, uint8_t* marginal) {
+    Vol& V = *(Vol*)vol;
+    auto it = V.touched.find(kf_id);
+    if (it == V.touched.end()) return -1;
+    const Touched& t = it->second;
+    if (coords) {
+        for (size_t i = 0; i < t.blocks.size(); ++i) {
+            long x, y, z;
+            unpack(t.blocks[i], &x, &y, &z);
+            coords[3 * i] = (int32_t)x;
+            coords[3 * i + 1] = (int32_t)y;
+            coords[3 * i + 2] = (int32_t)z;
+            if (marginal) marginal[i] = t.marginal[i];
+        }
+    }
+    return (long)t.blocks.size();
+}
+
+// Allocation set A(k, T) alone, without touching any volume: returns the count
+// or fills coords [n][3] and marginal [n] (as or_vol_touched).
+extern "C" long or_allocation_set(double voxel_size, double trunc, const float* depth, double fx, double fy,
+                                  double cx, double cy, int W, int H, const float* pose, int32_t* coords,
+                                  uint8_t* marginal) {
+    Vol V;
+    V.s = voxel_size;
+    V.mu = trunc;
+    V.rgba8 = 0;
+    const Intr K{fx, fy, cx, cy, W, H};
+    std::vector<int64_t> out;
+    std::vector<uint8_t> marg;
+    allocation_set(V, depth, K, pose_from(pose), out, marg);
+    if (coords) {
+        for (size_t i = 0; i < out.size(); ++i) {
+            long x, y, z;
+            unpack(out[i], &x, &y, &z);
+            coords[3 * i] = (int32_t)x;
+            coords[3 * i + 1] = (int32_t)y;
+            coords[3 * i + 2] = (int32_t)z;
+            if (marginal) marginal[i] = marg[i];
+        }
+    }
+    return (long)out.size();
+}
+
+// ============================================================================
+// Keyframe selection (Section 4.3, Eq. 3, Fig. 4)
+// ============================================================================
+
+// ||s t_i - s t_i'|| with t = (Euler angles, translation), s = (2,2,2,1,1,1).
+// Reading: Z-Y-X Euler angles (R = Rz(a) Ry(b) Rx(c)) of the world_from_camera
+// rotation, in radians, each angle difference wrapped to (-pi, pi].
+extern "C" double or_pose_distance(const float* T0, const float* T1) {
+    auto euler = [](const Pose& P, double e[3]) {
+        e[1] = std::asin(std::max(-1.0, std::min(1.0, -P.R[2][0])));
+        e[0] = std::atan2(P.R[1][0], P.R[0][0]);
+        e[2] = std::atan2(P.R[2][1], P.R[2][2]);
+    };
+    Pose A = pose_from(T0), B = pose_from(T1);
+    double ea[3], eb[3];
+    euler(A, ea);
+    euler(B, eb);
+    const double pi = 3.14159265358979323846;
+    double acc = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double d = ea[k] - eb[k];
+        while (d > pi) d -= 2 * pi;
+        while (d <= -pi) d += 2 * pi;
+        acc += (2.0 * d) * (2.0 * d);
+    }
+    for (int k = 0; k < 3; ++k) {
+        double d = A.t[k] - B.t[k];
+        acc += d * d;
+    }
+    return std::sqrt(acc);
+}
+
+// The m most-moved keyframes: descending distance, ties to the lower index.
+extern "C" void or_select_topm(const double* dist, int K, int m, int* out) {
+    std::vector<int> idx(K);
+    for (int i = 0; i < K; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return dist[a] > dist[b]; });
+    for (int i = 0; i < m && i < K; ++i) out[i] = idx[i];
+}
+
+// Eq. 3: first index j (0-based) of the m consecutive keyframes with the
+// largest summed distance; ties to the smallest j.
+extern "C" int or_select_consecutive(const double* dist, int K, int m, double* sums_out) {
+    int best = -1;
+    double best_sum = -1.0;
+    for (int j = 0; j + m <= K; ++j) {
+        double s = 0.0;
+        for (int i = j; i < j + m; ++i) s += dist[i];
+        if (sums_out) sums_out[j] = s;
+        if (s > best_sum) {
+            best_sum = s;
+            best = j;
+        }
+    }
+    return best;
+}
+
+// ============================================================================
+// Loss on the fused SDF and its gradient (no counterpart in the paper)
+// ============================================================================
+//
+// L = (1/P) sum_p Dt(p)^2 + lambda * sum_v W(v) D(v)^2 / sum_v W(v)
+// Dt(p) is the trilinear interpolation of D over the 8 voxels around p (voxel i
+// at i*s); points whose 8 voxels are not all observed (W > 0) are dropped and P
+// counts the rest.  The second sum runs over voxels with W > 0.
+
+namespace {
+
+struct DOverlay {
+    // optional replacement D values: block key -> D[512]
+    const std::unordered_map<int64_t, std::vector<double>>* over = nullptr;
+};
+
+bool voxel_at(const Vol& V, const DOverlay& ov, long ix, long iy, long iz, double* D, double* W) {
+    long bx = floor_div(ix, BS), by = floor_div(iy, BS), bz = floor_div(iz, BS);
+    int64_t key = pack(bx, by, bz);
+    auto it = V.blocks.find(key);
+    if (it == V.blocks.end()) return false;
+    int vi = (int)(ix - bx * BS) + BS * (int)(iy - by * BS) + BS * BS * (int)(iz - bz * BS);
+    *W = it->second.W[vi];
+    *D = it->second.D[vi];
+    if (ov.over) {
+        auto jt = ov.over->find(key);
+        if (jt != ov.over->end()) *D = jt->second[vi];
+    }
+    return *W > 0.0;
+}
+
+struct PointEval {
+    bool valid;
+    bool marginal;
+    double Dt;
+    long ix[8], iy[8], iz[8];
+    double beta[8];
+};
+
+PointEval eval_point(const Vol& V, const DOverlay& ov, const double* p) {
+    PointEval E{};
+    E.valid = false;
+    E.marginal = false;
+    double g[3], f[3];
+    long i0[3];
+    for (int a = 0; a < 3; ++a) {
+        g[a] = p[a] / V.s;
+        double fl = std::floor(g[a]);
+        i0[a] = (long)fl;
+        f[a] = g[a] - fl;
+        if (f[a] < 1e-6 || f[a] > 1.0 - 1e-6) E.marginal = true;
+    }
+    double acc = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int ox = c & 1, oy = (c >> 1) & 1, oz = (c >> 2) & 1;
+        E.ix[c] = i0[0] + ox;
+        E.iy[c] = i0[1] + oy;
+        E.iz[c] = i0[2] + oz;
+        E.beta[c] = (ox ? f[0] : 1 - f[0]) * (oy ? f[1] : 1 - f[1]) * (oz ? f[2] : 1 - f[2]);
+        double D, W;
+        if (!voxel_at(V, ov, E.ix[c], E.iy[c], E.iz[c], &D, &W)) return E;
+        acc += E.beta[c] * D;
+    }
+    E.valid = true;
+    E.Dt = acc;
+    return E;
+}
+
+double loss_impl(const Vol& V, const DOverlay& ov, const double* pts, long n, double lambda, long* n_valid,
+                 uint8_t* pflag) {
+    double s1 = 0.0;
+    long P = 0;
+    for (long i = 0; i < n; ++i) {
+        PointEval E = eval_point(V, ov, pts + 3 * i);
+        if (pflag) pflag[i] = E.marginal;
+        if (!E.valid) continue;
+        s1 += E.Dt * E.Dt;
+        ++P;
+    }
+    double swd = 0.0, sw = 0.0;
+    for (auto& kv : V.blocks) {
+        const std::vector<double>* od = nullptr;
+        if (ov.over) {
+            auto jt = ov.over->find(kv.first);
+            if (jt != ov.over->end()) od = &jt->second;
+        }
+        for (int vi = 0; vi < NV; ++vi) {
+            double W = kv.second.W[vi];
+            if (!(W > 0.0)) continue;
+            double D = od ? (*od)[vi] : kv.second.D[vi];
+            swd += W * D * D;
+            sw += W;
+        }
+    }
+    if (n_valid) *n_valid = P;
+    double L = (P > 0 ? s1 / (double)P : 0.0);
+    if (sw > 0.0) L += lambda * swd / sw;
+    return L;
+}
+
+// T(xi) = exp(xi^) T with xi = (rho, omega) (reading: left perturbation of the
+// world_from_camera pose, Rodrigues exponential).
+Pose perturb(const Pose& T, const double* xi) {
+    const double* rho = xi;
+    const double* w = xi + 3;
+    double th = std::sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    double Kx[3][3] = {{0, -w[2], w[1]}, {w[2], 0, -w[0]}, {-w[1], w[0], 0}};
+    double K2[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            K2[r][c] = 0;
+            for (int k = 0; k < 3; ++k) K2[r][c] += Kx[r][k] * Kx[k][c];
+        }
+    double A, Bc, Cc;
+    if (th < 1e-8) {
+        A = 1.0 - th * th / 6.0;
+        Bc = 0.5 - th * th / 24.0;
+        Cc = 1.0 / 6.0 - th * th / 120.0;
+    } else {
+        A = std::sin(th) / th;
+        Bc = (1 - std::cos(th)) / (th * th);
+        Cc = (th - std::sin(th)) / (th * th * th);
+    }
+    double Rx[3][3], Vx[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double I = (r == c) ? 1.0 : 0.0;
+            Rx[r][c] = I + A * Kx[r][c] + Bc * K2[r][c];
+            Vx[r][c] = I + Bc * Kx[r][c] + Cc * K2[r][c];
+        }
+    Pose O;
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) {
+            O.R[r][c] = 0;
+            for (int k = 0; k < 3; ++k) O.R[r][c] += Rx[r][k] * T.R[k][c];
+        }
+        O.t[r] = 0;
+        for (int k = 0; k < 3; ++k) O.t[r] += Rx[r][k] * T.t[k] + Vx[r][k] * rho[k];
+    }
+    return O;
+}
+
+}  // namespace
+
+extern "C" double or_loss(void* vol, const double* pts, long n, double lambda, long* n_valid, uint8_t* pflag) {
+    DOverlay ov;
+    return loss_impl(*(Vol*)vol, ov, pts, n, lambda, n_valid, pflag);
+}
+
+// Analytic gradient of L with respect to each listed keyframe's pose (left
+// se(3) perturbation xi = (rho, omega) at xi = 0) and depth pixels.
+//   D(v) = sum_k w_k d_k(v) / W(v)  =>  dD(v)/dd_k = w_k / W(v)
+//   d_k = Z_k(x) - z_c  when unclamped (eta < mu), else mu (zero derivative)
+//   dd/dZ_k(x) = 1;  dd/dxi = -dz_c/dxi,  p_c = R^T (p_v - t)
+//   dp_c/drho = -R^T,  dp_c/domega = R^T [p_v]_x
+// Pixel assignment, band membership and the clamp are piecewise constant in the
+// pose and depth; they contribute no derivative.
+// grad_xi [K][6] (rho then omega), grad_depth [K][H][W] (may be null).
+extern "C" int or_grad(void* vol, int K_, const int* kf_ids, const float* depths, const uint8_t* rgba,
+                       const float* poses, double fx, double fy, double cx, double cy, int W, int H,
+                       const double* pts, long n, double lambda, double* grad_xi, double* grad_depth) {
+    Vol& V = *(Vol*)vol;
+    const Intr K{fx, fy, cx, cy, W, H};
+    DOverlay ov;
+    // dL/dD(v)
+    std::unordered_map<int64_t, std::vector<double>> G;
+    double sw = 0.0;
+    for (auto& kv : V.blocks)
+        for (int vi = 0; vi < NV; ++vi)
+            if (kv.second.W[vi] > 0.0) sw += kv.second.W[vi];
+    for (auto& kv : V.blocks) {
+        std::vector<double> g(NV, 0.0);
+        for (int vi = 0; vi < NV; ++vi)
+            if (kv.second.W[vi] > 0.0 && sw > 0.0) g[vi] = 2.0 * lambda * kv.second.W[vi] * kv.second.D[vi] / sw;
+        G.emplace(kv.first, std::move(g));
+    }
+    std::vector<PointEval> evs;
+    long P = 0;
+    for (long i = 0; i < n; ++i) {
+        PointEval E = eval_point(V, ov, pts + 3 * i);
+        if (E.valid) {
+            evs.push_back(E);
+            ++P;
+        }
+    }
+    for (const PointEval& E : evs) {
+        for (int c = 0; c < 8; ++c) {
+            long bx = floor_div(E.ix[c], BS), by = floor_div(E.iy[c], BS), bz = floor_div(E.iz[c], BS);
+            int vi = (int)(E.ix[c] - bx * BS) + BS * (int)(E.iy[c] - by * BS) + BS * BS * (int)(E.iz[c] - bz * BS);
+            G[pack(bx, by, bz)][vi] += 2.0 / (double)P * E.Dt * E.beta[c];
+        }
+    }
+    long img = (long)W * H;
+    for (int k = 0; k < K_; ++k) {
+        double* gx = grad_xi + 6 * k;
+        for (int j = 0; j < 6; ++j) gx[j] = 0.0;
+        double* gd = grad_depth ? grad_depth + k * img : nullptr;
+        if (gd)
+            for (long q = 0; q < img; ++q) gd[q] = 0.0;
+        auto it = V.touched.find(kf_ids[k]);
+        if (it == V.touched.end()) return -1;
+        const Pose T = pose_from(poses + 12 * k);
+        const float* depth = depths + k * img;
+        const double r3[3] = {T.R[0][2], T.R[1][2], T.R[2][2]};  // third row of R^T
+        const Touched& tl = it->second;
+        for (size_t b = 0; b < tl.blocks.size(); ++b) {
+            if (tl.marginal[b] == 2) continue;
+            long bx, by, bz;
+            unpack(tl.blocks[b], &bx, &by, &bz);
+            const Block& blk = V.blocks.at(tl.blocks[b]);
+            const std::vector<double>& g = G.at(tl.blocks[b]);
+            for (int lz = 0; lz < BS; ++lz)
+                for (int ly = 0; ly < BS; ++ly)
+                    for (int lx = 0; lx < BS; ++lx) {
+                        int vi = lx + BS * ly + BS * BS * lz;
+                        Sample S = sample_voxel(V, depth, nullptr, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
+                        if (!S.upd || S.clamped) continue;
+                        double gv = g[vi] * 1.0 / blk.W[vi];
+                        if (gd) gd[S.pix] += gv;
+                        // -dz_c/drho = r3 ; -dz_c/domega = -(r3 x p_v) = p_v x r3
+                        const double* p = S.pv;
+                        double cx_[3] = {p[1] * r3[2] - p[2] * r3[1], p[2] * r3[0] - p[0] * r3[2],
+                                         p[0] * r3[1] - p[1] * r3[0]};
+                        for (int j = 0; j < 3; ++j) {
+                            gx[j] += gv * r3[j];
+                            gx[3 + j] += gv * cx_[j];
+                        }
+                    }
+        }
+    }
+    (void)rgba;
+    return 0;
+}
+
+// Loss with keyframe kf_ids[k_sel]'s contribution re-evaluated at the perturbed
+// pose exp(xi^) T_k and depth Z_k + dz * [pixel == pix] (pix < 0: no depth
+// change), with every discrete decision (pixel, band membership, clamp) frozen
+// at the unperturbed state:  D'(v) = D(v) + (d_k(v; xi, dz) - d_k(v; 0)) w / W(v).
+// Used for central finite differences.
+extern "C" double or_loss_perturbed(void* vol, int kf_id, const float* depth, const float* pose, double fx,
+                                    double fy, double cx, double cy, int W, int H, const double* xi, long pix,
+                                    double dz, const double* pts, long n, double lambda) {
+    Vol& V = *(Vol*)vol;
+    const Intr K{fx, fy, cx, cy, W, H};
+    auto it = V.touched.find(kf_id);
+    if (it == V.touched.end()) return NAN;
+    const Pose T = pose_from(pose);
+    const Pose Tp = perturb(T, xi);
+    std::unordered_map<int64_t, std::vector<double>> over;
+    const Touched& tl = it->second;
+    for (size_t b = 0; b < tl.blocks.size(); ++b) {
+        if (tl.marginal[b] == 2) continue;
+        long bx, by, bz;
+        unpack(tl.blocks[b], &bx, &by, &bz);
+        const Block& blk = V.blocks.at(tl.blocks[b]);
+        std::vector<double> D(blk.D, blk.D + NV);
+        bool any = false;
+        for (int lz = 0; lz < BS; ++lz)
+            for (int ly = 0; ly < BS; ++ly)
+                for (int lx = 0; lx < BS; ++lx) {
+                    int vi = lx + BS * ly + BS * BS * lz;
+                    Sample S = sample_voxel(V, depth, nullptr, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
+                    if (!S.upd || S.clamped) continue;
+                    double pc[3];
+                    apply_inv(Tp, S.pv, pc);
+                    double Z = (double)depth[S.pix] + (S.pix == pix ? dz : 0.0);
+                    double d_new = Z - pc[2];
+                    D[vi] += (d_new - S.d) * 1.0 / blk.W[vi];
+                    any = true;
+                }
+        if (any) over.emplace(tl.blocks[b], std::move(D));
+    }
+    DOverlay ov;
+    ov.over = &over;
+    return loss_impl(V, ov, pts, n, lambda, nullptr, nullptr);
+}
