@@ -1,0 +1,460 @@
+"""Benchmark: keyframe de-/re-integrations per second on the Kinect-scale workload.
+
+Workload (640x480 Kinect-class frames, 1 cm voxels, 4 cm truncation, 2^20 hash
+buckets): 600 synthetic depth + colour frames of a 10x8x3 m multi-room scene,
+fused 10 per keyframe into 60 keyframes, integrated at drifted poses, then one
+pose-graph update re-integrates all 60 at their true poses.  The inputs are
+seeded synthetic stand-ins for the paper's RGB-D sequences; all of them (737 MB of
+depth, 737 MB of colour) are resident in HBM before the timed region, and they
+exceed the 126 MB L2, so no flush is needed between steps.
+
+One step = one pass of the whole hot path over that input:
+  fuse 600 frames into 60 keyframes (Eq. 1) -> reset the volume -> integrate the 60
+  keyframes (allocation + running average) -> ONE batched pose update (de-integrate
+  all 60 at the drifted poses, re-integrate at the true poses) -> SDF loss at 1 M
+  surface points + adjoint for all 60 keyframes -> extract the block list.
+value = 60 re-integrations / step time.  The JSON line also reports the update
+alone, batched (one graph) vs plain (120 per-keyframe calls), the roofline of the
+dominant kernel, the oracle on the host cores, clocks and the kernel count.
+
+--gpus N > 1 (under torchrun) runs N independent replicas (the path does not
+shard across GPUs in this build); value sums the replicas' throughput.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "keyframe de+re-integrations/s @640x480,1cm; batched vs plain; HBM GB/s % peak"
+UNIT = "re-integrations/s"
+KAPPA = 10
+N_FRAMES = 600
+N_POINTS = 1_000_000
+LAMBDA = 0.1
+IMG_BYTES = 640 * 480 * (4 + 4)  # keyframe depth f32 + RGBA8
+VOXEL_BYTES_RW = 24             # D, W, RGBA8: 12 B read + 12 B written per voxel
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=20, help="keyframe re-integrations the oracle times")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+                for name, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.remove(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+# --------------------------------------------------------------------------------------
+
+def make_workload(device):
+    import torch
+    from paper_1709_03763_b300 import synthetic
+    w = synthetic.workload_kinect(device=device, n_frames=N_FRAMES, kappa=KAPPA)
+    pts = synthetic.surface_points(w.scene, N_POINTS, 4, lo=np.array([0.0, 0.0, 0.0]),
+                                   hi=np.array([10.0, 8.0, 3.0]))
+    w.extra["points"] = torch.tensor(pts, dtype=torch.float32, device=device)
+    return w
+
+
+class Pipeline:
+    """One step of the whole hot path (see module docstring)."""
+
+    def __init__(self, w, vol):
+        import torch
+        self.w = w
+        self.V = vol
+        K = N_FRAMES // KAPPA
+        self.K = K
+        dev = w.frames_depth.device
+        self.kf_depth = torch.empty((K, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
+        self.kf_weight = torch.empty_like(self.kf_depth)
+        self.kf_rgba = w.kf_rgba
+        self.ids = list(range(K))
+        self.frame_poses = w.frame_poses
+        self.drift = w.kf_poses
+        self.true = w.new_poses
+        self.grad_D = vol.grad_buffer()
+
+    def fuse(self):
+        from paper_1709_03763_b300 import fuse_frames_into_keyframe
+        w = self.w
+        for k in range(self.K):
+            s = k * KAPPA
+            fuse_frames_into_keyframe(w.frames_depth[s:s + KAPPA], self.frame_poses[s:s + KAPPA],
+                                      self.frame_poses[s], w.intr, 0.1, self.kf_depth[k], self.kf_weight[k])
+
+    def integrate(self):
+        self.V.reset()
+        for k in range(self.K):
+            self.V.integrate(k, self.kf_depth[k], self.kf_rgba[k], self.w.intr, self.drift[k])
+
+    def update_batched(self):
+        self.V.reintegrate_batch(self.ids, self.kf_depth, self.kf_rgba, self.drift, self.true, self.w.intr)
+
+    def update_plain(self):
+        for k in self.ids:
+            self.V.deintegrate(k, self.kf_depth[k], self.kf_rgba[k], self.w.intr, self.drift[k])
+        for k in self.ids:
+            self.V.integrate(k, self.kf_depth[k], self.kf_rgba[k], self.w.intr, self.true[k])
+
+    def loss_adjoint(self):
+        out, _ = self.V.sdf_loss(self.w.extra["points"], LAMBDA, grad_D=self.grad_D)
+        gx, gd = self.V.sdf_adjoint(self.ids, self.kf_depth, self.true, self.w.intr, self.grad_D, with_depth=True)
+        return out, gx, gd
+
+    def extract(self):
+        return self.V.extract(payload=False, capacity=self.capacity)
+
+    def step(self):
+        self.fuse()
+        self.integrate()
+        self.update_batched()
+        out, gx, gd = self.loss_adjoint()
+        ex = self.extract()
+        return out, ex
+
+
+def time_region(fn, steps, warmup, ws):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(ws)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1) / steps
+    return max_over_ranks(ms, ws)
+
+
+def update_only_timing(P, steps, batched: bool):
+    """Median time of one 60-keyframe pose update (the integrated state is re-built before
+    each repetition, outside the timed part)."""
+    import torch
+    ts = []
+    s = torch.cuda.current_stream()
+    for _ in range(steps):
+        P.integrate()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        (P.update_batched if batched else P.update_plain)()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def oracle_reintegration(n_kf, steps=1, warmup=0, w=None):
+    """The FP64 oracle, as it stands, re-integrating the first n_kf keyframes of this
+    workload (de-integrate at the drifted pose + integrate at the true pose, allocation
+    included) on the host cores.  Its keyframe depth is the oracle's own Eq. 1 fusion of
+    the keyframe's 10 frames.  Returns (median seconds per step, threads used)."""
+    import oracle
+    from paper_1709_03763_b300 import synthetic
+    oracle.build()
+    if w is None:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        w = synthetic.workload_kinect(device=dev, n_frames=N_FRAMES, kappa=KAPPA, render_frames=n_kf * KAPPA)
+    it = w.intr.as_tuple()
+    frames = w.frames_depth[:n_kf * KAPPA].cpu()
+    depth = []
+    for k in range(n_kf):
+        s = k * KAPPA
+        Z, _, _ = oracle.fuse(frames[s:s + KAPPA], w.frame_poses[s:s + KAPPA], w.frame_poses[s], it)
+        depth.append(Z.astype(np.float32))
+    rgba = w.kf_rgba.cpu().numpy()
+    times = []
+    for step in range(warmup + steps):
+        O = oracle.Volume(w.voxel_size, w.trunc, rgba8=True)
+        for k in range(n_kf):
+            O.integrate(k, depth[k], rgba[k], it, w.kf_poses[k])
+        t0 = time.perf_counter()
+        for k in range(n_kf):
+            O.deintegrate(k, depth[k], rgba[k], it, w.kf_poses[k])
+            O.integrate(k, depth[k], rgba[k], it, w.new_poses[k])
+        if step >= warmup:
+            times.append(time.perf_counter() - t0)
+    return statistics.median(times), oracle.get_threads()
+
+
+def cpu_baseline(n_kf, w):
+    dt, cores = oracle_reintegration(n_kf, w=w)
+    return {"value": n_kf / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_kf} keyframe re-integrations (de-integrate at drifted pose + integrate at true pose, "
+                      f"allocation included) of the 640x480 / 1 cm workload, RGBA8 colour, FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n_kf = max(1, args.cpu_sample)
+    sec, cores = oracle_reintegration(n_kf, steps=args.steps, warmup=args.warmup)
+    ms = sec * 1000.0
+    value = n_kf / sec
+    sample = (f"{n_kf} keyframe re-integrations per step (de-integrate at drifted pose + integrate at true "
+              f"pose, allocation included), 640x480, 1 cm voxels, FP64")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "kinect-scale: 60 keyframes 640x480 fused from 600 frames, voxel 1 cm, "
+                                   "trunc 4 cm, 2^20 buckets", "sample_keyframes": n_kf},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    ws, rank, local = dist_init()
+    from paper_1709_03763_b300 import Volume, lib
+    from paper_1709_03763_b300 import build as _build
+    _build.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    t_setup = time.perf_counter()
+    w = make_workload(dev)
+    V = Volume(w.voxel_size, w.trunc, w.n_buckets, bucket_size=4, max_blocks=1 << 21, colour="rgba8",
+               max_keyframes=64, max_blocks_per_keyframe=1 << 17, max_batch=64)
+    P = Pipeline(w, V)
+    P.capacity = 1 << 21
+    P.fuse()
+    P.integrate()
+    torch.cuda.synchronize()
+    cfg, tune_ms = V.autotune_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true, w.intr)
+    setup_s = time.perf_counter() - t_setup
+
+    # ---- the timed whole-path step
+    L0 = lib().sc_kernel_launches()
+    with Clocks(local) as clk:
+        ms = time_region(P.step, args.steps, args.warmup, ws)
+    launches_per_step = (lib().sc_kernel_launches() - L0) / (args.steps + args.warmup)
+    clocks = clk.summary()
+    value = ws * P.K / (ms / 1000.0)
+
+    # ---- end to end through the public API with host buffers: per step, the 600 frames
+    # (depth + colour) go host -> device from pinned memory and the loss / block count
+    # come back
+    h_depth = w.frames_depth.cpu().pin_memory()
+    h_rgba = w.frames_rgba.cpu().pin_memory()
+    h_out = torch.empty(6, dtype=torch.float64).pin_memory()
+    d_depth, d_rgba = w.frames_depth, w.frames_rgba
+
+    def e2e_step():
+        d_depth.copy_(h_depth, non_blocking=True)
+        d_rgba.copy_(h_rgba, non_blocking=True)
+        out, ex = P.step()
+        h_out[:5].copy_(out, non_blocking=True)
+        h_out[5] = ex["coords"].shape[0]
+    e2e_ms = time_region(e2e_step, args.steps, args.warmup, ws)
+    h2d = h_depth.numel() * 4 + h_rgba.numel()
+    d2h = 5 * 8 + 8
+
+    # ---- breakdown: the update alone, batched vs plain; per-kernel profile of one step
+    upd_batched_ms = update_only_timing(P, 5, True)
+    upd_plain_ms = update_only_timing(P, 5, False)
+    V.set_profiling(True)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record(s)
+    P.fuse()
+    ev[1].record(s)
+    P.integrate()
+    ev[2].record(s)
+    P.update_batched()
+    ev[3].record(s)
+    P.loss_adjoint()
+    ev[4].record(s)
+    P.extract()
+    ev[5].record(s)
+    torch.cuda.synchronize()
+    prof = V.profile()
+    stage = {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(["fuse", "integrate", "batched_update",
+                                                                      "loss_adjoint", "extract"])}
+    V.set_profiling(False)
+
+    peak, peak_kind = peaks()
+    # candidate dominant kernels with their algorithmic bytes per launch
+    kernels = {}
+    if prof["update_launches"]:
+        nb = prof["update_blocks"] / prof["update_launches"]
+        kernels["update_voxels"] = (prof["update_ms"] / prof["update_launches"],
+                                    nb * 512 * VOXEL_BYTES_RW + IMG_BYTES + nb * 32, prof["update_ms"])
+    if prof["batch_launches"]:
+        u = prof["batch_union_blocks"] / prof["batch_launches"]
+        kernels["net_delta"] = (prof["batch_net_ms"] / prof["batch_launches"],
+                                u * 512 * VOXEL_BYTES_RW + P.K * IMG_BYTES + prof["batch_pairs"] * 4,
+                                prof["batch_net_ms"])
+    dom = max(kernels, key=lambda k: kernels[k][2])
+    t_ms, bytes_, _ = kernels[dom]
+    achieved = bytes_ / (t_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_launch": bytes_, "ms_per_launch": t_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_sample, w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "kinect-scale: 600 frames 640x480 fused 10 per keyframe into 60 keyframes, "
+                                   "voxel 1 cm, trunc 4 cm, 2^20 buckets, one pose update of all 60, "
+                                   "1M-point SDF loss + adjoint, block-list extraction",
+                       "l2": "inputs (1.47 GB frames, ~2 GB voxel state) exceed L2; no flush",
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "colour": "rgba8", "batch_config": cfg},
+            "e2e": {"value": ws * P.K / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "gpu_launches_per_step": launches_per_step,
+            "update_only": {"batched_ms": upd_batched_ms, "plain_ms": upd_plain_ms,
+                            "batched_reint_per_s": P.K / (upd_batched_ms / 1000.0),
+                            "plain_reint_per_s": P.K / (upd_plain_ms / 1000.0),
+                            "union_blocks": prof["batch_union_blocks"], "pairs": prof["batch_pairs"]},
+            "stage_ms": stage,
+            "profile": prof,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "setup_s": setup_s,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,321 @@
+/*
+ * surfcorr.h -- C ABI of the B300 (sm_103a) keyframe surface-correction library.
+ *
+ * The library implements the GPU hot path of on-the-fly surface correction for
+ * large-scale RGB-D reconstruction (Maier, Schaller, Cremers, arXiv 1709.03763):
+ * keyframe depth fusion (Eq. 1), a voxel-hashed sparse truncated SDF with
+ * 8^3-voxel blocks (Section 3 "SDF volume"), keyframe integration by a running
+ * weighted average, its exact inverse (de-integration, Eq. 2) and batched
+ * re-integration on pose-graph updates (Section 4.3).  It adds two extensions
+ * the paper does not have: one persistent, graph-captured launch per pose update
+ * and an adjoint (backward) pass for a loss on the fused SDF.
+ *
+ * Conventions (Section 3 "Preliminaries"):
+ *   - A pose is world_from_camera: p_world = R p_cam + t, stored as a row-major
+ *     3x4 float matrix [R | t] (sc_pose).
+ *   - Pinhole intrinsics; pixel centres at integer (u, v); pi^-1(x, Z) =
+ *     ((u - cx) / fx * Z, (v - cy) / fy * Z, Z).  Depth is z-depth in metres, 0 or
+ *     negative = invalid.  Images are row-major [height][width]; colour is RGBA8
+ *     [height][width][4] (alpha ignored).
+ *   - Voxel index i (int3) sits at world position i * voxel_size; block b holds
+ *     voxels 8b .. 8b+7 on each axis.
+ *
+ * Memory and execution:
+ *   - Image, pose-output and gradient buffers are caller-owned device memory
+ *     (plain pointers, e.g. torch tensors' data_ptr()).  Device pointers must be
+ *     16-byte aligned.  Pose and item arrays are host memory unless stated.
+ *   - The volume (hash table, voxel pool, per-keyframe block lists, scratch)
+ *     is owned by the library and allocated on the device that is current when
+ *     sc_create_volume is called; every later call on that volume must run with
+ *     that device current.
+ *   - Calls are asynchronous on the given stream (NULL = legacy default stream)
+ *     unless stated.  Calls on one volume must be serialised by the caller (one
+ *     stream, or events between streams).
+ *   - Device-side failures (full hash table, full pool, full block list, a
+ *     bounded retry giving up) set a sticky per-volume status word; calls that
+ *     synchronise return it, and sc_get_status reads and clears it.  Host-side
+ *     argument errors are returned before anything is launched.
+ *
+ * Every entry point returns SC_OK (0) or a negative sc_status.
+ */
+#ifndef SURFCORR_H
+#define SURFCORR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SC_ABI_VERSION 1
+
+typedef enum {
+    SC_OK = 0,
+    SC_ERR_INVALID_ARG = -1,        /* bad pointer / size / id, rejected before launch */
+    SC_ERR_CUDA = -2,               /* a CUDA runtime call failed */
+    SC_ERR_HASH_FULL = -3,          /* no free hash entry within the probe limit */
+    SC_ERR_POOL_FULL = -4,          /* voxel pool has no free block */
+    SC_ERR_RETRY_LIMIT = -5,        /* a bounded device wait gave up */
+    SC_ERR_NOT_INTEGRATED = -6,     /* de-integrating a keyframe id that is not integrated */
+    SC_ERR_CAPACITY = -7,           /* output buffer too small (count still reported) */
+    SC_ERR_ALREADY_INTEGRATED = -8, /* integrating a keyframe id that is integrated */
+    SC_ERR_LIST_FULL = -9           /* a keyframe touched more blocks than its list holds */
+} sc_status;
+
+typedef enum { SC_RGBA8 = 0, SC_RGB_F32 = 1 } sc_colour_format;
+
+typedef void* sc_stream; /* a cudaStream_t */
+
+typedef struct sc_volume sc_volume;
+
+typedef struct {
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} sc_intrinsics;
+
+typedef struct {
+    float m[3][4]; /* [R | t], world_from_camera */
+} sc_pose;
+
+typedef struct {
+    float voxel_size;                 /* metres */
+    float trunc;                      /* truncation mu, metres */
+    uint32_t n_buckets;               /* hash buckets, power of two */
+    uint32_t bucket_size;             /* entries per bucket, 1..16 */
+    uint32_t max_blocks;              /* voxel pool capacity, 8^3 blocks, <= 2^23 */
+    int32_t colour_format;            /* SC_RGBA8 or SC_RGB_F32 */
+    int32_t max_keyframes;            /* keyframe ids are 0 .. max_keyframes-1 */
+    uint32_t max_blocks_per_keyframe; /* touched-list capacity per keyframe */
+    int32_t max_batch;                /* max items per sc_reintegrate_batch (<= 1024) */
+} sc_volume_params;
+
+typedef struct {
+    float disc_rel; /* drop pixels whose 4-neighbour depth differs by more than disc_rel * Z */
+} sc_fusion_params;
+
+/* One keyframe of a pose-graph update: de-integrate at old_pose, re-integrate at new_pose. */
+typedef struct {
+    const float* depth;   /* device [H][W] keyframe depth (same as at its integration) */
+    const uint8_t* rgba;  /* device [H][W][4] keyframe colour */
+    sc_pose old_pose;     /* pose it is currently integrated with */
+    sc_pose new_pose;     /* updated pose */
+    int32_t kf_id;
+} sc_reint_item;
+
+/* Launch configuration of the batched re-integration (chosen by sc_autotune_batch). */
+typedef struct {
+    int32_t warps_per_cta;   /* 2, 4, 8 or 16 */
+    int32_t ctas_per_sm;     /* persistent CTAs per SM, 1..16 */
+    int32_t blocks_per_grab; /* voxel blocks a warp takes from the queue at once, 1..16 */
+} sc_batch_config;
+
+typedef struct {
+    uint32_t allocated_blocks; /* pool slots in use */
+    uint32_t max_blocks;
+    uint32_t hash_entries;     /* n_buckets * bucket_size */
+    int32_t integrated_keyframes;
+    uint64_t device_bytes;     /* device memory owned by the volume */
+} sc_volume_info;
+
+/* ---------------------------------------------------------------- volume ---- */
+
+/* Create an empty volume (Section 3 "SDF volume") on the current device.
+ * All device memory is allocated here.  Returns SC_ERR_INVALID_ARG for a zero or
+ * non-power-of-two bucket count, a non-positive voxel size or truncation, or
+ * sizes out of range; SC_ERR_CUDA if allocation fails. */
+int sc_create_volume(const sc_volume_params* params, sc_volume** out);
+
+/* Free a volume and all its device memory (synchronises the device). */
+int sc_destroy_volume(sc_volume* vol);
+
+/* Empty the volume: clear the hash table, the pool counter and every keyframe's
+ * block list (stream-ordered).  Pool memory is re-initialised lazily: a block is
+ * zeroed by the first update that touches it after its allocation. */
+int sc_reset_volume(sc_volume* vol, sc_stream stream);
+
+/* Read (and clear) the sticky device status word; synchronises the stream the
+ * volume last used.  *device_status receives the sc_status the device reported. */
+int sc_get_status(sc_volume* vol, int32_t* device_status);
+
+int sc_get_volume_info(sc_volume* vol, sc_volume_info* info); /* synchronises */
+
+const char* sc_status_string(int status);
+
+/* -------------------------------------------------------- keyframe fusion ---- */
+
+/* Eq. 1 (Section 3 "Keyframe Fusion"): warp every valid pixel x of each of the
+ * n frames into the keyframe, p* = g(T*^-1, g(T_i, pi^-1(x, Z_i(x)))), round
+ * pi(p*) to the nearest pixel x*, and accumulate the depth-weighted average
+ *   Z*(x*) = sum w_z Z*_p / sum w_z,   W*(x*) = sum w_z,
+ * with w_z = cos(theta) / Z^2 (theta: angle between the central-difference depth
+ * normal and the camera axis).  Pixels on the border, with an invalid 4-neighbour
+ * or a neighbour depth jump above disc_rel * Z are dropped.
+ *   depths     device [n][H][W] frame depth
+ *   frame_poses host [n] frame poses T_i;  kf_pose host keyframe pose T*
+ *   kf_depth   device [H][W] output Z* (0 where W* = 0)
+ *   kf_weight  device [H][W] output W*
+ * Both outputs are overwritten.  n >= 1. */
+int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses, int32_t n,
+                                 const sc_pose* kf_pose, const sc_intrinsics* intr,
+                                 const sc_fusion_params* fusion, float* kf_depth, float* kf_weight,
+                                 sc_stream stream);
+
+/* ------------------------------------------------ integration (plain path) ---- */
+
+/* Integrate keyframe kf_id at pose T (Section 3 "SDF volume": voxel blocks are
+ * first allocated, then updated with a running weighted average):
+ *  1. allocation: every block whose closed box meets the band segment
+ *     {pi^-1(x, z) : z in [Z(x) - mu, Z(x) + mu]} (world coordinates) of a valid
+ *     pixel x is inserted into the hash table if absent; the set of these blocks,
+ *     A(k, T), becomes the keyframe's block list;
+ *  2. update: for each voxel v of each block in A(k, T): p_c = R^T (p_v - t);
+ *     x = nearest pixel of pi(p_c) (halves up); if z_c > 0, x inside the image,
+ *     Z(x) > 0 and eta = Z(x) - z_c >= -mu:
+ *       d = min(eta, mu), w = 1, c = rgba(x).rgb,
+ *       D <- (D W + d w) / (W + w),  C <- (C W + c w) / (W + w),  W <- W + w.
+ * depth device [H][W]; rgba device [H][W][4]; pose host.
+ * Returns SC_ERR_ALREADY_INTEGRATED if kf_id is integrated. */
+int sc_integrate_keyframe(sc_volume* vol, int32_t kf_id, const float* depth, const uint8_t* rgba,
+                          const sc_intrinsics* intr, const sc_pose* pose, sc_stream stream);
+
+/* De-integrate keyframe kf_id (Eq. 2, Section 4.3): over the keyframe's stored
+ * block list, with the same per-voxel d, c, w as its integration,
+ *   D <- (D W - d w) / (W - w),  C <- (C W - c w) / (W - w),  W <- W - w,
+ * and D = C = 0 where W reaches 0.  depth, rgba and pose must be the ones kf_id
+ * was integrated with.  Returns SC_ERR_NOT_INTEGRATED if kf_id is not integrated. */
+int sc_deintegrate_keyframe(sc_volume* vol, int32_t kf_id, const float* depth, const uint8_t* rgba,
+                            const sc_intrinsics* intr, const sc_pose* pose, sc_stream stream);
+
+/* ------------------------------------------------ batched re-integration ---- */
+
+/* One pose-graph update (Section 4.3 "Re-integration strategy"): de-integrate
+ * every item at old_pose and re-integrate it at new_pose.  The result equals
+ * de-integrating all items in order and then integrating all items in order
+ * (up to float rounding): the new poses' blocks are allocated first, then every
+ * voxel touched by any item receives its summed net change in one
+ * read-modify-write.  Runs as one CUDA graph (replayed across calls) whose voxel
+ * work is a single persistent launch.  items host [n], 1 <= n <= max_batch, kf_ids
+ * distinct and integrated.  Synchronises the stream to read the device status. */
+int sc_reintegrate_batch(sc_volume* vol, const sc_reint_item* items, int32_t n, const sc_intrinsics* intr,
+                         sc_stream stream);
+
+/* Set / read the launch configuration of sc_reintegrate_batch. */
+int sc_set_batch_config(sc_volume* vol, const sc_batch_config* cfg);
+int sc_get_batch_config(sc_volume* vol, sc_batch_config* cfg);
+
+/* Time each candidate configuration on this batch and keep the fastest.  The
+ * volume is snapshotted before and restored after every trial, so on return it
+ * is unchanged; the batch itself is NOT applied.  ms_out (host, may be NULL)
+ * receives the best time per batch.  Synchronises; needs device memory for one
+ * snapshot of the used pool. */
+int sc_autotune_batch(sc_volume* vol, const sc_reint_item* items, int32_t n, const sc_intrinsics* intr,
+                      sc_stream stream, sc_batch_config* best, float* ms_out);
+
+/* ------------------------------------------------------------ extraction ---- */
+
+/* Compact the occupied hash entries (Section 3: extraction of the allocated
+ * blocks precedes surface extraction) into block coordinates coords [cap][3] and
+ * pool slots slots [cap] (device, either may be NULL).  If D, W or C are given
+ * (device [cap][512] float, [cap][512] float, and [cap][512][4] uint8 for RGBA8 or
+ * [cap][512][3] float for RGB_F32, voxel index x + 8y + 64z), the voxel payloads
+ * are copied too.  Block order is unspecified.  *count (host) receives the number
+ * of blocks; SC_ERR_CAPACITY if it exceeds capacity (the first capacity blocks
+ * are written).  Synchronises. */
+int sc_extract_block_list(sc_volume* vol, int32_t* coords, int32_t* slots, float* D, float* W, void* C,
+                          int32_t capacity, int32_t* count, sc_stream stream);
+
+/* Copy the block list stored for kf_id (pool slots, device out [capacity]) and
+ * its length (*count, host).  Synchronises. */
+int sc_get_keyframe_blocks(sc_volume* vol, int32_t kf_id, int32_t* slots, int32_t capacity, int32_t* count,
+                           sc_stream stream);
+
+/* --------------------------------------------- loss and adjoint (extension) ---- */
+
+/* Loss on the fused SDF (no counterpart in the paper):
+ *   L = (1/P) sum_p Dt(p)^2 + lambda * sum_v W D^2 / sum_v W,
+ * Dt the trilinear interpolation of D over the 8 voxels around point p (voxel i
+ * at i * voxel_size); points whose 8 voxels are not all observed (W > 0) are
+ * dropped; P counts the rest.  Writes dL/dD for every voxel of the allocated
+ * pool slots [0, allocated_blocks) into grad_D (device [max_blocks][512] float;
+ * entries of unallocated slots are left untouched) and, into out (device, 5
+ * doubles), {L, P, sum_p Dt^2, sum_v W D^2, sum_v W}.  points device [n][3]
+ * float. */
+int sc_sdf_loss(sc_volume* vol, const float* points, int64_t n, float lambda, float* grad_D, double* out,
+                sc_stream stream);
+
+/* Adjoint of the keyframe integrations: given dL/dD (grad_D, from sc_sdf_loss),
+ * the gradient of L with respect to each keyframe's pose (left se(3)
+ * perturbation exp(xi^) T, xi = (rho, omega), at xi = 0) and depth pixels.
+ * Uses D(v) = sum_k w_k d_k(v) / W(v) and recomputes each voxel's projection:
+ * for each voxel of the keyframe's block list that its integration updated
+ * without clamping (eta < mu), g = dL/dD(v) w / W(v) contributes
+ *   dL/dZ_k(x) += g,   dL/drho += g r3,   dL/domega += g (p_v x r3),
+ * r3 = R e3 (camera z axis in world coordinates).  Discrete decisions (pixel,
+ * band, clamp) contribute nothing.
+ *   kf_ids, poses  host [n]; depths host [n] array of device [H][W] pointers
+ *   grad_xi        device [n][6] double, overwritten
+ *   grad_depth     device [n][H][W] float or NULL, overwritten */
+int sc_sdf_adjoint(sc_volume* vol, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
+                   int32_t n, const sc_intrinsics* intr, const float* grad_D, double* grad_xi, float* grad_depth,
+                   sc_stream stream);
+
+/* ------------------------------------------------ keyframe selection (host) ---- */
+
+/* ||s t - s t'|| (Section 4.3) with t = (Z-Y-X Euler angles of R in radians,
+ * translation), s = (2,2,2,1,1,1); angle differences wrapped to (-pi, pi]. */
+double sc_pose_distance(const sc_pose* a, const sc_pose* b);
+
+/* BundleFusion's rule (Section 4.3): the m keyframes with the largest distance,
+ * ties to the lower index.  dist host [K]; out host [min(m, K)]. */
+int sc_select_topm(const double* dist, int32_t K, int32_t m, int32_t* out);
+
+/* Eq. 3: first index j (0-based) of the m consecutive keyframes with the largest
+ * summed distance, ties to the smallest j.  Returns j, or a negative sc_status. */
+int sc_select_consecutive(const double* dist, int32_t K, int32_t m);
+
+/* exp(xi^) T: the pose T moved by the left se(3) perturbation xi = (rho, omega)
+ * (host, double precision, rounded to float once); the perturbation whose
+ * gradient sc_sdf_adjoint returns. */
+int sc_pose_exp_left(const sc_pose* T, const double* xi, sc_pose* out);
+
+/* ----------------------------------------------------------------- debug ---- */
+
+/* Per-kernel timing of the volume's own launches (CUDA events on the launching
+ * stream, event nodes inside the batch graph) and the work they covered. */
+typedef struct {
+    int32_t enabled;
+    int32_t pad;
+    double alloc_ms;            /* plain-path block allocation */
+    int64_t alloc_launches;
+    double update_ms;           /* plain-path voxel update (integrate and de-integrate) */
+    int64_t update_launches;
+    int64_t update_blocks;      /* sum of the updated block-list lengths */
+    double batch_alloc_ms;      /* batched allocation of the new poses' blocks */
+    double batch_mark_ms;       /* marking of the old footprints */
+    double batch_net_ms;        /* persistent net-delta voxel update */
+    int64_t batch_launches;
+    int64_t batch_union_blocks; /* sum over batches of the union of touched blocks */
+    int64_t batch_pairs;        /* sum over batches of old + new block-list lengths */
+} sc_profile;
+
+/* Enable (1) or disable (0) timing; either way the counters are reset. */
+int sc_set_profiling(sc_volume* vol, int32_t enabled);
+/* Read the counters (synchronises the volume's last stream). */
+int sc_get_profile(sc_volume* vol, sc_profile* out);
+
+
+/* Cap on every bounded device wait (slot publication, queue) in iterations; a
+ * cap of 1 forces the give-up path.  0 restores the default. */
+int sc_set_retry_limit(sc_volume* vol, int32_t limit);
+
+int sc_abi_version(void);
+
+/* Number of kernels this library has launched in the process so far (a graph
+ * launch counts its kernel nodes). */
+uint64_t sc_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SURFCORR_H */

@@ -97,6 +97,17 @@ def _u8(a):
     return None if a is None else np.ascontiguousarray(np.asarray(a), dtype=np.uint8)
 
 
+def f32(x) -> float:
+    """The float32 value of a parameter (the GPU library's parameters are float32;
+    the oracle computes in double from exactly those values)."""
+    return float(np.float32(x))
+
+
+def _intr(intr):
+    fx, fy, cx, cy = (f32(v) for v in tuple(intr)[:4])
+    return fx, fy, cx, cy
+
+
 def _np(t):
     """torch tensor or array -> numpy (host)."""
     if hasattr(t, "detach"):
@@ -126,8 +137,8 @@ def fuse(depths, poses, kf_pose, intr, disc_rel=0.1):
     Zs = np.zeros((H, W), np.float64)
     Ws = np.zeros((H, W), np.float64)
     fl = np.zeros((H, W), np.uint8)
-    fx, fy, cx, cy = intr[:4]
-    lib().or_fuse(_ptr(d), _ptr(p), n, _ptr(k), fx, fy, cx, cy, W, H, disc_rel, _ptr(Zs), _ptr(Ws), _ptr(fl))
+    fx, fy, cx, cy = _intr(intr)
+    lib().or_fuse(_ptr(d), _ptr(p), n, _ptr(k), fx, fy, cx, cy, W, H, f32(disc_rel), _ptr(Zs), _ptr(Ws), _ptr(fl))
     return Zs, Ws, fl
 
 
@@ -137,7 +148,8 @@ def allocation_set(depth, pose, intr, voxel_size, trunc):
     d = _f32(_np(depth))
     H, W = d.shape
     p = _f32(_np(pose)).reshape(12)
-    fx, fy, cx, cy = intr[:4]
+    fx, fy, cx, cy = _intr(intr)
+    voxel_size, trunc = f32(voxel_size), f32(trunc)
     n = lib().or_allocation_set(voxel_size, trunc, _ptr(d), fx, fy, cx, cy, W, H, _ptr(p), None, None)
     c = np.zeros((n, 3), np.int32)
     m = np.zeros(n, np.uint8)
@@ -160,6 +172,7 @@ class Volume:
     """Voxel-hashed TSDF in FP64.  rgba8=True stores colour as 8-bit integers."""
 
     def __init__(self, voxel_size, trunc, rgba8=False, _handle=None):
+        voxel_size, trunc = f32(voxel_size), f32(trunc)
         self.voxel_size = voxel_size
         self.trunc = trunc
         self.rgba8 = rgba8
@@ -178,7 +191,7 @@ class Volume:
         H, W = d.shape
         c = _u8(_np(rgba)) if rgba is not None else None
         p = _f32(_np(pose)).reshape(12)
-        fx, fy, cx, cy = intr[:4]
+        fx, fy, cx, cy = _intr(intr)
         rc = lib().or_integrate(self.h, kf_id, _ptr(d), _ptr(c), fx, fy, cx, cy, W, H, _ptr(p))
         if rc:
             raise ValueError(f"keyframe {kf_id} already integrated")
@@ -188,7 +201,7 @@ class Volume:
         H, W = d.shape
         c = _u8(_np(rgba)) if rgba is not None else None
         p = _f32(_np(pose)).reshape(12)
-        fx, fy, cx, cy = intr[:4]
+        fx, fy, cx, cy = _intr(intr)
         rc = lib().or_deintegrate(self.h, kf_id, _ptr(d), _ptr(c), fx, fy, cx, cy, W, H, _ptr(p))
         if rc:
             raise ValueError(f"keyframe {kf_id} not integrated")
@@ -200,7 +213,7 @@ class Volume:
         c = _u8(_np(rgbas)) if rgbas is not None else None
         op = _f32(_np(old_poses)).reshape(n, 12)
         np_ = _f32(_np(new_poses)).reshape(n, 12)
-        fx, fy, cx, cy = intr[:4]
+        fx, fy, cx, cy = _intr(intr)
         rc = lib().or_reintegrate_batch(self.h, n, _ptr(ids), _ptr(d), _ptr(c), _ptr(op), _ptr(np_),
                                         fx, fy, cx, cy, W, H)
         if rc:
@@ -247,7 +260,7 @@ class Volume:
         pts = np.ascontiguousarray(points, np.float64)
         gx = np.zeros((K, 6))
         gd = np.zeros((K, H, W)) if with_depth else None
-        fx, fy, cx, cy = intr[:4]
+        fx, fy, cx, cy = _intr(intr)
         rc = lib().or_grad(self.h, K, _ptr(ids), _ptr(d), None, _ptr(p), fx, fy, cx, cy, W, H,
                            _ptr(pts), len(pts), lam, _ptr(gx), _ptr(gd))
         if rc:
@@ -260,7 +273,7 @@ class Volume:
         p = _f32(_np(pose)).reshape(12)
         x = np.ascontiguousarray(xi, np.float64).reshape(6)
         pts = np.ascontiguousarray(points, np.float64)
-        fx, fy, cx, cy = intr[:4]
+        fx, fy, cx, cy = _intr(intr)
         return lib().or_loss_perturbed(self.h, kf_id, _ptr(d), _ptr(p), fx, fy, cx, cy, W, H, _ptr(x),
                                        int(pix), float(dz), _ptr(pts), len(pts), lam)
 

@@ -1,0 +1,236 @@
+// Block allocation (Section 3 "SDF volume": blocks are allocated before the
+// voxels are updated), shared by the per-keyframe path and the batched path.
+//
+// A(k, T): every 8^3 block whose closed box meets the band segment
+// {pi^-1(x, z) : z in [Z(x) - mu, Z(x) + mu]} of a valid pixel x, in world
+// coordinates.  Computed per 32x8 pixel tile by one CTA:
+//   A  enumerate each pixel's candidate blocks (slab test) into a shared-memory
+//      set, which removes the many duplicates neighbouring pixels produce;
+//   B  claim every unique key in the global hash table (64-bit CAS); the tile's
+//      new entries get consecutive pool slots from one atomic add;
+//   C  read each key's slot and let the Sink decide whether this call lists it
+//      (first time for this keyframe) and, for batches, whether it joins the
+//      batch's union of touched blocks; appends go through one atomic per CTA;
+//   D  only if the shared set overflowed: the overflowing keys one at a time.
+#pragma once
+
+#include "common.cuh"
+
+namespace sc {
+
+constexpr int ALLOC_TX = 32;
+constexpr int ALLOC_TY = 8;
+constexpr int ALLOC_THREADS = ALLOC_TX * ALLOC_TY;
+constexpr int SET_SIZE = 512;        // unique blocks a tile may touch before overflow handling
+constexpr int MAX_BLOCK_SPAN = 16;   // per-axis candidate blocks of one band segment
+constexpr float MAX_DEPTH = 1.0e4f;  // metres; larger depth values are treated as invalid
+
+// Blocks whose closed box meets pixel (u, v)'s band segment; calls f(bx, by, bz).
+// Geometry in voxel units relative to the camera's integer voxel position ti.
+template <typename F>
+__device__ inline void for_each_segment_block(const KfCam& k, int u, int v, float Z, F&& f) {
+    const float xn = __fdiv_rn(__fsub_rn((float)u, k.cx), k.fx);
+    const float yn = __fdiv_rn(__fsub_rn((float)v, k.cy), k.fy);
+    const float z0 = __fsub_rn(Z, k.mu), z1 = __fadd_rn(Z, k.mu);
+    const float c0[3] = {__fmul_rn(xn, z0), __fmul_rn(yn, z0), z0};
+    const float c1[3] = {__fmul_rn(xn, z1), __fmul_rn(yn, z1), z1};
+    float q0[3], q1[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        q0[r] = __fadd_rn(
+            __fmaf_rn(k.Ms[3 * r + 2], c0[2], __fmaf_rn(k.Ms[3 * r + 1], c0[1], __fmul_rn(k.Ms[3 * r], c0[0]))),
+            k.tf[r]);
+        q1[r] = __fadd_rn(
+            __fmaf_rn(k.Ms[3 * r + 2], c1[2], __fmaf_rn(k.Ms[3 * r + 1], c1[1], __fmul_rn(k.Ms[3 * r], c1[0]))),
+            k.tf[r]);
+    }
+    int blo[3], bhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // conservative candidate range; the slab test decides
+        const float lo = fminf(q0[a], q1[a]), hi = fmaxf(q0[a], q1[a]);
+        blo[a] = (((int)floorf(lo) + k.ti[a]) >> 3) - 1;
+        bhi[a] = ((int)floorf(hi) + k.ti[a]) >> 3;
+    }
+    // a band segment spans a handful of blocks; a larger range comes from a
+    // degenerate input and is skipped rather than looped over
+    if (bhi[0] - blo[0] > MAX_BLOCK_SPAN || bhi[1] - blo[1] > MAX_BLOCK_SPAN || bhi[2] - blo[2] > MAX_BLOCK_SPAN)
+        return;
+    for (int bz = blo[2]; bz <= bhi[2]; ++bz)
+        for (int by = blo[1]; by <= bhi[1]; ++by)
+            for (int bx = blo[0]; bx <= bhi[0]; ++bx) {
+                const float lo[3] = {(float)(8 * bx - k.ti[0]), (float)(8 * by - k.ti[1]),
+                                     (float)(8 * bz - k.ti[2])};
+                const float hi[3] = {lo[0] + 8.f, lo[1] + 8.f, lo[2] + 8.f};
+                if (seg_box(q0, q1, lo, hi)) f(bx, by, bz);
+            }
+}
+
+__device__ inline bool set_insert(unsigned long long* set, unsigned long long key) {
+    uint32_t h = hash_bucket(key, SET_SIZE - 1);
+    for (int i = 0; i < SET_SIZE; ++i) {
+        const unsigned long long old = atomicCAS(&set[h], KEY_EMPTY, key);
+        if (old == KEY_EMPTY || old == key) return true;
+        h = (h + 1) & (SET_SIZE - 1);
+    }
+    return false;
+}
+
+__device__ inline bool set_contains(const unsigned long long* set, unsigned long long key) {
+    uint32_t h = hash_bucket(key, SET_SIZE - 1);
+    for (int i = 0; i < SET_SIZE; ++i) {
+        const unsigned long long k = set[h];
+        if (k == key) return true;
+        if (k == KEY_EMPTY) return false;
+        h = (h + 1) & (SET_SIZE - 1);
+    }
+    return false;
+}
+
+// Publish a claimed entry: record its block coordinate, mark the slot fresh,
+// then make the slot visible to other threads.
+__device__ inline void publish(const DevVolume& V, int entry, unsigned long long key, uint32_t slot) {
+    if (slot >= V.max_blocks) {
+        set_status(V.status, SC_ERR_POOL_FULL);
+        atomicExch(&V.table[entry].slot, SLOT_FAILED);
+        return;
+    }
+    const int3 c = unpack_key(key);
+    V.coord[slot] = make_int4(c.x, c.y, c.z, 0);
+    V.flags[slot] = FLAG_FRESH;
+    __threadfence();
+    atomicExch(&V.table[entry].slot, (int32_t)slot);
+}
+
+struct AllocShared {
+    unsigned long long set[SET_SIZE];
+    int ent[SET_SIZE];
+    int idx[SET_SIZE];   // new entries (phase B), then list appends (phase C)
+    int uidx[SET_SIZE];  // union appends (batches)
+    int n_new, n_app, n_uapp, overflow;
+    uint32_t pool_base;
+    int app_base, uapp_base;
+};
+
+// Append one slot through a global counter (used by phase D).
+__device__ inline void append_one(const DevVolume& V, int32_t* list, int32_t* count, uint32_t cap, int32_t slot) {
+    const uint32_t p = (uint32_t)atomicAdd(count, 1);
+    if (p < cap) list[p] = slot;
+    else set_status(V.status, SC_ERR_LIST_FULL);
+}
+
+// Process tile (tx, ty) of keyframe camera k.  The Sink provides
+//   bool list_first(slot)  : true the first time this keyframe reaches slot
+//   bool union_first(slot) : true the first time the batch reaches slot (batches only)
+//   int32_t* list, *count; uint32_t cap; int32_t* ulist, *ucount; uint32_t ucap
+// Must be called by all ALLOC_THREADS threads of the CTA.
+template <typename Sink>
+__device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, int ty, Sink& sk, AllocShared& sh) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY_EMPTY;
+    if (tid == 0) {
+        sh.n_new = 0;
+        sh.n_app = 0;
+        sh.n_uapp = 0;
+        sh.overflow = 0;
+    }
+    __syncthreads();
+
+    const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
+    const int v = ty * ALLOC_TY + (tid / ALLOC_TX);
+    float Z = 0.f;
+    if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
+    const bool valid = Z > 0.f && Z < MAX_DEPTH;
+    bool my_ovf = false;
+    if (valid) {
+        for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
+            if (!coord_ok(bx, by, bz)) {
+                set_status(V.status, SC_ERR_INVALID_ARG);
+                return;
+            }
+            if (!set_insert(sh.set, pack_key(bx, by, bz))) my_ovf = true;
+        });
+    }
+    if (my_ovf) sh.overflow = 1;
+    __syncthreads();
+
+    // B: claim each unique key
+    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) {
+        sh.ent[i] = -1;
+        const unsigned long long key = sh.set[i];
+        if (key == KEY_EMPTY) continue;
+        bool won;
+        sh.ent[i] = hash_claim(V, key, &won);
+        if (sh.ent[i] >= 0 && won) sh.idx[atomicAdd(&sh.n_new, 1)] = i;
+    }
+    __syncthreads();
+    if (tid == 0 && sh.n_new > 0) sh.pool_base = atomicAdd(V.pool_count, (uint32_t)sh.n_new);
+    __syncthreads();
+    for (int i = tid; i < sh.n_new; i += ALLOC_THREADS) {
+        const int j = sh.idx[i];
+        publish(V, sh.ent[j], sh.set[j], sh.pool_base + (uint32_t)i);
+    }
+    __syncthreads();
+
+    // C: dedupe and append
+    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) {
+        if (sh.ent[i] < 0) continue;
+        const int32_t slot = entry_slot(V, sh.ent[i]);
+        if (slot < 0) continue;
+        if (sk.list_first(slot)) sh.idx[atomicAdd(&sh.n_app, 1)] = slot;
+        if (Sink::kUnion && sk.union_first(slot)) sh.uidx[atomicAdd(&sh.n_uapp, 1)] = slot;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (sh.n_app > 0) sh.app_base = atomicAdd(sk.count, sh.n_app);
+        if (Sink::kUnion && sh.n_uapp > 0) sh.uapp_base = atomicAdd(sk.ucount, sh.n_uapp);
+    }
+    __syncthreads();
+    for (int i = tid; i < sh.n_app; i += ALLOC_THREADS) {
+        const uint32_t p = (uint32_t)sh.app_base + (uint32_t)i;
+        if (p < sk.cap) sk.list[p] = sh.idx[i];
+        else set_status(V.status, SC_ERR_LIST_FULL);
+    }
+    if (Sink::kUnion) {
+        for (int i = tid; i < sh.n_uapp; i += ALLOC_THREADS) {
+            const uint32_t p = (uint32_t)sh.uapp_base + (uint32_t)i;
+            if (p < sk.ucap) sk.ulist[p] = sh.uidx[i];
+            else set_status(V.status, SC_ERR_POOL_FULL);
+        }
+    }
+
+    // D: keys that did not fit in the shared set
+    const bool ovf = sh.overflow != 0;
+    if (ovf && my_ovf) {
+        for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
+            if (!coord_ok(bx, by, bz)) return;
+            const unsigned long long key = pack_key(bx, by, bz);
+            if (set_contains(sh.set, key)) return;
+            bool won;
+            const int e = hash_claim(V, key, &won);
+            if (e < 0) return;
+            if (won) publish(V, e, key, atomicAdd(V.pool_count, 1u));
+            const int32_t slot = entry_slot(V, e);
+            if (slot < 0) return;
+            if (sk.list_first(slot)) append_one(V, sk.list, sk.count, sk.cap, slot);
+            if (Sink::kUnion && sk.union_first(slot)) append_one(V, sk.ulist, sk.ucount, sk.ucap, slot);
+        });
+    }
+    __syncthreads();  // shared state is reused by the CTA's next tile
+}
+
+struct PlainSink {
+    static constexpr bool kUnion = false;
+    uint32_t* stamp;
+    uint32_t call_id;
+    int32_t* list;
+    int32_t* count;
+    uint32_t cap;
+    int32_t* ulist;
+    int32_t* ucount;
+    uint32_t ucap;
+    __device__ bool list_first(int32_t slot) { return atomicExch(&stamp[slot], call_id) != call_id; }
+    __device__ bool union_first(int32_t) { return false; }
+};
+
+}  // namespace sc

@@ -1,0 +1,601 @@
+// Batched re-integration of one pose-graph update (Section 4.3 "Re-integration
+// strategy"): every item is de-integrated at its former pose and re-integrated
+// at its updated pose.
+//
+// Sequential semantics (de-integrate all items in order, then integrate all
+// items in order) give, per voxel, in exact arithmetic
+//   W' = W - sum_old w + sum_new w,   D' = (D W - sum_old d w + sum_new d w) / W'
+// (and D' = 0 when W' = 0; a voxel whose weight passes through 0 mid-sequence
+// has D W - sum_old d w = 0 there, so the reset of Eq. 2 changes nothing).  The
+// batch therefore computes each touched voxel's net change over all items and
+// applies it with ONE read-modify-write of its D / W / C, instead of 2n.
+//
+// Graph (captured once per launch configuration, replayed every call):
+//   1. H2D copy of the item table (pinned staging -> device; node resized per call)
+//   2. init: zero counters and the items' new block-list counts
+//   3. batched allocation of A(k, T_new) for all items (persistent over
+//      (item, pixel tile)); each item's new list is deduplicated with a per-slot
+//      item bit; every touched slot joins the batch's union list once
+//   4. mark old footprints: set (item, old) bits on every slot of each item's
+//      current list, union as above
+//   5. net-delta: persistent warps take union blocks from a queue, recompute each
+//      (voxel, item) sample for the items whose bits are set, sum, and apply once
+//   6. D2H copy of the status word
+// Per-slot item bitmasks: [max_blocks][mw] words, old bits then new bits; the
+// net-delta kernel clears a slot's words after applying it, so the masks are all
+// zero between calls.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "alloc.cuh"
+#include "volume.cuh"
+
+using namespace sc;
+
+namespace {
+
+struct BatchItem {
+    KfCam oldc;
+    KfCam newc;
+    int32_t* old_list;
+    int32_t* old_count;
+    int32_t* new_list;
+    int32_t* new_count;
+};
+
+struct BatchHeader {
+    int32_t n;
+    uint32_t call_id;
+    int32_t tiles_x;
+    int32_t tiles;
+};
+
+constexpr int ALLOC_CTAS_PER_SM = 4;
+
+struct BatchSink {
+    static constexpr bool kUnion = true;
+    uint32_t* masks;  // this item's new-bit word, slot stride mw
+    int mw;
+    uint32_t bit;
+    uint32_t* stamp;
+    uint32_t call_id;
+    int32_t* list;
+    int32_t* count;
+    uint32_t cap;
+    int32_t* ulist;
+    int32_t* ucount;
+    uint32_t ucap;
+    __device__ bool list_first(int32_t slot) {
+        return !(atomicOr(masks + (size_t)slot * mw, bit) & bit);
+    }
+    __device__ bool union_first(int32_t slot) { return atomicExch(&stamp[slot], call_id) != call_id; }
+};
+
+__global__ void batch_init_kernel(const BatchItem* items, const BatchHeader* hdr, int32_t* counters) {
+    const int n = hdr->n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) *items[i].new_count = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 4) counters[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(ALLOC_THREADS) batch_alloc_kernel(DevVolume V, const BatchItem* items,
+                                                                    const BatchHeader* hdr, uint32_t* masks, int mw,
+                                                                    int32_t* ulist, int32_t* counters,
+                                                                    uint32_t list_cap) {
+    __shared__ AllocShared sh;
+    const int n = hdr->n, tiles = hdr->tiles, tiles_x = hdr->tiles_x;
+    const uint32_t call_id = hdr->call_id;
+    const int half = mw / 2;
+    for (int w = blockIdx.x; w < n * tiles; w += gridDim.x) {
+        const int i = w / tiles, t = w - i * tiles;
+        const BatchItem& it = items[i];
+        BatchSink sk{masks + half + (i >> 5), mw, 1u << (i & 31), V.stamp, call_id, it.new_list, it.new_count,
+                     list_cap, ulist, counters, V.max_blocks};
+        alloc_tile(V, it.newc, t % tiles_x, t / tiles_x, sk, sh);
+    }
+}
+
+__global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const BatchHeader* hdr, uint32_t* masks,
+                                      int mw, int32_t* ulist, int32_t* counters, uint32_t list_cap) {
+    const int n = hdr->n;
+    const uint32_t call_id = hdr->call_id;
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t cnt = min((uint32_t)*items[i].old_count, list_cap);
+        const int32_t* list = items[i].old_list;
+        const uint32_t bit = 1u << (i & 31);
+        // warp-uniform trip count so the ballot below sees the full warp
+        for (uint32_t base = blockIdx.x * blockDim.x; base < cnt; base += stride) {
+            const uint32_t j = base + threadIdx.x;
+            bool first = false;
+            int32_t slot = -1;
+            if (j < cnt) {
+                slot = list[j];
+                atomicOr(masks + (size_t)slot * mw + (i >> 5), bit);
+                first = atomicExch(&V.stamp[slot], call_id) != call_id;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, first);
+            if (!m) continue;
+            int b = 0;
+            if (lane == 0) b = atomicAdd(counters, __popc(m));
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (first) {
+                const uint32_t p = (uint32_t)b + __popc(m & ((1u << lane) - 1u));
+                if (p < V.max_blocks) ulist[p] = slot;
+                else set_status(V.status, SC_ERR_POOL_FULL);
+            }
+        }
+    }
+}
+
+// Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over every item whose
+// bit is set in the slot's mask (old bits subtract, new bits add), in item order.
+template <bool F32>
+__device__ __forceinline__ void net_delta_group(const BatchItem* items, const int4 c, int lx0, int ly, int lz,
+                                                uint32_t mw0, uint32_t mw1, int mw, float aD[4], float aW[4],
+                                                float aC[4][3], bool& touched) {
+    const int half = mw / 2;
+    for (int w = 0; w < mw; ++w) {
+        uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
+        const float sgn = w < half ? -1.f : 1.f;
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            const int item = ((w < half ? w : w - half) << 5) + b;
+            const KfCam& k = w < half ? items[item].oldc : items[item].newc;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float d;
+                int pix;
+                if (sample_voxel(k, 8 * c.x + lx0 + j, 8 * c.y + ly, 8 * c.z + lz, d, pix)) {
+                    touched = true;
+                    aD[j] = __fmaf_rn(sgn, d, aD[j]);
+                    aW[j] = __fadd_rn(aW[j], sgn);
+                    const uint32_t cc = __ldg(k.rgba + pix);
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) aC[j][ch] = __fmaf_rn(sgn, (float)((cc >> (8 * ch)) & 255u), aC[j][ch]);
+                }
+            }
+        }
+    }
+}
+
+template <bool F32>
+__global__ void net_delta_kernel(DevVolume V, const BatchItem* items, const BatchHeader* hdr, uint32_t* masks,
+                                 int mw, const int32_t* ulist, int32_t* counters, int grab, uint32_t list_cap) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t n_union = min((uint32_t)counters[0], V.max_blocks);
+    if (V.prof && blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long pairs = 0;
+        for (int i = 0; i < hdr->n; ++i)
+            pairs += min((uint32_t)*items[i].old_count, list_cap) + min((uint32_t)*items[i].new_count, list_cap);
+        atomicAdd(V.prof + 1, (unsigned long long)n_union);
+        atomicAdd(V.prof + 2, pairs);
+    }
+    while (true) {
+        uint32_t base = 0;
+        if (lane == 0) base = (uint32_t)atomicAdd(&counters[1], grab);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n_union) break;
+        const uint32_t end = min(base + (uint32_t)grab, n_union);
+        for (uint32_t u = base; u < end; ++u) {
+            const int32_t slot = ulist[u];
+            const int4 c = V.coord[slot];
+            const bool fresh = (V.flags[slot] & FLAG_FRESH) != 0;
+            uint32_t* mp = masks + (size_t)slot * mw;
+            const uint32_t mw0 = lane < mw ? mp[lane] : 0u;
+            const uint32_t mw1 = lane + 32 < mw ? mp[lane + 32] : 0u;
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+                int lx0, ly, lz;
+                lane_voxels(lane, g, lx0, ly, lz);
+                float aD[4] = {0.f, 0.f, 0.f, 0.f}, aW[4] = {0.f, 0.f, 0.f, 0.f};
+                float aC[4][3] = {};
+                bool touched = false;
+                net_delta_group<F32>(items, c, lx0, ly, lz, mw0, mw1, mw, aD, aW, aC, touched);
+                if (!touched && !fresh) continue;
+                const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+                float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
+                if (!fresh) {
+                    Dv = *reinterpret_cast<const float4*>(V.D + off);
+                    Wv = *reinterpret_cast<const float4*>(V.W + off);
+                }
+                float* Dp = &Dv.x;
+                float* Wp = &Wv.x;
+                float Wn[4], inv_ok[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    Wn[j] = __fadd_rn(Wp[j], aW[j]);
+                    inv_ok[j] = Wn[j] != 0.f;
+                }
+                if (F32) {
+                    const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
+#pragma unroll
+                    for (int ch = 0; ch < 3; ++ch) {
+                        float4 Cv = fresh ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                          : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
+                        float* Cp = &Cv.x;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (aW[j] != 0.f || aC[j][ch] != 0.f)
+                                Cp[j] = inv_ok[j] ? __fdiv_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), Wn[j]) : 0.f;
+                        *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cv;
+                    }
+                } else {
+                    uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
+                    if (!fresh) Cv = *reinterpret_cast<const uint4*>(V.C8 + off);
+                    uint32_t* Cp = &Cv.x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (aW[j] == 0.f && aC[j][0] == 0.f && aC[j][1] == 0.f && aC[j][2] == 0.f) continue;
+                        if (!inv_ok[j]) {
+                            Cp[j] = 0u;
+                            continue;
+                        }
+                        uint32_t out = 0;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
+                            out |= u8_sat(__fdiv_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), Wn[j])) << (8 * ch);
+                        }
+                        Cp[j] = out;
+                    }
+                    *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (aW[j] == 0.f && aD[j] == 0.f) continue;
+                    Dp[j] = inv_ok[j] ? __fdiv_rn(__fmaf_rn(Dp[j], Wp[j], aD[j]), Wn[j]) : 0.f;
+                    Wp[j] = Wn[j];
+                }
+                *reinterpret_cast<float4*>(V.D + off) = Dv;
+                *reinterpret_cast<float4*>(V.W + off) = Wv;
+            }
+            __syncwarp();
+            if (lane < mw) mp[lane] = 0u;
+            if (lane + 32 < mw) mp[lane + 32] = 0u;
+            if (fresh && lane == 0) V.flags[slot] = 0u;
+        }
+    }
+}
+
+}  // namespace
+
+struct BatchState {
+    int mw = 0;
+    uint32_t* masks = nullptr;
+    int32_t* ulist = nullptr;
+    int32_t* counters = nullptr;
+    BatchItem* items_d = nullptr;
+    BatchHeader* hdr_d = nullptr;
+    BatchItem* items_h = nullptr;  // pinned
+    BatchHeader* hdr_h = nullptr;  // pinned
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t items_node = nullptr;
+    sc_batch_config graph_cfg{};
+    DevVolume graph_dv{};
+    int graph_f32 = 0;
+};
+
+void batch_destroy(sc_volume* V) {
+    BatchState* B = V->batch;
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+    if (B->masks) cudaFree(B->masks);
+    if (B->ulist) cudaFree(B->ulist);
+    if (B->counters) cudaFree(B->counters);
+    if (B->items_d) cudaFree(B->items_d);
+    if (B->hdr_d) cudaFree(B->hdr_d);
+    if (B->items_h) cudaFreeHost(B->items_h);
+    if (B->hdr_h) cudaFreeHost(B->hdr_h);
+    delete B;
+    V->batch = nullptr;
+}
+
+namespace {
+
+int batch_init(sc_volume* V) {
+    if (V->batch) return SC_OK;
+    BatchState* B = new BatchState();
+    V->batch = B;
+    B->mw = 2 * ((V->p.max_batch + 31) / 32);
+    const size_t mbytes = (size_t)V->p.max_blocks * B->mw * sizeof(uint32_t);
+    SC_CUDA(cudaMalloc((void**)&B->masks, mbytes));
+    SC_CUDA(cudaMemset(B->masks, 0, mbytes));
+    SC_CUDA(cudaMalloc((void**)&B->ulist, (size_t)V->p.max_blocks * sizeof(int32_t)));
+    SC_CUDA(cudaMalloc((void**)&B->counters, 4 * sizeof(int32_t)));
+    SC_CUDA(cudaMalloc((void**)&B->items_d, (size_t)V->p.max_batch * sizeof(BatchItem)));
+    SC_CUDA(cudaMalloc((void**)&B->hdr_d, sizeof(BatchHeader)));
+    SC_CUDA(cudaMallocHost((void**)&B->items_h, (size_t)V->p.max_batch * sizeof(BatchItem)));
+    SC_CUDA(cudaMallocHost((void**)&B->hdr_h, sizeof(BatchHeader)));
+    SC_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+    V->device_bytes += mbytes + (size_t)V->p.max_blocks * 4 + (size_t)V->p.max_batch * sizeof(BatchItem);
+    return SC_OK;
+}
+
+int ctas_per_sm_clamped(sc_volume* V, const sc_batch_config& c) {
+    int occ = 0;
+    const int threads = 32 * c.warps_per_cta;
+    cudaError_t e = V->p.colour_format == SC_RGB_F32
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_delta_kernel<true>, threads, 0)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_delta_kernel<false>, threads, 0);
+    if (e != cudaSuccess || occ < 1) occ = 1;
+    return std::max(1, std::min(c.ctas_per_sm, occ));
+}
+
+// Enqueue steps 2-6 (and the item copy) on stream s; used for capture.
+cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_node) {
+    BatchState* B = V->batch;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(B->hdr_d, B->hdr_h, sizeof(BatchHeader), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    if ((e = cudaMemcpyAsync(B->items_d, B->items_h, sizeof(BatchItem), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    if (items_node) {
+        cudaStreamCaptureStatus st;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        if ((e = cudaStreamGetCaptureInfo(s, &st, nullptr, nullptr, &deps, nullptr, &ndeps)) != cudaSuccess)
+            return e;
+        if (ndeps != 1) return cudaErrorUnknown;
+        *items_node = deps[0];
+    }
+    batch_init_kernel<<<4, 256, 0, s>>>(B->items_d, B->hdr_d, B->counters);
+    if (V->prof_on) cudaEventRecord(V->graph_ev[0], s);
+    batch_alloc_kernel<<<V->num_sms * ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
+        V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
+    if (V->prof_on) cudaEventRecord(V->graph_ev[1], s);
+    batch_mark_old_kernel<<<V->num_sms * 8, 256, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist,
+                                                         B->counters, V->p.max_blocks_per_keyframe);
+    if (V->prof_on) cudaEventRecord(V->graph_ev[2], s);
+    const sc_batch_config& c = V->bcfg;
+    const int grid = V->num_sms * ctas_per_sm_clamped(V, c);
+    const uint32_t cap = V->p.max_blocks_per_keyframe;
+    if (V->p.colour_format == SC_RGB_F32)
+        net_delta_kernel<true><<<grid, 32 * c.warps_per_cta, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw,
+                                                                    B->ulist, B->counters, c.blocks_per_grab, cap);
+    else
+        net_delta_kernel<false><<<grid, 32 * c.warps_per_cta, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw,
+                                                                     B->ulist, B->counters, c.blocks_per_grab, cap);
+    if (V->prof_on) cudaEventRecord(V->graph_ev[3], s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemcpyAsync(V->h_status, V->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+}
+
+int ensure_graph(sc_volume* V) {
+    BatchState* B = V->batch;
+    const bool same = B->exec && !memcmp(&B->graph_cfg, &V->bcfg, sizeof(sc_batch_config)) &&
+                      !memcmp(&B->graph_dv, &V->dv, sizeof(DevVolume));
+    if (same) return SC_OK;
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    if (B->graph) {
+        cudaGraphDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    SC_CUDA(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_batch(V, B->cap_stream, &B->items_node);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(B->cap_stream, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_status(e);
+    }
+    SC_CUDA(e2);
+    B->graph = g;
+    SC_CUDA(cudaGraphInstantiate(&B->exec, g, 0));
+    B->graph_cfg = V->bcfg;
+    B->graph_dv = V->dv;
+    return SC_OK;
+}
+
+int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_intrinsics* K) {
+    if (!V || !items || n < 1 || n > V->p.max_batch || !intrinsics_ok(K)) return SC_ERR_INVALID_ARG;
+    std::vector<uint8_t> seen(V->p.max_keyframes, 0);
+    for (int i = 0; i < n; ++i) {
+        const sc_reint_item& it = items[i];
+        if (it.kf_id < 0 || it.kf_id >= V->p.max_keyframes || seen[it.kf_id]) return SC_ERR_INVALID_ARG;
+        if (!it.depth || !it.rgba || ((uintptr_t)it.depth & 15) || ((uintptr_t)it.rgba & 15))
+            return SC_ERR_INVALID_ARG;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 4; ++c)
+                if (!std::isfinite(it.old_pose.m[r][c]) || !std::isfinite(it.new_pose.m[r][c]))
+                    return SC_ERR_INVALID_ARG;
+        seen[it.kf_id] = 1;
+        if (!V->integrated[it.kf_id]) return SC_ERR_NOT_INTEGRATED;
+    }
+    int rc = batch_init(V);
+    if (rc) return rc;
+    BatchState* B = V->batch;
+    for (int i = 0; i < n; ++i) {
+        const sc_reint_item& it = items[i];
+        BatchItem& b = B->items_h[i];
+        const int cur = V->cur[it.kf_id];
+        b.oldc = make_cam(V, K, &it.old_pose, it.depth, it.rgba);
+        b.newc = make_cam(V, K, &it.new_pose, it.depth, it.rgba);
+        b.old_list = list_ptr(V, it.kf_id, cur);
+        b.old_count = count_ptr(V, it.kf_id, cur);
+        b.new_list = list_ptr(V, it.kf_id, 1 - cur);
+        b.new_count = count_ptr(V, it.kf_id, 1 - cur);
+    }
+    if (++V->call_id == 0) V->call_id = 1;  // (plain calls reset stamps on wrap)
+    B->hdr_h->n = n;
+    B->hdr_h->call_id = V->call_id;
+    B->hdr_h->tiles_x = (K->width + ALLOC_TX - 1) / ALLOC_TX;
+    B->hdr_h->tiles = B->hdr_h->tiles_x * ((K->height + ALLOC_TY - 1) / ALLOC_TY);
+    rc = ensure_graph(V);
+    if (rc) return rc;
+    // resize the item-table copy to the n items of this call
+    SC_CUDA(cudaGraphExecMemcpyNodeSetParams1D(B->exec, B->items_node, B->items_d, B->items_h,
+                                               (size_t)n * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    return SC_OK;
+}
+
+constexpr int GRAPH_KERNELS = 4;  // init, batched allocation, mark old, net-delta
+
+int launch_and_check(sc_volume* V, cudaStream_t s) {
+    SC_CUDA(cudaGraphLaunch(V->batch->exec, s));
+    count_launches(GRAPH_KERNELS);
+    SC_CUDA(cudaStreamSynchronize(s));
+    V->last_stream = s;
+    if (V->prof_on) {
+        float a = 0.f, b = 0.f, c = 0.f;
+        if (cudaEventElapsedTime(&a, V->graph_ev[0], V->graph_ev[1]) == cudaSuccess &&
+            cudaEventElapsedTime(&b, V->graph_ev[1], V->graph_ev[2]) == cudaSuccess &&
+            cudaEventElapsedTime(&c, V->graph_ev[2], V->graph_ev[3]) == cudaSuccess) {
+            V->prof_ms[2] += a;
+            V->prof_ms[3] += b;
+            V->prof_ms[4] += c;
+            V->prof_n[2] += 1;
+        }
+        (void)cudaGetLastError();
+    }
+    return *V->h_status;
+}
+
+}  // namespace
+
+extern "C" int sc_reintegrate_batch(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_intrinsics* K,
+                                    sc_stream stream) {
+    int rc = prepare_items(V, items, n, K);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = launch_and_check(V, s);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) V->cur[items[i].kf_id] ^= 1;
+    return SC_OK;
+}
+
+extern "C" int sc_set_batch_config(sc_volume* V, const sc_batch_config* c) {
+    if (!V || !c) return SC_ERR_INVALID_ARG;
+    if (!(c->warps_per_cta == 2 || c->warps_per_cta == 4 || c->warps_per_cta == 8 || c->warps_per_cta == 16) ||
+        c->ctas_per_sm < 1 || c->ctas_per_sm > 16 || c->blocks_per_grab < 1 || c->blocks_per_grab > 16)
+        return SC_ERR_INVALID_ARG;
+    V->bcfg = *c;
+    return SC_OK;
+}
+
+extern "C" int sc_get_batch_config(sc_volume* V, sc_batch_config* c) {
+    if (!V || !c) return SC_ERR_INVALID_ARG;
+    *c = V->bcfg;
+    return SC_OK;
+}
+
+// ------------------------------------------------------------------ autotune ----
+
+namespace {
+
+struct Snapshot {
+    uint32_t used = 0;
+    size_t col_bytes = 0;
+    void* buf = nullptr;
+    size_t bytes = 0;
+};
+
+int snapshot_take(sc_volume* V, Snapshot& S, cudaStream_t s) {
+    SC_CUDA(cudaMemcpyAsync(V->h_word, V->pool_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    S.used = std::min(V->h_word[0], V->p.max_blocks);
+    const size_t nb = S.used;
+    S.col_bytes = nb * NVOX * (V->p.colour_format == SC_RGB_F32 ? 3 * sizeof(float) : sizeof(uint32_t));
+    const size_t tbytes = (size_t)V->p.n_buckets * V->p.bucket_size * sizeof(HashEntry);
+    S.bytes = 2 * nb * NVOX * sizeof(float) + S.col_bytes + nb * sizeof(uint32_t) + tbytes + 256;
+    SC_CUDA(cudaMalloc(&S.buf, S.bytes));
+    char* p = (char*)S.buf;
+    SC_CUDA(cudaMemcpyAsync(p, V->D, nb * NVOX * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    p += nb * NVOX * sizeof(float);
+    SC_CUDA(cudaMemcpyAsync(p, V->W, nb * NVOX * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    p += nb * NVOX * sizeof(float);
+    SC_CUDA(cudaMemcpyAsync(p, V->Cf ? (void*)V->Cf : (void*)V->C8, S.col_bytes, cudaMemcpyDeviceToDevice, s));
+    p += S.col_bytes;
+    SC_CUDA(cudaMemcpyAsync(p, V->flags, nb * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    p += nb * sizeof(uint32_t);
+    SC_CUDA(cudaMemcpyAsync(p, V->table, tbytes, cudaMemcpyDeviceToDevice, s));
+    return SC_OK;
+}
+
+int snapshot_restore(sc_volume* V, const Snapshot& S, cudaStream_t s) {
+    const size_t nb = S.used;
+    const size_t tbytes = (size_t)V->p.n_buckets * V->p.bucket_size * sizeof(HashEntry);
+    const char* p = (const char*)S.buf;
+    SC_CUDA(cudaMemcpyAsync(V->D, p, nb * NVOX * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    p += nb * NVOX * sizeof(float);
+    SC_CUDA(cudaMemcpyAsync(V->W, p, nb * NVOX * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    p += nb * NVOX * sizeof(float);
+    SC_CUDA(cudaMemcpyAsync(V->Cf ? (void*)V->Cf : (void*)V->C8, p, S.col_bytes, cudaMemcpyDeviceToDevice, s));
+    p += S.col_bytes;
+    SC_CUDA(cudaMemcpyAsync(V->flags, p, nb * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+    p += nb * sizeof(uint32_t);
+    SC_CUDA(cudaMemcpyAsync(V->table, p, tbytes, cudaMemcpyDeviceToDevice, s));
+    SC_CUDA(cudaMemcpyAsync(V->pool_count, &S.used, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaMemsetAsync(V->status, 0, sizeof(int32_t), s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    return SC_OK;
+}
+
+}  // namespace
+
+extern "C" int sc_autotune_batch(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_intrinsics* K,
+                                 sc_stream stream, sc_batch_config* best, float* ms_out) {
+    if (!V || !best) return SC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Snapshot S;
+    int rc = snapshot_take(V, S, s);
+    if (rc) {
+        if (S.buf) cudaFree(S.buf);
+        return rc;
+    }
+    const sc_batch_config orig = V->bcfg;
+    std::vector<sc_batch_config> cands;
+    for (int w : {4, 8})
+        for (int c : {2, 4, 8})
+            for (int g : {1, 4}) cands.push_back(sc_batch_config{w, c, g});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    sc_batch_config best_cfg = orig;
+    for (const sc_batch_config& c : cands) {
+        V->bcfg = c;
+        std::vector<float> ts;
+        for (int rep = 0; rep < 4 && rc == SC_OK; ++rep) {
+            rc = prepare_items(V, items, n, K);
+            if (rc) break;
+            cudaEventRecord(e0, s);
+            rc = cuda_status(cudaGraphLaunch(V->batch->exec, s));
+            count_launches(GRAPH_KERNELS);
+            cudaEventRecord(e1, s);
+            if (rc == SC_OK) rc = cuda_status(cudaStreamSynchronize(s));
+            if (rc == SC_OK) rc = *V->h_status;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ts.push_back(ms);  // first run warms up the graph
+            const int rr = snapshot_restore(V, S, s);
+            if (rc == SC_OK) rc = rr;
+        }
+        if (rc) break;
+        std::sort(ts.begin(), ts.end());
+        const float med = ts[ts.size() / 2];
+        if (med < best_ms) {
+            best_ms = med;
+            best_cfg = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(S.buf);
+    V->bcfg = rc ? orig : best_cfg;
+    V->last_stream = s;
+    if (rc) return rc;
+    *best = best_cfg;
+    if (ms_out) *ms_out = best_ms;
+    return SC_OK;
+}

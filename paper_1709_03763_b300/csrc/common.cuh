@@ -1,0 +1,274 @@
+// Device-side building blocks shared by the surfcorr kernels: volume layout,
+// spatial hash, the per-voxel projective sample and the running-average update.
+//
+// Layout in HBM (all arrays indexed by pool slot, one slot per 8^3 block):
+//   D      float [max_blocks][512]      signed distance, metres
+//   W      float [max_blocks][512]      integration weight (integer-valued)
+//   C8     uint32 [max_blocks][512]     colour RGBA8 (r | g<<8 | b<<16), or
+//   Cf     float [max_blocks][3][512]   colour RGB_F32 (parity mode)
+//   coord  int4 [max_blocks]            block coordinate of each slot
+//   flags  uint32 [max_blocks]          bit 0: fresh (zero-initialise on first update)
+// Voxel index inside a block: x + 8 y + 64 z, so a warp's 32 lanes x float4
+// cover 128 consecutive voxels (four 512-byte coalesced transactions per block
+// and field).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "surfcorr.h"
+
+namespace sc {
+
+constexpr int BLK = 8;
+constexpr int NVOX = 512;
+constexpr unsigned long long KEY_EMPTY = ~0ull;
+constexpr int32_t SLOT_PENDING = -1;
+constexpr int32_t SLOT_FAILED = -2;
+constexpr uint32_t FLAG_FRESH = 1u;
+constexpr int COORD_BIAS = 1 << 20;  // block coordinates in [-2^20, 2^20 - 1]
+constexpr int DEFAULT_RETRY = 1 << 20;
+
+struct __align__(16) HashEntry {
+    unsigned long long key;
+    int32_t slot;
+    uint32_t pad;
+};
+
+__host__ __device__ inline unsigned long long pack_key(int x, int y, int z) {
+    return (unsigned long long)(uint32_t)(x + COORD_BIAS) |
+           ((unsigned long long)(uint32_t)(y + COORD_BIAS) << 21) |
+           ((unsigned long long)(uint32_t)(z + COORD_BIAS) << 42);
+}
+
+__host__ __device__ inline bool coord_ok(int x, int y, int z) {
+    return x >= -COORD_BIAS && x < COORD_BIAS && y >= -COORD_BIAS && y < COORD_BIAS && z >= -COORD_BIAS &&
+           z < COORD_BIAS;
+}
+
+__device__ inline int3 unpack_key(unsigned long long k) {
+    const unsigned long long M = (1ull << 21) - 1;
+    return make_int3((int)(k & M) - COORD_BIAS, (int)((k >> 21) & M) - COORD_BIAS,
+                     (int)((k >> 42) & M) - COORD_BIAS);
+}
+
+// 64-bit finaliser (xor-shift-multiply) -> bucket index.
+__host__ __device__ inline uint32_t hash_bucket(unsigned long long k, uint32_t mask) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ull;
+    k ^= k >> 33;
+    return (uint32_t)k & mask;
+}
+
+// Everything a kernel needs to address the volume, passed by value.
+struct DevVolume {
+    HashEntry* table;
+    uint32_t bucket_mask;
+    uint32_t bucket_size;
+    uint32_t max_probe;
+    uint32_t max_blocks;
+    float* D;
+    float* W;
+    uint32_t* C8;
+    float* Cf;
+    int4* coord;
+    uint32_t* flags;
+    uint32_t* stamp;
+    uint32_t* pool_count;
+    int32_t* status;
+    int32_t retry_limit;
+    int32_t colour_f32;
+    unsigned long long* prof;  // device work counters when profiling, else null
+};
+
+__device__ inline void set_status(int32_t* status, int32_t code) { atomicCAS(status, 0, code); }
+
+// Per keyframe-operation camera constants, built on the host from the float
+// pose in double precision and rounded once:
+//   q = (i - ti) - tf   voxel index relative to the camera position (voxel units)
+//   p_c = M q           camera coordinates (metres), M = voxel_size * R^T
+//   segment endpoint in relative voxel units: Ms * pi^-1(x, z) + tf, Ms = R / voxel_size
+struct KfCam {
+    float M[9];
+    float Ms[9];
+    float tf[3];
+    int ti[3];
+    float fx, fy, cx, cy;
+    int W, H;
+    float mu;
+    const float* depth;
+    const uint32_t* rgba;  // RGBA8 as one 32-bit word per pixel
+};
+
+// Projective sample of voxel (ix, iy, iz) in the keyframe: returns true when the
+// voxel is updated, with d = min(eta, mu) and the sampled pixel.  Every
+// operation is an explicit round-to-nearest intrinsic so that integration,
+// de-integration, the batched net-delta kernel and the adjoint reach bit-identical
+// decisions and distances for the same keyframe and pose.
+__device__ __forceinline__ bool sample_voxel(const KfCam& k, int ix, int iy, int iz, float& d, int& pix,
+                                             float* eta_out = nullptr) {
+    const float qx = __fsub_rn((float)(ix - k.ti[0]), k.tf[0]);
+    const float qy = __fsub_rn((float)(iy - k.ti[1]), k.tf[1]);
+    const float qz = __fsub_rn((float)(iz - k.ti[2]), k.tf[2]);
+    const float pz = __fmaf_rn(k.M[8], qz, __fmaf_rn(k.M[7], qy, __fmul_rn(k.M[6], qx)));
+    if (!(pz > 0.f)) return false;
+    const float px = __fmaf_rn(k.M[2], qz, __fmaf_rn(k.M[1], qy, __fmul_rn(k.M[0], qx)));
+    const float py = __fmaf_rn(k.M[5], qz, __fmaf_rn(k.M[4], qy, __fmul_rn(k.M[3], qx)));
+    const float rz = __frcp_rn(pz);
+    // nearest pixel, halves rounded up: floor(u + 1/2); NaN / inf fail the range test
+    const float uu = __fadd_rn(__fmaf_rn(__fmul_rn(k.fx, px), rz, k.cx), 0.5f);
+    const float vv = __fadd_rn(__fmaf_rn(__fmul_rn(k.fy, py), rz, k.cy), 0.5f);
+    if (!(uu >= 0.f && uu < (float)k.W && vv >= 0.f && vv < (float)k.H)) return false;
+    pix = (int)vv * k.W + (int)uu;
+    const float Z = __ldg(k.depth + pix);
+    if (!(Z > 0.f)) return false;
+    const float eta = __fsub_rn(Z, pz);
+    if (eta < -k.mu) return false;
+    d = fminf(eta, k.mu);
+    if (eta_out) *eta_out = eta;
+    return true;
+}
+
+__device__ __forceinline__ uint32_t u8_sat(float x) {
+    // round half to even, saturate to [0, 255]
+    return (uint32_t)fminf(fmaxf(rintf(x), 0.f), 255.f);
+}
+
+// Running weighted average with w = 1 (sign +1) or its inverse, Eq. 2 (sign -1).
+// W reaching 0 resets D to 0.
+__device__ __forceinline__ void update_dw(float& D, float& W, float d, int sign) {
+    if (sign > 0) {
+        const float Wn = __fadd_rn(W, 1.f);
+        D = __fdiv_rn(__fmaf_rn(D, W, d), Wn);
+        W = Wn;
+    } else {
+        const float Wn = __fsub_rn(W, 1.f);
+        D = (Wn == 0.f) ? 0.f : __fdiv_rn(__fmaf_rn(D, W, -d), Wn);
+        W = Wn;
+    }
+}
+
+// Colour channel in float (RGB_F32 mode): same rule as D.  W is the weight
+// before the update.
+__device__ __forceinline__ float update_cf(float C, float W, float c, int sign) {
+    if (sign > 0) return __fdiv_rn(__fmaf_rn(C, W, c), __fadd_rn(W, 1.f));
+    const float Wn = __fsub_rn(W, 1.f);
+    return (Wn == 0.f) ? 0.f : __fdiv_rn(__fmaf_rn(C, W, -c), Wn);
+}
+
+// RGBA8 word: each channel averaged in float then rounded half-to-even.
+__device__ __forceinline__ uint32_t update_c8(uint32_t C, float W, uint32_t c, int sign) {
+    const float Wn = sign > 0 ? __fadd_rn(W, 1.f) : __fsub_rn(W, 1.f);
+    if (Wn == 0.f) return 0u;
+    uint32_t out = 0;
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+        const float a = (float)((C >> (8 * ch)) & 255u);
+        const float b = (float)((c >> (8 * ch)) & 255u);
+        const float v = __fdiv_rn(__fmaf_rn(a, W, sign > 0 ? b : -b), Wn);
+        out |= u8_sat(v) << (8 * ch);
+    }
+    return out;
+}
+
+// Voxel coordinates of the 4 consecutive voxels lane `lane` owns in group g
+// (0..3) of a block: linear index v0 = 4 lane + 128 g.
+__device__ __forceinline__ void lane_voxels(int lane, int g, int& lx0, int& ly, int& lz) {
+    const int v0 = 4 * lane + 128 * g;
+    lx0 = v0 & 7;
+    ly = (v0 >> 3) & 7;
+    lz = v0 >> 6;
+}
+
+// ---------------------------------------------------------------- hashing ----
+
+// Lock-free insert-or-find of `key`.  Bucketed open addressing: the key's home
+// bucket, then the following buckets (wrapping) up to max_probe buckets.  An
+// empty entry is claimed with a 64-bit CAS on its key; the slot is published
+// later (SLOT_PENDING until then).  Returns the entry index, or -1 with the
+// status set (SC_ERR_HASH_FULL).  *won is set when this call created the entry.
+__device__ inline int hash_claim(const DevVolume& V, unsigned long long key, bool* won) {
+    const uint32_t b = hash_bucket(key, V.bucket_mask);
+    *won = false;
+    for (uint32_t probe = 0; probe < V.max_probe; ++probe) {
+        const uint32_t base = ((b + probe) & V.bucket_mask) * V.bucket_size;
+        for (uint32_t e = 0; e < V.bucket_size; ++e) {
+            unsigned long long* kp = &V.table[base + e].key;
+            unsigned long long k = *((volatile unsigned long long*)kp);
+            if (k == KEY_EMPTY) {
+                k = atomicCAS(kp, KEY_EMPTY, key);
+                if (k == KEY_EMPTY) {
+                    *won = true;
+                    return (int)(base + e);
+                }
+            }
+            if (k == key) return (int)(base + e);
+        }
+    }
+    set_status(V.status, SC_ERR_HASH_FULL);
+    return -1;
+}
+
+// Find without inserting: entry index or -1.
+__device__ inline int hash_find(const DevVolume& V, unsigned long long key) {
+    const uint32_t b = hash_bucket(key, V.bucket_mask);
+    for (uint32_t probe = 0; probe < V.max_probe; ++probe) {
+        const uint32_t base = ((b + probe) & V.bucket_mask) * V.bucket_size;
+        for (uint32_t e = 0; e < V.bucket_size; ++e) {
+            const unsigned long long k = V.table[base + e].key;
+            if (k == key) return (int)(base + e);
+            if (k == KEY_EMPTY) return -1;
+        }
+    }
+    return -1;
+}
+
+// Slot of a claimed entry, waiting (bounded) for its publication by the CTA that
+// created it.  Returns the slot or -1 (status SC_ERR_RETRY_LIMIT on give-up; a
+// failed allocation returns -1 silently, its creator set the status).
+__device__ inline int32_t entry_slot(const DevVolume& V, int entry) {
+    volatile int32_t* sp = &V.table[entry].slot;
+    for (int32_t it = 0; it < V.retry_limit; ++it) {
+        const int32_t s = *sp;
+        if (s >= 0) return s;
+        if (s == SLOT_FAILED) return -1;
+        __nanosleep(64);
+    }
+    set_status(V.status, SC_ERR_RETRY_LIMIT);
+    return -1;
+}
+
+// Slot of voxel-block `key` for lookups: pool slot or -1.
+__device__ inline int32_t find_slot(const DevVolume& V, unsigned long long key) {
+    const int e = hash_find(V, key);
+    if (e < 0) return -1;
+    const int32_t s = V.table[e].slot;
+    return s >= 0 ? s : -1;
+}
+
+// Closed segment [q0, q1] against the closed box [lo, hi]^3 (slab test).
+__device__ __forceinline__ bool seg_box(const float q0[3], const float q1[3], const float lo[3],
+                                        const float hi[3]) {
+    float tmin = 0.f, tmax = 1.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float d = q1[a] - q0[a];
+        if (d == 0.f) {
+            if (q0[a] < lo[a] || q0[a] > hi[a]) return false;
+            continue;
+        }
+        float t0 = (lo[a] - q0[a]) / d, t1 = (hi[a] - q0[a]) / d;
+        if (t0 > t1) {
+            const float t = t0;
+            t0 = t1;
+            t1 = t;
+        }
+        tmin = fmaxf(tmin, t0);
+        tmax = fminf(tmax, t1);
+    }
+    return tmin <= tmax;
+}
+
+}  // namespace sc

@@ -1,0 +1,346 @@
+// Loss on the fused SDF and its adjoint with respect to keyframe poses and depth
+// (an extension; the paper has no counterpart).
+//
+//   L = (1/P) sum_p Dt(p)^2 + lambda * sum_v W D^2 / sum_v W
+//
+// Forward: two passes over the points (count + sum of Dt^2, then the scatter of
+// dL/dD once P is known) and one pass over the pool for the weighted
+// regulariser.  Adjoint: D(v) = sum_k w_k d_k(v) / W(v), so for each keyframe the
+// kernel walks its block list, recomputes each voxel's projective sample exactly
+// as the integration did (same sample function, same camera constants) and
+// accumulates g = dL/dD(v) / W(v) for unclamped samples into the depth-pixel
+// gradient and into four pose moments (sum g, sum g q) from which the se(3)
+// gradient follows.  Lane values are float, warp and CTA partials double.
+#include <cmath>
+
+#include "volume.cuh"
+
+using namespace sc;
+
+namespace {
+
+constexpr int LOSS_THREADS = 256;
+
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Trilinear neighbourhood of point p: voxel corner indices and weights; returns
+// false if any corner is unallocated or unobserved (W = 0).
+struct Corners {
+    uint32_t vox[8];  // slot * 512 + voxel index (max_blocks <= 2^23)
+    float beta[8];
+};
+
+__device__ inline bool point_corners(const DevVolume& V, float s, const float* p, Corners& c, float& Dt) {
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float g = __fdiv_rn(p[a], s);
+        const float fl = floorf(g);
+        i0[a] = (int)fl;
+        f[a] = __fsub_rn(g, fl);
+    }
+    int32_t last_slot = -1;
+    int lbx = 0x7fffffff, lby = 0, lbz = 0;
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
+        const int ix = i0[0] + ox, iy = i0[1] + oy, iz = i0[2] + oz;
+        const int bx = ix >> 3, by = iy >> 3, bz = iz >> 3;
+        if (bx != lbx || by != lby || bz != lbz) {
+            lbx = bx;
+            lby = by;
+            lbz = bz;
+            last_slot = coord_ok(bx, by, bz) ? find_slot(V, pack_key(bx, by, bz)) : -1;
+        }
+        if (last_slot < 0) return false;
+        const int vi = (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7);
+        const uint32_t gv = (uint32_t)last_slot * NVOX + vi;
+        const float w = V.W[gv];
+        if (!(w > 0.f)) return false;
+        const float b = (ox ? f[0] : 1.f - f[0]) * (oy ? f[1] : 1.f - f[1]) * (oz ? f[2] : 1.f - f[2]);
+        c.vox[k] = gv;
+        c.beta[k] = b;
+        acc = fmaf(b, V.D[gv], acc);
+    }
+    Dt = acc;
+    return true;
+}
+
+// out[1] += P, out[2] += sum Dt^2
+__global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64_t n, double* out) {
+    __shared__ double sh[2][LOSS_THREADS / 32];
+    double a = 0.0, cnt = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Corners c;
+        float Dt;
+        if (point_corners(V, s, pts + 3 * i, c, Dt)) {
+            a += (double)Dt * Dt;
+            cnt += 1.0;
+        }
+    }
+    a = warp_sum(a);
+    cnt = warp_sum(cnt);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][w] = a;
+        sh[1][w] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0, C = 0;
+        for (int k = 0; k < LOSS_THREADS / 32; ++k) {
+            A += sh[0][k];
+            C += sh[1][k];
+        }
+        atomicAdd(out + 1, C);
+        atomicAdd(out + 2, A);
+    }
+}
+
+// out[3] += sum W D^2, out[4] += sum W over pool slots [0, used)
+__global__ void loss_reg_kernel(DevVolume V, double* out) {
+    __shared__ double sh[2][LOSS_THREADS / 32];
+    const size_t nv = (size_t)min(*V.pool_count, V.max_blocks) * NVOX;
+    double a = 0.0, b = 0.0;
+    for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < nv; i += (size_t)gridDim.x * blockDim.x * 4) {
+        const float4 W = *reinterpret_cast<const float4*>(V.W + i);
+        const float4 D = *reinterpret_cast<const float4*>(V.D + i);
+        float pa = 0.f, pb = 0.f;
+        if (W.x > 0.f) { pa = fmaf(W.x * D.x, D.x, pa); pb += W.x; }
+        if (W.y > 0.f) { pa = fmaf(W.y * D.y, D.y, pa); pb += W.y; }
+        if (W.z > 0.f) { pa = fmaf(W.z * D.z, D.z, pa); pb += W.z; }
+        if (W.w > 0.f) { pa = fmaf(W.w * D.w, D.w, pa); pb += W.w; }
+        a += pa;
+        b += pb;
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][w] = a;
+        sh[1][w] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0, B = 0;
+        for (int k = 0; k < LOSS_THREADS / 32; ++k) {
+            A += sh[0][k];
+            B += sh[1][k];
+        }
+        atomicAdd(out + 3, A);
+        atomicAdd(out + 4, B);
+    }
+}
+
+// grad_D = 2 lambda W D / sum W (0 where W = 0), pool slots [0, used)
+__global__ void loss_grad_init_kernel(DevVolume V, float lambda, const double* out, float* grad) {
+    const size_t nv = (size_t)min(*V.pool_count, V.max_blocks) * NVOX;
+    const double sw = out[4];
+    const float scale = sw > 0.0 ? (float)(2.0 * lambda / sw) : 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
+        const float W = V.W[i];
+        grad[i] = W > 0.f ? scale * W * V.D[i] : 0.f;
+    }
+}
+
+// grad_D += (2/P) Dt beta
+__global__ void loss_points_grad_kernel(DevVolume V, float s, const float* pts, int64_t n, const double* out,
+                                        float* grad) {
+    const double P = out[1];
+    if (!(P > 0.0)) return;
+    const float sc2 = (float)(2.0 / P);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Corners c;
+        float Dt;
+        if (!point_corners(V, s, pts + 3 * i, c, Dt)) continue;
+        const float g = sc2 * Dt;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) atomicAdd(grad + c.vox[k], g * c.beta[k]);
+    }
+}
+
+__global__ void loss_finalize_kernel(float lambda, double* out) {
+    const double P = out[1];
+    double L = P > 0.0 ? out[2] / P : 0.0;
+    if (out[4] > 0.0) L += (double)lambda * out[3] / out[4];
+    out[0] = L;
+}
+
+// ------------------------------------------------------------------ adjoint ----
+
+struct AdjItem {
+    KfCam cam;
+    const int32_t* list;
+    const int32_t* count;
+    float* grad_depth;  // [H][W] or null
+};
+
+// acc [n][4]: sum g, sum g qx, sum g qy, sum g qz  (q = voxel - camera, voxel units)
+__global__ void adjoint_kernel(DevVolume V, const AdjItem* items, int n, uint32_t cap, const float* grad,
+                               double* acc) {
+    __shared__ double sh[4];
+    const int lane = threadIdx.x & 31;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x < 4) sh[threadIdx.x] = 0.0;
+        __syncthreads();
+        const AdjItem& it = items[k];
+        const KfCam& cam = it.cam;
+        const uint32_t cnt = min((uint32_t)*it.count, cap);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (uint32_t b = wid; b < cnt; b += nw) {
+            const int32_t slot = it.list[b];
+            const int4 c = V.coord[slot];
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+                int lx0, ly, lz;
+                lane_voxels(lane, g, lx0, ly, lz);
+                const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float d, eta;
+                    int pix;
+                    const int ix = 8 * c.x + lx0 + j, iy = 8 * c.y + ly, iz = 8 * c.z + lz;
+                    if (!sample_voxel(cam, ix, iy, iz, d, pix, &eta)) continue;
+                    if (!(eta < cam.mu)) continue;  // clamped: no derivative
+                    const float gv = __fdiv_rn(grad[off + j], V.W[off + j]);
+                    if (gv == 0.f) continue;
+                    if (it.grad_depth) atomicAdd(it.grad_depth + pix, gv);
+                    a0 += gv;
+                    a1 = fmaf(gv, __fsub_rn((float)(ix - cam.ti[0]), cam.tf[0]), a1);
+                    a2 = fmaf(gv, __fsub_rn((float)(iy - cam.ti[1]), cam.tf[1]), a2);
+                    a3 = fmaf(gv, __fsub_rn((float)(iz - cam.ti[2]), cam.tf[2]), a3);
+                }
+            }
+        }
+        const double s0 = warp_sum((double)a0), s1 = warp_sum((double)a1), s2 = warp_sum((double)a2),
+                     s3 = warp_sum((double)a3);
+        if (lane == 0 && (s0 != 0.0 || s1 != 0.0 || s2 != 0.0 || s3 != 0.0)) {
+            atomicAdd(&sh[0], s0);
+            atomicAdd(&sh[1], s1);
+            atomicAdd(&sh[2], s2);
+            atomicAdd(&sh[3], s3);
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 && sh[threadIdx.x] != 0.0) atomicAdd(acc + 4 * k + threadIdx.x, sh[threadIdx.x]);
+        __syncthreads();
+    }
+}
+
+// grad_xi[k] = (r3 A, s B x r3 + (t x r3) A), A = sum g, B = sum g q
+struct AdjPose {
+    double r3[3];
+    double t[3];
+};
+
+__global__ void adjoint_finalize_kernel(const AdjPose* poses, const double* acc, int n, double s, double* grad_xi) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double* r = poses[k].r3;
+    const double* t = poses[k].t;
+    const double A = acc[4 * k];
+    const double B[3] = {s * acc[4 * k + 1], s * acc[4 * k + 2], s * acc[4 * k + 3]};
+    double* g = grad_xi + 6 * k;
+    for (int j = 0; j < 3; ++j) g[j] = r[j] * A;
+    const double bx[3] = {B[1] * r[2] - B[2] * r[1], B[2] * r[0] - B[0] * r[2], B[0] * r[1] - B[1] * r[0]};
+    const double tx[3] = {t[1] * r[2] - t[2] * r[1], t[2] * r[0] - t[0] * r[2], t[0] * r[1] - t[1] * r[0]};
+    for (int j = 0; j < 3; ++j) g[3 + j] = bx[j] + tx[j] * A;
+}
+
+struct AdjScratch {
+    int cap = 0;
+    AdjItem* items_d = nullptr;
+    AdjPose* poses_d = nullptr;
+    double* acc_d = nullptr;
+    AdjItem* items_h = nullptr;
+    AdjPose* poses_h = nullptr;
+};
+
+// one scratch per process and device is enough for the serialised calls on a volume
+AdjScratch g_adj[64];
+
+int adj_reserve(int device, int n) {
+    AdjScratch& A = g_adj[device & 63];
+    if (A.cap >= n) return SC_OK;
+    if (A.items_d) cudaFree(A.items_d);
+    if (A.poses_d) cudaFree(A.poses_d);
+    if (A.acc_d) cudaFree(A.acc_d);
+    if (A.items_h) cudaFreeHost(A.items_h);
+    if (A.poses_h) cudaFreeHost(A.poses_h);
+    A = AdjScratch();
+    const int cap = n < 256 ? 256 : n;
+    SC_CUDA(cudaMalloc((void**)&A.items_d, cap * sizeof(AdjItem)));
+    SC_CUDA(cudaMalloc((void**)&A.poses_d, cap * sizeof(AdjPose)));
+    SC_CUDA(cudaMalloc((void**)&A.acc_d, cap * 4 * sizeof(double)));
+    SC_CUDA(cudaMallocHost((void**)&A.items_h, cap * sizeof(AdjItem)));
+    SC_CUDA(cudaMallocHost((void**)&A.poses_h, cap * sizeof(AdjPose)));
+    A.cap = cap;
+    return SC_OK;
+}
+
+}  // namespace
+
+extern "C" int sc_sdf_loss(sc_volume* V, const float* points, int64_t n, float lambda, float* grad_D, double* out,
+                           sc_stream stream) {
+    if (!V || (!points && n > 0) || n < 0 || !grad_D || !out || !(lambda >= 0.f)) return SC_ERR_INVALID_ARG;
+    if (((uintptr_t)grad_D & 15) || ((uintptr_t)out & 7)) return SC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const float vs = V->p.voxel_size;
+    SC_CUDA(cudaMemsetAsync(out, 0, 5 * sizeof(double), s));
+    const int grid = V->num_sms * 8;
+    if (n > 0) loss_points_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, points, n, out);
+    loss_reg_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, out);
+    loss_grad_init_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, lambda, out, grad_D);
+    if (n > 0) loss_points_grad_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, points, n, out, grad_D);
+    loss_finalize_kernel<<<1, 1, 0, s>>>(lambda, out);
+    count_launches(n > 0 ? 5 : 3);
+    SC_CUDA(cudaGetLastError());
+    V->last_stream = s;
+    return SC_OK;
+}
+
+extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
+                              int32_t n, const sc_intrinsics* K, const float* grad_D, double* grad_xi,
+                              float* grad_depth, sc_stream stream) {
+    if (!V || !kf_ids || !depths || !poses || n < 1 || !intrinsics_ok(K) || !grad_D || !grad_xi)
+        return SC_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes || !depths[i]) return SC_ERR_INVALID_ARG;
+        if (!V->integrated[kf_ids[i]]) return SC_ERR_NOT_INTEGRATED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = adj_reserve(V->device, n);
+    if (rc) return rc;
+    AdjScratch& A = g_adj[V->device & 63];
+    // the pinned staging tables may still be read by a previous call's copies
+    SC_CUDA(cudaStreamSynchronize(s));
+    const size_t img = (size_t)K->width * K->height;
+    for (int i = 0; i < n; ++i) {
+        const int kf = kf_ids[i];
+        A.items_h[i].cam = make_cam(V, K, &poses[i], depths[i], nullptr);
+        A.items_h[i].list = list_ptr(V, kf, V->cur[kf]);
+        A.items_h[i].count = count_ptr(V, kf, V->cur[kf]);
+        A.items_h[i].grad_depth = grad_depth ? grad_depth + i * img : nullptr;
+        for (int r = 0; r < 3; ++r) {
+            A.poses_h[i].r3[r] = (double)poses[i].m[r][2];
+            A.poses_h[i].t[r] = (double)poses[i].m[r][3];
+        }
+    }
+    SC_CUDA(cudaMemcpyAsync(A.items_d, A.items_h, n * sizeof(AdjItem), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaMemcpyAsync(A.poses_d, A.poses_h, n * sizeof(AdjPose), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaMemsetAsync(A.acc_d, 0, n * 4 * sizeof(double), s));
+    if (grad_depth) SC_CUDA(cudaMemsetAsync(grad_depth, 0, n * img * sizeof(float), s));
+    adjoint_kernel<<<V->num_sms * 8, 256, 0, s>>>(V->dv, A.items_d, n, V->p.max_blocks_per_keyframe, grad_D, A.acc_d);
+    adjoint_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(A.poses_d, A.acc_d, n, (double)V->p.voxel_size, grad_xi);
+    count_launches(2);
+    SC_CUDA(cudaGetLastError());
+    V->last_stream = s;
+    return SC_OK;
+}

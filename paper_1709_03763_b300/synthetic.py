@@ -493,14 +493,16 @@ def drift_poses(poses, angle, shift, g) -> np.ndarray:
     return np.stack(out)
 
 
-def workload_kinect(device="cpu", n_frames=600, kappa=10) -> Workload:
+def workload_kinect(device="cpu", n_frames=600, kappa=10, render_frames=None) -> Workload:
     """Plain method at Kinect scale: 600 raw 640x480 frames fused 10 per keyframe into 60
     keyframes (keyframe pose = first frame of its group), integrated at drifted poses
     (0.2 deg / 0.5 cm random walk per keyframe); one pose update moves all 60 to their
-    true poses.  Voxel 1 cm, truncation 4 cm, 2^20 buckets."""
+    true poses.  Voxel 1 cm, truncation 4 cm, 2^20 buckets.  render_frames renders only
+    that many leading frames (the poses of all frames and keyframes are still made)."""
     scene, _ = scene_kinect()
     frame_poses = kinect_trajectory(n_frames)
-    fd, fr = render(scene, KINECT, frame_poses, device=device)
+    nr = n_frames if render_frames is None else render_frames
+    fd, fr = render(scene, KINECT, frame_poses[:nr], device=device)
     fd = add_sensor_noise(fd, 2)
     kf_true = frame_poses[::kappa]
     g = rng(2, STREAM_PERTURB)

@@ -1,0 +1,291 @@
+"""Python binding of the surfcorr C ABI: argument marshalling over torch tensors.
+
+Every computation runs in libsurfcorr.so's CUDA kernels; this module only checks
+shapes / dtypes / devices, turns tensors into device pointers and poses into the
+ABI's structs, and raises SurfcorrError on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import (BatchConfig, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
+                   VolumeParams, check, lib)
+
+__all__ = ["Volume", "fuse_frames_into_keyframe", "pose_distance", "select_topm", "select_consecutive",
+           "pose_exp_left", "SurfcorrError", "make_intrinsics", "make_pose"]
+
+
+def make_intrinsics(intr) -> Intrinsics:
+    """From a synthetic.Intrinsics, an Intrinsics struct or a (fx, fy, cx, cy, W, H) tuple."""
+    if isinstance(intr, Intrinsics):
+        return intr
+    if hasattr(intr, "as_tuple"):
+        intr = intr.as_tuple()
+    fx, fy, cx, cy, W, H = intr
+    return Intrinsics(float(fx), float(fy), float(cx), float(cy), int(W), int(H))
+
+
+def make_pose(T) -> Pose:
+    """[3,4] world_from_camera (numpy / torch / sequence) -> Pose struct."""
+    if isinstance(T, Pose):
+        return T
+    if hasattr(T, "detach"):
+        T = T.detach().cpu().numpy()
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float32).reshape(12))
+    p = Pose()
+    ctypes.memmove(ctypes.addressof(p), a.ctypes.data, 48)
+    return p
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+class Volume:
+    """A voxel-hashed TSDF volume on the current CUDA device (owned by libsurfcorr)."""
+
+    def __init__(self, voxel_size: float, trunc: float, n_buckets: int, *, bucket_size: int = 4,
+                 max_blocks: int = 1 << 20, colour: str = "rgba8", max_keyframes: int = 1024,
+                 max_blocks_per_keyframe: int = 1 << 16, max_batch: int = 256):
+        self.colour = colour
+        self.params = VolumeParams(float(voxel_size), float(trunc), int(n_buckets), int(bucket_size),
+                                   int(max_blocks), _lib.SC_RGB_F32 if colour == "f32" else _lib.SC_RGBA8,
+                                   int(max_keyframes), int(max_blocks_per_keyframe), int(max_batch))
+        self.device = torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        check(lib().sc_create_volume(ctypes.byref(self.params), ctypes.byref(h)), "sc_create_volume")
+        self.h = h
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sc_destroy_volume(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def voxel_size(self) -> float:
+        return self.params.voxel_size
+
+    @property
+    def trunc(self) -> float:
+        return self.params.trunc
+
+    def reset(self, stream=None):
+        check(lib().sc_reset_volume(self.h, _stream(stream)), "sc_reset_volume")
+
+    def status(self) -> int:
+        """Read and clear the sticky device status (0 = ok)."""
+        st = ctypes.c_int32(0)
+        check(lib().sc_get_status(self.h, ctypes.byref(st)), "sc_get_status")
+        return st.value
+
+    def check(self):
+        st = self.status()
+        if st:
+            raise SurfcorrError(st, "device status")
+
+    def info(self) -> dict:
+        i = VolumeInfo()
+        check(lib().sc_get_volume_info(self.h, ctypes.byref(i)), "sc_get_volume_info")
+        return {k: getattr(i, k) for k, _ in VolumeInfo._fields_}
+
+    def set_profiling(self, enabled: bool):
+        check(lib().sc_set_profiling(self.h, int(bool(enabled))), "sc_set_profiling")
+
+    def profile(self) -> dict:
+        p = Profile()
+        check(lib().sc_get_profile(self.h, ctypes.byref(p)), "sc_get_profile")
+        return {k: getattr(p, k) for k, _ in Profile._fields_ if k != "pad"}
+
+    def set_retry_limit(self, n: int):
+        check(lib().sc_set_retry_limit(self.h, int(n)), "sc_set_retry_limit")
+
+    # -- plain path
+    def integrate(self, kf_id: int, depth: torch.Tensor, rgba: torch.Tensor, intr, pose, stream=None):
+        check(lib().sc_integrate_keyframe(self.h, int(kf_id), _dev(depth, torch.float32, "depth"),
+                                          _dev(rgba, torch.uint8, "rgba"), ctypes.byref(make_intrinsics(intr)),
+                                          ctypes.byref(make_pose(pose)), _stream(stream)),
+              "sc_integrate_keyframe")
+
+    def deintegrate(self, kf_id: int, depth: torch.Tensor, rgba: torch.Tensor, intr, pose, stream=None):
+        check(lib().sc_deintegrate_keyframe(self.h, int(kf_id), _dev(depth, torch.float32, "depth"),
+                                            _dev(rgba, torch.uint8, "rgba"), ctypes.byref(make_intrinsics(intr)),
+                                            ctypes.byref(make_pose(pose)), _stream(stream)),
+              "sc_deintegrate_keyframe")
+
+    # -- batched path
+    def _items(self, kf_ids, depths, rgbas, old_poses, new_poses):
+        n = len(kf_ids)
+        arr = (ReintItem * n)()
+        for i in range(n):
+            d = depths[i]
+            c = rgbas[i]
+            arr[i].depth = _dev(d, torch.float32, "depth")
+            arr[i].rgba = _dev(c, torch.uint8, "rgba")
+            arr[i].old_pose = make_pose(old_poses[i])
+            arr[i].new_pose = make_pose(new_poses[i])
+            arr[i].kf_id = int(kf_ids[i])
+        return arr
+
+    def reintegrate_batch(self, kf_ids: Sequence[int], depths, rgbas, old_poses, new_poses, intr, stream=None):
+        """One pose-graph update: de-integrate each keyframe at its old pose and re-integrate at
+        its new pose (one graph launch).  depths / rgbas: tensors [n,H,W] / [n,H,W,4] or lists."""
+        arr = self._items(kf_ids, depths, rgbas, old_poses, new_poses)
+        check(lib().sc_reintegrate_batch(self.h, arr, len(kf_ids), ctypes.byref(make_intrinsics(intr)),
+                                         _stream(stream)), "sc_reintegrate_batch")
+
+    def set_batch_config(self, warps_per_cta=4, ctas_per_sm=8, blocks_per_grab=1):
+        c = BatchConfig(warps_per_cta, ctas_per_sm, blocks_per_grab)
+        check(lib().sc_set_batch_config(self.h, ctypes.byref(c)), "sc_set_batch_config")
+
+    def batch_config(self) -> dict:
+        c = BatchConfig()
+        check(lib().sc_get_batch_config(self.h, ctypes.byref(c)), "sc_get_batch_config")
+        return {k: getattr(c, k) for k, _ in BatchConfig._fields_}
+
+    def autotune_batch(self, kf_ids, depths, rgbas, old_poses, new_poses, intr, stream=None):
+        arr = self._items(kf_ids, depths, rgbas, old_poses, new_poses)
+        best = BatchConfig()
+        ms = ctypes.c_float(0)
+        check(lib().sc_autotune_batch(self.h, arr, len(kf_ids), ctypes.byref(make_intrinsics(intr)),
+                                      _stream(stream), ctypes.byref(best), ctypes.byref(ms)), "sc_autotune_batch")
+        return {k: getattr(best, k) for k, _ in BatchConfig._fields_}, ms.value
+
+    # -- extraction
+    def extract(self, payload: bool = True, capacity: int | None = None, stream=None) -> dict:
+        """Allocated blocks: coords [n,3] int32, slots [n] int32 and, with payload, D / W [n,512]
+        float32 and C [n,512,4] uint8 (rgba8) or [n,512,3] float32 (f32).  Unordered."""
+        cap = int(capacity if capacity is not None else self.info()["allocated_blocks"])
+        dev = torch.device("cuda", self.device)
+        coords = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
+        slots = torch.empty((max(cap, 1),), dtype=torch.int32, device=dev)
+        D = W = C = None
+        if payload:
+            D = torch.empty((max(cap, 1), 512), dtype=torch.float32, device=dev)
+            W = torch.empty_like(D)
+            C = (torch.empty((max(cap, 1), 512, 3), dtype=torch.float32, device=dev) if self.colour == "f32"
+                 else torch.empty((max(cap, 1), 512, 4), dtype=torch.uint8, device=dev))
+        n = ctypes.c_int32(0)
+        rc = lib().sc_extract_block_list(self.h, coords.data_ptr(), slots.data_ptr(),
+                                         D.data_ptr() if payload else None, W.data_ptr() if payload else None,
+                                         C.data_ptr() if payload else None, cap, ctypes.byref(n), _stream(stream))
+        check(rc, "sc_extract_block_list")
+        m = n.value
+        out = {"coords": coords[:m], "slots": slots[:m]}
+        if payload:
+            out.update(D=D[:m], W=W[:m], C=C[:m])
+        return out
+
+    def keyframe_blocks(self, kf_id: int, stream=None) -> torch.Tensor:
+        """Pool slots of kf_id's stored block list (its allocation set A(k, T))."""
+        n = ctypes.c_int32(0)
+        rc = lib().sc_get_keyframe_blocks(self.h, int(kf_id), None, 0, ctypes.byref(n), _stream(stream))
+        if rc not in (_lib.SC_OK, _lib.SC_ERR_CAPACITY):
+            check(rc, "sc_get_keyframe_blocks")
+        out = torch.empty((max(n.value, 1),), dtype=torch.int32, device=torch.device("cuda", self.device))
+        check(lib().sc_get_keyframe_blocks(self.h, int(kf_id), out.data_ptr(), n.value, ctypes.byref(n),
+                                           _stream(stream)), "sc_get_keyframe_blocks")
+        return out[:n.value]
+
+    # -- loss and adjoint
+    def grad_buffer(self) -> torch.Tensor:
+        return torch.zeros((self.params.max_blocks, 512), dtype=torch.float32,
+                           device=torch.device("cuda", self.device))
+
+    def sdf_loss(self, points: torch.Tensor, lam: float = 0.1, grad_D: torch.Tensor | None = None, stream=None):
+        """Returns (out [5] float64 device: L, P, sum Dt^2, sum W D^2, sum W;  grad_D)."""
+        if grad_D is None:
+            grad_D = self.grad_buffer()
+        out = torch.empty(5, dtype=torch.float64, device=torch.device("cuda", self.device))
+        pts = points
+        check(lib().sc_sdf_loss(self.h, _dev(pts, torch.float32, "points"), int(pts.shape[0]), float(lam),
+                                _dev(grad_D, torch.float32, "grad_D"), out.data_ptr(), _stream(stream)),
+              "sc_sdf_loss")
+        return out, grad_D
+
+    def sdf_adjoint(self, kf_ids, depths, poses, intr, grad_D, with_depth=True, stream=None):
+        """Gradient of the loss w.r.t. each keyframe's left se(3) pose perturbation
+        (grad_xi [n,6] float64) and its depth pixels (grad_depth [n,H,W] float32)."""
+        n = len(kf_ids)
+        ids = (ctypes.c_int32 * n)(*[int(k) for k in kf_ids])
+        ptrs = (ctypes.c_void_p * n)(*[_dev(depths[i], torch.float32, "depth") for i in range(n)])
+        pz = (Pose * n)(*[make_pose(poses[i]) for i in range(n)])
+        K = make_intrinsics(intr)
+        dev = torch.device("cuda", self.device)
+        gx = torch.empty((n, 6), dtype=torch.float64, device=dev)
+        gd = torch.empty((n, K.height, K.width), dtype=torch.float32, device=dev) if with_depth else None
+        check(lib().sc_sdf_adjoint(self.h, ids, ptrs, pz, n, ctypes.byref(K), _dev(grad_D, torch.float32, "grad_D"),
+                                   gx.data_ptr(), gd.data_ptr() if with_depth else None, _stream(stream)),
+              "sc_sdf_adjoint")
+        return gx, gd
+
+
+def fuse_frames_into_keyframe(depths: torch.Tensor, frame_poses, kf_pose, intr, disc_rel: float = 0.1,
+                              out_depth: torch.Tensor | None = None, out_weight: torch.Tensor | None = None,
+                              stream=None):
+    """Eq. 1 keyframe depth fusion of frames [n,H,W] into the keyframe pose.  Returns (Z*, W*)."""
+    n, H, W = depths.shape
+    if out_depth is None:
+        out_depth = torch.empty((H, W), dtype=torch.float32, device=depths.device)
+    if out_weight is None:
+        out_weight = torch.empty((H, W), dtype=torch.float32, device=depths.device)
+    pz = (Pose * n)(*[make_pose(frame_poses[i]) for i in range(n)])
+    fp = FusionParams(float(disc_rel))
+    check(lib().sc_fuse_frames_into_keyframe(_dev(depths, torch.float32, "depths"), pz, n,
+                                             ctypes.byref(make_pose(kf_pose)), ctypes.byref(make_intrinsics(intr)),
+                                             ctypes.byref(fp), _dev(out_depth, torch.float32, "out_depth"),
+                                             _dev(out_weight, torch.float32, "out_weight"), _stream(stream)),
+          "sc_fuse_frames_into_keyframe")
+    return out_depth, out_weight
+
+
+def pose_distance(a, b) -> float:
+    pa, pb = make_pose(a), make_pose(b)
+    return lib().sc_pose_distance(ctypes.byref(pa), ctypes.byref(pb))
+
+
+def select_topm(dist, m: int) -> np.ndarray:
+    d = np.ascontiguousarray(dist, np.float64)
+    out = np.zeros(min(m, len(d)), np.int32)
+    check(lib().sc_select_topm(d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(d), int(m),
+                               out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))), "sc_select_topm")
+    return out
+
+
+def select_consecutive(dist, m: int) -> int:
+    d = np.ascontiguousarray(dist, np.float64)
+    j = lib().sc_select_consecutive(d.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(d), int(m))
+    if j < 0:
+        raise SurfcorrError(j, "sc_select_consecutive")
+    return j
+
+
+def pose_exp_left(T, xi) -> np.ndarray:
+    x = np.ascontiguousarray(np.asarray(xi, np.float64).reshape(6))
+    out = Pose()
+    check(lib().sc_pose_exp_left(ctypes.byref(make_pose(T)), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.byref(out)), "sc_pose_exp_left")
+    return np.array(out.m, dtype=np.float32).reshape(3, 4)

@@ -1,0 +1,47 @@
+"""GPU keyframe depth fusion (Eq. 1) against the oracle on Kinect-scale frames."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_03763_b300 import fuse_frames_into_keyframe, synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+def _frames():
+    scene, _ = synthetic.scene_kinect()
+    poses = synthetic.kinect_trajectory(600)[100:110].astype(np.float32)
+    d, c = synthetic.render(scene, synthetic.KINECT, poses)
+    d = synthetic.add_sensor_noise(d, 2, first_frame=100)
+    return d, poses
+
+
+def test_fusion_matches_oracle():
+    d, poses = _frames()
+    Zg, Wg = fuse_frames_into_keyframe(d.cuda(), poses, poses[0], synthetic.KINECT, disc_rel=0.1)
+    Zo, Wo, fl = oracle.fuse(d, poses, poses[0], synthetic.KINECT.as_tuple(), disc_rel=0.1)
+    Zg, Wg = Zg.cpu().numpy().astype(np.float64), Wg.cpu().numpy().astype(np.float64)
+    good = fl == 0
+    assert good.mean() > 0.99
+    cov = good & (Wo > 0)
+    assert cov.sum() > 0.5 * Wo.size
+    assert np.all((Wg[good] > 0) == (Wo[good] > 0))
+    assert np.abs(Zg - Zo)[cov].max() <= 1e-5
+    assert (np.abs(Wg - Wo)[cov] / Wo[cov]).max() <= 1e-5
+
+
+def test_fusion_identical_frames_and_ragged_size():
+    z0 = 1.37
+    H, W = 37, 53
+    intr = (40.0, 40.0, 26.0, 18.0, W, H)
+    T = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
+    d = torch.full((3, H, W), z0, dtype=torch.float32)
+    Zg, Wg = fuse_frames_into_keyframe(d.cuda(), [T] * 3, T, intr)
+    Zg, Wg = Zg.cpu().numpy(), Wg.cpu().numpy()
+    inner = np.zeros((H, W), bool)
+    inner[1:-1, 1:-1] = True
+    zf = float(np.float32(z0))
+    assert np.abs(Zg[inner] - zf).max() < 1e-6
+    assert np.abs(Wg[inner] - 3 / zf ** 2).max() < 1e-5
+    assert np.all(Wg[~inner] == 0)

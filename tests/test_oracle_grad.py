@@ -7,7 +7,7 @@ from oracle_helpers import identity_pose, plane_depth, uniform_rgba
 from paper_1709_03763_b300 import synthetic
 
 INTR = (30.0, 30.0, 15.5, 11.5, 32, 24)
-S, MU = 0.01, 0.04
+S, MU = oracle.f32(0.01), oracle.f32(0.04)
 
 
 def _plane_points(z, n=3000, seed=0):

@@ -16,7 +16,7 @@ def _proj(p, intr):
 
 
 def test_plane_closed_form_truncated_distance():
-    s, mu, z0 = 0.01, 0.04, 1.0047
+    s, mu, z0 = oracle.f32(0.01), oracle.f32(0.04), 1.0047
     V = oracle.Volume(s, mu)
     V.integrate(0, plane_depth(INTR, z0), uniform_rgba(INTR, (10, 20, 30)), INTR, identity_pose())
     e = V.export()
@@ -39,7 +39,7 @@ def test_plane_closed_form_truncated_distance():
 
 
 def test_sphere_closed_form_truncated_distance():
-    s, mu = 0.01, 0.04
+    s, mu = oracle.f32(0.01), oracle.f32(0.04)
     intr = (60.0, 60.0, 31.5, 23.5, 64, 48)
     c, r = (0.05, -0.03, 1.5), 0.4
     depth = sphere_depth(intr, c, r)
@@ -177,7 +177,7 @@ def test_allocation_matches_dense_segment_sampling(tiny):
     fx = tiny.intr.fx / 20
     intr = (fx, fx, (16 - 1) / 2, (12 - 1) / 2, 16, 12)
     pose = tiny.kf_poses[0]
-    s, mu = tiny.voxel_size, tiny.trunc
+    s, mu = oracle.f32(tiny.voxel_size), oracle.f32(tiny.trunc)
     coords, marg = oracle.allocation_set(d, pose, intr, s, mu)
     A_all = set(map(tuple, coords))
     A_robust = set(map(tuple, coords[marg == 0]))
