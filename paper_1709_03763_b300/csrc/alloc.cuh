@@ -44,26 +44,53 @@ __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, floa
             __fmaf_rn(k.Ms[3 * r + 2], c1[2], __fmaf_rn(k.Ms[3 * r + 1], c1[1], __fmul_rn(k.Ms[3 * r], c1[0]))),
             k.tf[r]);
     }
+    // Blocks whose closed box [8b, 8b+8] (absolute voxel units) meets [lo, hi] on an
+    // axis: b from ceil(lo) - 1 >> 3 to floor(hi) >> 3 (exact for these float
+    // endpoints); the slab test then decides per block.
     int blo[3], bhi[3];
+    float inv[3];
+    bool flat[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        // conservative candidate range; the slab test decides
         const float lo = fminf(q0[a], q1[a]), hi = fmaxf(q0[a], q1[a]);
-        blo[a] = (((int)floorf(lo) + k.ti[a]) >> 3) - 1;
+        blo[a] = ((int)ceilf(lo) - 1 + k.ti[a]) >> 3;
         bhi[a] = ((int)floorf(hi) + k.ti[a]) >> 3;
+        const float d = __fsub_rn(q1[a], q0[a]);
+        flat[a] = d == 0.f;
+        inv[a] = flat[a] ? 0.f : __frcp_rn(d);
     }
     // a band segment spans a handful of blocks; a larger range comes from a
     // degenerate input and is skipped rather than looped over
     if (bhi[0] - blo[0] > MAX_BLOCK_SPAN || bhi[1] - blo[1] > MAX_BLOCK_SPAN || bhi[2] - blo[2] > MAX_BLOCK_SPAN)
         return;
-    for (int bz = blo[2]; bz <= bhi[2]; ++bz)
-        for (int by = blo[1]; by <= bhi[1]; ++by)
+    // segment parameter interval [t0, t1] inside block b's slab on axis a
+    auto slab = [&](int a, int b, float& t0, float& t1) -> bool {
+        const float lo = (float)(8 * b - k.ti[a]), hi = lo + 8.f;
+        if (flat[a]) {
+            t0 = 0.f;
+            t1 = 1.f;
+            return !(q0[a] < lo || q0[a] > hi);
+        }
+        float ta = __fmul_rn(__fsub_rn(lo, q0[a]), inv[a]), tb = __fmul_rn(__fsub_rn(hi, q0[a]), inv[a]);
+        t0 = fmaxf(fminf(ta, tb), 0.f);
+        t1 = fminf(fmaxf(ta, tb), 1.f);
+        return t0 <= t1;
+    };
+    for (int bz = blo[2]; bz <= bhi[2]; ++bz) {
+        float z0, z1;
+        if (!slab(2, bz, z0, z1)) continue;
+        for (int by = blo[1]; by <= bhi[1]; ++by) {
+            float y0, y1;
+            if (!slab(1, by, y0, y1)) continue;
+            const float t0 = fmaxf(z0, y0), t1 = fminf(z1, y1);
+            if (t0 > t1) continue;
             for (int bx = blo[0]; bx <= bhi[0]; ++bx) {
-                const float lo[3] = {(float)(8 * bx - k.ti[0]), (float)(8 * by - k.ti[1]),
-                                     (float)(8 * bz - k.ti[2])};
-                const float hi[3] = {lo[0] + 8.f, lo[1] + 8.f, lo[2] + 8.f};
-                if (seg_box(q0, q1, lo, hi)) f(bx, by, bz);
+                float x0, x1;
+                if (!slab(0, bx, x0, x1)) continue;
+                if (fmaxf(t0, x0) <= fminf(t1, x1)) f(bx, by, bz);
             }
+        }
+    }
 }
 
 __device__ inline bool set_insert(unsigned long long* set, unsigned long long key) {

@@ -18,12 +18,13 @@
 //      item bit; every touched slot joins the batch's union list once
 //   4. mark old footprints: set (item, old) bits on every slot of each item's
 //      current list, union as above
-//   5. net-delta: persistent warps take union blocks from a queue, recompute each
-//      (voxel, item) sample for the items whose bits are set, sum, and apply once
-//   6. D2H copy of the status word
-// Per-slot item bitmasks: [max_blocks][mw] words, old bits then new bits; the
-// net-delta kernel clears a slot's words after applying it, so the masks are all
-// zero between calls.
+//   5. net-delta: persistent warps take (union block, voxel group) units from a
+//      queue, recompute each (voxel, item) sample for the items whose bits are set,
+//      sum, and apply once
+//   6. clear the union slots' item bits and fresh flags
+//   7. D2H copy of the status word
+// Per-slot item bitmasks: [max_blocks][mw] words, old bits then new bits; step 6
+// zeroes them again, so the masks are all zero between calls.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -162,11 +163,14 @@ __device__ __forceinline__ void net_delta_group(const BatchItem* items, const in
     }
 }
 
+// Work unit u = (union block u / 4, voxel group u % 4): one warp, 128 voxels, four
+// per lane.  Units come from a queue in chunks of `grab`.
 template <bool F32>
 __global__ void net_delta_kernel(DevVolume V, const BatchItem* items, const BatchHeader* hdr, uint32_t* masks,
                                  int mw, const int32_t* ulist, int32_t* counters, int grab, uint32_t list_cap) {
     const int lane = threadIdx.x & 31;
     const uint32_t n_union = min((uint32_t)counters[0], V.max_blocks);
+    const uint32_t n_units = 4 * n_union;
     if (V.prof && blockIdx.x == 0 && threadIdx.x == 0) {
         unsigned long long pairs = 0;
         for (int i = 0; i < hdr->n; ++i)
@@ -178,86 +182,95 @@ __global__ void net_delta_kernel(DevVolume V, const BatchItem* items, const Batc
         uint32_t base = 0;
         if (lane == 0) base = (uint32_t)atomicAdd(&counters[1], grab);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_union) break;
-        const uint32_t end = min(base + (uint32_t)grab, n_union);
-        for (uint32_t u = base; u < end; ++u) {
-            const int32_t slot = ulist[u];
+        if (base >= n_units) break;
+        const uint32_t end = min(base + (uint32_t)grab, n_units);
+        for (uint32_t unit = base; unit < end; ++unit) {
+            const int32_t slot = ulist[unit >> 2];
+            const int g = unit & 3;
             const int4 c = V.coord[slot];
             const bool fresh = (V.flags[slot] & FLAG_FRESH) != 0;
-            uint32_t* mp = masks + (size_t)slot * mw;
+            const uint32_t* mp = masks + (size_t)slot * mw;
             const uint32_t mw0 = lane < mw ? mp[lane] : 0u;
             const uint32_t mw1 = lane + 32 < mw ? mp[lane + 32] : 0u;
-#pragma unroll 1
-            for (int g = 0; g < 4; ++g) {
-                int lx0, ly, lz;
-                lane_voxels(lane, g, lx0, ly, lz);
-                float aD[4] = {0.f, 0.f, 0.f, 0.f}, aW[4] = {0.f, 0.f, 0.f, 0.f};
-                float aC[4][3] = {};
-                bool touched = false;
-                net_delta_group<F32>(items, c, lx0, ly, lz, mw0, mw1, mw, aD, aW, aC, touched);
-                if (!touched && !fresh) continue;
-                const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
-                float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
-                if (!fresh) {
-                    Dv = *reinterpret_cast<const float4*>(V.D + off);
-                    Wv = *reinterpret_cast<const float4*>(V.W + off);
+            int lx0, ly, lz;
+            lane_voxels(lane, g, lx0, ly, lz);
+            float aD[4] = {0.f, 0.f, 0.f, 0.f}, aW[4] = {0.f, 0.f, 0.f, 0.f};
+            float aC[4][3] = {};
+            bool touched = false;
+            net_delta_group<F32>(items, c, lx0, ly, lz, mw0, mw1, mw, aD, aW, aC, touched);
+            if (!touched && !fresh) continue;
+            const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+            float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
+            if (!fresh) {
+                Dv = *reinterpret_cast<const float4*>(V.D + off);
+                Wv = *reinterpret_cast<const float4*>(V.W + off);
+            }
+            float* Dp = &Dv.x;
+            float* Wp = &Wv.x;
+            float Wn[4];
+            bool nz[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                Wn[j] = __fadd_rn(Wp[j], aW[j]);
+                nz[j] = Wn[j] != 0.f;
+            }
+            if (F32) {
+                const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) {
+                    float4 Cv = fresh ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                      : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
+                    float* Cp = &Cv.x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (aW[j] != 0.f || aC[j][ch] != 0.f)
+                            Cp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), Wn[j]) : 0.f;
+                    *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cv;
                 }
-                float* Dp = &Dv.x;
-                float* Wp = &Wv.x;
-                float Wn[4], inv_ok[4];
+            } else {
+                uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
+                if (!fresh) Cv = *reinterpret_cast<const uint4*>(V.C8 + off);
+                uint32_t* Cp = &Cv.x;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    Wn[j] = __fadd_rn(Wp[j], aW[j]);
-                    inv_ok[j] = Wn[j] != 0.f;
-                }
-                if (F32) {
-                    const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
+                    if (aW[j] == 0.f && aC[j][0] == 0.f && aC[j][1] == 0.f && aC[j][2] == 0.f) continue;
+                    if (!nz[j]) {
+                        Cp[j] = 0u;
+                        continue;
+                    }
+                    uint32_t out = 0;
 #pragma unroll
                     for (int ch = 0; ch < 3; ++ch) {
-                        float4 Cv = fresh ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                          : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
-                        float* Cp = &Cv.x;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (aW[j] != 0.f || aC[j][ch] != 0.f)
-                                Cp[j] = inv_ok[j] ? __fdiv_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), Wn[j]) : 0.f;
-                        *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cv;
+                        const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
+                        out |= u8_sat(__fdiv_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), Wn[j])) << (8 * ch);
                     }
-                } else {
-                    uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
-                    if (!fresh) Cv = *reinterpret_cast<const uint4*>(V.C8 + off);
-                    uint32_t* Cp = &Cv.x;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (aW[j] == 0.f && aC[j][0] == 0.f && aC[j][1] == 0.f && aC[j][2] == 0.f) continue;
-                        if (!inv_ok[j]) {
-                            Cp[j] = 0u;
-                            continue;
-                        }
-                        uint32_t out = 0;
-#pragma unroll
-                        for (int ch = 0; ch < 3; ++ch) {
-                            const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
-                            out |= u8_sat(__fdiv_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), Wn[j])) << (8 * ch);
-                        }
-                        Cp[j] = out;
-                    }
-                    *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
+                    Cp[j] = out;
                 }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (aW[j] == 0.f && aD[j] == 0.f) continue;
-                    Dp[j] = inv_ok[j] ? __fdiv_rn(__fmaf_rn(Dp[j], Wp[j], aD[j]), Wn[j]) : 0.f;
-                    Wp[j] = Wn[j];
-                }
-                *reinterpret_cast<float4*>(V.D + off) = Dv;
-                *reinterpret_cast<float4*>(V.W + off) = Wv;
+                *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
             }
-            __syncwarp();
-            if (lane < mw) mp[lane] = 0u;
-            if (lane + 32 < mw) mp[lane + 32] = 0u;
-            if (fresh && lane == 0) V.flags[slot] = 0u;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (aW[j] == 0.f && aD[j] == 0.f) continue;
+                Dp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Dp[j], Wp[j], aD[j]), Wn[j]) : 0.f;
+                Wp[j] = Wn[j];
+            }
+            *reinterpret_cast<float4*>(V.D + off) = Dv;
+            *reinterpret_cast<float4*>(V.W + off) = Wv;
         }
+    }
+}
+
+// After the net-delta update: zero the union slots' item bits and fresh flags, so
+// the masks are all zero between calls.
+__global__ void net_delta_clear_kernel(DevVolume V, uint32_t* masks, int mw, const int32_t* ulist,
+                                       const int32_t* counters) {
+    const uint32_t n_union = min((uint32_t)counters[0], V.max_blocks);
+    const size_t n = (size_t)n_union * mw;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int32_t slot = ulist[i / mw];
+        const int w = (int)(i % mw);
+        masks[(size_t)slot * mw + w] = 0u;
+        if (w == 0) V.flags[slot] = 0u;
     }
 }
 
@@ -347,13 +360,13 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
         *items_node = deps[0];
     }
     batch_init_kernel<<<4, 256, 0, s>>>(B->items_d, B->hdr_d, B->counters);
-    if (V->prof_on) cudaEventRecord(V->graph_ev[0], s);
+    if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[0], s, cudaEventRecordExternal);
     batch_alloc_kernel<<<V->num_sms * ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
         V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
-    if (V->prof_on) cudaEventRecord(V->graph_ev[1], s);
+    if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[1], s, cudaEventRecordExternal);
     batch_mark_old_kernel<<<V->num_sms * 8, 256, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist,
                                                          B->counters, V->p.max_blocks_per_keyframe);
-    if (V->prof_on) cudaEventRecord(V->graph_ev[2], s);
+    if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[2], s, cudaEventRecordExternal);
     const sc_batch_config& c = V->bcfg;
     const int grid = V->num_sms * ctas_per_sm_clamped(V, c);
     const uint32_t cap = V->p.max_blocks_per_keyframe;
@@ -363,7 +376,8 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
     else
         net_delta_kernel<false><<<grid, 32 * c.warps_per_cta, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw,
                                                                      B->ulist, B->counters, c.blocks_per_grab, cap);
-    if (V->prof_on) cudaEventRecord(V->graph_ev[3], s);
+    if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[3], s, cudaEventRecordExternal);
+    net_delta_clear_kernel<<<V->num_sms * 4, 256, 0, s>>>(V->dv, B->masks, B->mw, B->ulist, B->counters);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return cudaMemcpyAsync(V->h_status, V->status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
 }
@@ -439,7 +453,7 @@ int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_
     return SC_OK;
 }
 
-constexpr int GRAPH_KERNELS = 4;  // init, batched allocation, mark old, net-delta
+constexpr int GRAPH_KERNELS = 5;  // init, batched allocation, mark old, net-delta, clear
 
 int launch_and_check(sc_volume* V, cudaStream_t s) {
     SC_CUDA(cudaGraphLaunch(V->batch->exec, s));

@@ -248,27 +248,4 @@ __device__ inline int32_t find_slot(const DevVolume& V, unsigned long long key) 
     return s >= 0 ? s : -1;
 }
 
-// Closed segment [q0, q1] against the closed box [lo, hi]^3 (slab test).
-__device__ __forceinline__ bool seg_box(const float q0[3], const float q1[3], const float lo[3],
-                                        const float hi[3]) {
-    float tmin = 0.f, tmax = 1.f;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float d = q1[a] - q0[a];
-        if (d == 0.f) {
-            if (q0[a] < lo[a] || q0[a] > hi[a]) return false;
-            continue;
-        }
-        float t0 = (lo[a] - q0[a]) / d, t1 = (hi[a] - q0[a]) / d;
-        if (t0 > t1) {
-            const float t = t0;
-            t0 = t1;
-            t1 = t;
-        }
-        tmin = fmaxf(tmin, t0);
-        tmax = fminf(tmax, t1);
-    }
-    return tmin <= tmax;
-}
-
 }  // namespace sc

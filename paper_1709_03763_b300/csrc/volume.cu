@@ -103,80 +103,79 @@ __global__ void __launch_bounds__(ALLOC_THREADS) alloc_kernel(DevVolume V, KfCam
 
 // =================================================================== update ====
 
-constexpr int UPD_THREADS = 128;
+constexpr int UPD_THREADS = 128;  // one CTA (4 warps) per 8^3 block; a thread owns 4 voxels
 
-// One warp per block of the list; lane l owns voxels 4l..4l+3 (+128 g, g = 0..3).
-// The four samples of a group are computed first; the group's D / W / C are
-// only read and written when one of its voxels is updated (or the block is
-// fresh and must be zero-initialised).
+// Thread t of the CTA owns voxels 4t .. 4t+3 of the block (one float4 of each
+// field).  The four samples are computed first; the thread's D / W / C are only
+// read and written when one of its voxels is updated (or the block is fresh and
+// must be zero-initialised).  Persistent: CTAs stride over the list.
 template <int SIGN, bool F32>
 __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam k, const int32_t* list,
                                                              const int32_t* count_ptr, uint32_t cap) {
-    const int lane = threadIdx.x & 31;
+    const int t = threadIdx.x;
     const uint32_t n = min((uint32_t)*count_ptr, cap);
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    if (V.prof && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(V.prof, (unsigned long long)n);
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    if (V.prof && blockIdx.x == 0 && t == 0) atomicAdd(V.prof, (unsigned long long)n);
+    const int lx0 = (4 * t) & 7, ly = ((4 * t) >> 3) & 7, lz = (4 * t) >> 6;
+    for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         const int32_t slot = list[i];
         const int4 c = V.coord[slot];
-        const bool fresh = SIGN > 0 && (V.flags[slot] & FLAG_FRESH);
-#pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
-            int lx0, ly, lz;
-            lane_voxels(lane, g, lx0, ly, lz);
-            float d[4];
-            int pix[4];
-            bool up[4];
-            bool any = false;
+        bool fresh = false;
+        if (SIGN > 0) {
+            fresh = (V.flags[slot] & FLAG_FRESH) != 0;
+            __syncthreads();  // every thread has read the flag before it is cleared
+            if (fresh && t == 0) V.flags[slot] = 0;
+        }
+        float d[4];
+        int pix[4];
+        bool up[4];
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            up[j] = sample_voxel(k, 8 * c.x + lx0 + j, 8 * c.y + ly, 8 * c.z + lz, d[j], pix[j]);
+            any |= up[j];
+        }
+        if (!any && !fresh) continue;
+        const size_t off = (size_t)slot * NVOX + 4 * t;
+        float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
+        if (!fresh) {
+            Dv = *reinterpret_cast<const float4*>(V.D + off);
+            Wv = *reinterpret_cast<const float4*>(V.W + off);
+        }
+        float* Dp = &Dv.x;
+        float* Wp = &Wv.x;
+        if (F32) {
+            const size_t cb = (size_t)slot * 3 * NVOX + 4 * t;
+            float4 Cv[3];
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch)
+                Cv[ch] = fresh ? make_float4(0.f, 0.f, 0.f, 0.f)
+                               : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                up[j] = sample_voxel(k, 8 * c.x + lx0 + j, 8 * c.y + ly, 8 * c.z + lz, d[j], pix[j]);
-                any |= up[j];
-            }
-            if (!any && !fresh) continue;
-            const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
-            float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
-            if (!fresh) {
-                Dv = *reinterpret_cast<const float4*>(V.D + off);
-                Wv = *reinterpret_cast<const float4*>(V.W + off);
-            }
-            float* Dp = &Dv.x;
-            float* Wp = &Wv.x;
-            if (F32) {
-                const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
-                float4 Cv[3];
+                if (!up[j]) continue;
+                const uint32_t cc = __ldg(k.rgba + pix[j]);
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch)
-                    Cv[ch] = fresh ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                   : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (!up[j]) continue;
-                    const uint32_t cc = __ldg(k.rgba + pix[j]);
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch)
-                        (&Cv[ch].x)[j] = update_cf((&Cv[ch].x)[j], Wp[j], (float)((cc >> (8 * ch)) & 255u), SIGN);
-                    update_dw(Dp[j], Wp[j], d[j], SIGN);
-                }
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cv[ch];
-            } else {
-                uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
-                if (!fresh) Cv = *reinterpret_cast<const uint4*>(V.C8 + off);
-                uint32_t* Cp = &Cv.x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (!up[j]) continue;
-                    const uint32_t cc = __ldg(k.rgba + pix[j]);
-                    Cp[j] = update_c8(Cp[j], Wp[j], cc, SIGN);
-                    update_dw(Dp[j], Wp[j], d[j], SIGN);
-                }
-                *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
+                    (&Cv[ch].x)[j] = update_cf((&Cv[ch].x)[j], Wp[j], (float)((cc >> (8 * ch)) & 255u), SIGN);
+                update_dw(Dp[j], Wp[j], d[j], SIGN);
             }
-            *reinterpret_cast<float4*>(V.D + off) = Dv;
-            *reinterpret_cast<float4*>(V.W + off) = Wv;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cv[ch];
+        } else {
+            uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
+            if (!fresh) Cv = *reinterpret_cast<const uint4*>(V.C8 + off);
+            uint32_t* Cp = &Cv.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!up[j]) continue;
+                const uint32_t cc = __ldg(k.rgba + pix[j]);
+                Cp[j] = update_c8(Cp[j], Wp[j], cc, SIGN);
+                update_dw(Dp[j], Wp[j], d[j], SIGN);
+            }
+            *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
         }
-        if (fresh && lane == 0) V.flags[slot] = 0;
+        *reinterpret_cast<float4*>(V.D + off) = Dv;
+        *reinterpret_cast<float4*>(V.W + off) = Wv;
     }
 }
 
@@ -264,7 +263,7 @@ cudaError_t launch_alloc(sc_volume* V, const KfCam& cam, int32_t* list, int32_t*
 
 cudaError_t launch_update(sc_volume* V, const KfCam& cam, const int32_t* list, const int32_t* count, int sign,
                           cudaStream_t s) {
-    const int grid = grid_for(V, 16);
+    const int grid = grid_for(V, 16);  // 16 x 4 warps per SM, persistent over the list
     const uint32_t cap = V->p.max_blocks_per_keyframe;
     const bool f32 = V->p.colour_format == SC_RGB_F32;
     if (sign > 0) {

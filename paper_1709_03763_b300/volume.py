@@ -252,7 +252,7 @@ def fuse_frames_into_keyframe(depths: torch.Tensor, frame_poses, kf_pose, intr, 
         out_depth = torch.empty((H, W), dtype=torch.float32, device=depths.device)
     if out_weight is None:
         out_weight = torch.empty((H, W), dtype=torch.float32, device=depths.device)
-    pz = (Pose * n)(*[make_pose(frame_poses[i]) for i in range(n)])
+    pz = (Pose * n)(*[make_pose(p) for p in frame_poses])
     fp = FusionParams(float(disc_rel))
     check(lib().sc_fuse_frames_into_keyframe(_dev(depths, torch.float32, "depths"), pz, n,
                                              ctypes.byref(make_pose(kf_pose)), ctypes.byref(make_intrinsics(intr)),
