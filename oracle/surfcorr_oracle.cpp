@@ -58,7 +58,7 @@
 
 namespace {
 
-double g_tau_px = 1e-3;   // pixel-rounding margin (pixels)
+double g_tau_px = 5e-4;   // pixel-rounding margin (pixels)
 double g_tau_m = 1e-5;    // distance margin (metres)
 double g_tau_rel = 1e-6;  // relative margin for the discontinuity test
 
@@ -134,8 +134,9 @@ long round_half_up(double a, double* margin) {
 //   * Eq. 1: Z*(x*) <- (W*(x*) Z*(x*) + w_z Z*_p) / (W*(x*) + w_z);
 //            W*(x*) <- W*(x*) + w_z.
 //     Reading: no z-test; every warped sample is averaged into its pixel.
-// Z* and W* start at zero.  flag[x*] marks target pixels that a source pixel
-// with a marginal decision may land in (3x3 neighbourhood of its x*).
+// Z* and W* start at zero.  flag marks the target pixels a source pixel with a
+// marginal decision may land in: x* and, for a marginal rounding, the pixel across
+// the tie.
 extern "C" int or_fuse(const float* depths, const float* poses, int n, const float* kf_pose,
                        double fx, double fy, double cx, double cy, int W, int H, double disc_rel,
                        double* Zs, double* Ws, uint8_t* flag) {
@@ -173,13 +174,19 @@ extern "C" int or_fuse(const float* depths, const float* poses, int n, const flo
                 if (std::fabs(ps[2]) < g_tau_m) marginal = true;
                 if (!(ps[2] > 0.0)) continue;
                 double mu_, mv_;
-                long xs = round_half_up(K.fx * ps[0] / ps[2] + K.cx, &mu_);
-                long ys = round_half_up(K.fy * ps[1] / ps[2] + K.cy, &mv_);
+                const double uf = K.fx * ps[0] / ps[2] + K.cx, vf = K.fy * ps[1] / ps[2] + K.cy;
+                long xs = round_half_up(uf, &mu_);
+                long ys = round_half_up(vf, &mv_);
                 if (mu_ < g_tau_px || mv_ < g_tau_px) marginal = true;
                 if (marginal) {
-                    for (long dy = -1; dy <= 1; ++dy)
-                        for (long dx = -1; dx <= 1; ++dx) {
-                            long yy = ys + dy, xx = xs + dx;
+                    // the target pixels a float32 evaluation could pick: x* and, on each axis
+                    // whose rounding is marginal, the neighbour across the tie
+                    const long ax = mu_ < g_tau_px ? (uf + 0.5 - std::floor(uf + 0.5) < 0.5 ? xs - 1 : xs + 1) : xs;
+                    const long ay = mv_ < g_tau_px ? (vf + 0.5 - std::floor(vf + 0.5) < 0.5 ? ys - 1 : ys + 1) : ys;
+                    const long cxs[2] = {xs, ax}, cys[2] = {ys, ay};
+                    for (int i = 0; i < 2; ++i)
+                        for (int j = 0; j < 2; ++j) {
+                            const long yy = cys[i], xx = cxs[j];
                             if (yy >= 0 && yy < H && xx >= 0 && xx < W) flag[yy * W + xx] = 1;
                         }
                 }

@@ -35,14 +35,16 @@ struct Corners {
 };
 
 __device__ inline bool point_corners(const DevVolume& V, float s, const float* p, Corners& c, float& Dt) {
+    // grid coordinate in double: at ~10^3 voxels from the origin a float fraction
+    // would carry 1e-4-voxel errors into the interpolation weights
     int i0[3];
     float f[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const float g = __fdiv_rn(p[a], s);
-        const float fl = floorf(g);
+        const double g = (double)p[a] / (double)s;
+        const double fl = floor(g);
         i0[a] = (int)fl;
-        f[a] = __fsub_rn(g, fl);
+        f[a] = (float)(g - fl);
     }
     int32_t last_slot = -1;
     int lbx = 0x7fffffff, lby = 0, lbz = 0;
