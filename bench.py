@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=20, help="keyframe re-integrations the oracle times")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="run --steps steps between cudaProfilerStart/Stop and exit (for ncu "
+                         "--profile-from-start off); prints only the timing")
+    ap.add_argument("--keyframes", type=int, default=60, help="keyframes of the workload (small ncu cases)")
+    ap.add_argument("--max-blocks", type=int, default=1 << 21)
     return ap.parse_args()
 
 
@@ -159,10 +164,13 @@ def max_over_ranks(x, ws):
 
 # --------------------------------------------------------------------------------------
 
-def make_workload(device):
+def make_workload(device, keyframes=60):
     import torch
     from paper_1709_03763_b300 import synthetic
-    w = synthetic.workload_kinect(device=device, n_frames=N_FRAMES, kappa=KAPPA)
+    w = synthetic.workload_kinect(device=device, n_frames=N_FRAMES, kappa=KAPPA, render_frames=keyframes * KAPPA)
+    w.kf_poses = w.kf_poses[:keyframes]
+    w.new_poses = w.new_poses[:keyframes]
+    w.kf_rgba = w.kf_rgba[:keyframes].contiguous()
     pts = synthetic.surface_points(w.scene, N_POINTS, 4, lo=np.array([0.0, 0.0, 0.0]),
                                    hi=np.array([10.0, 8.0, 3.0]))
     w.extra["points"] = torch.tensor(pts, dtype=torch.float32, device=device)
@@ -176,7 +184,7 @@ class Pipeline:
         import torch
         self.w = w
         self.V = vol
-        K = N_FRAMES // KAPPA
+        K = len(w.kf_poses)
         self.K = K
         dev = w.frames_depth.device
         self.kf_depth = torch.empty((K, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
@@ -192,14 +200,19 @@ class Pipeline:
         self.grad_D = vol.grad_buffer()
 
     def fuse(self):
-        from paper_1709_03763_b300 import fuse_frames_into_keyframe
+        """Eq. 1 for all keyframes in one call (KF_CONST: frames k*10 .. k*10+9 -> keyframe k)."""
+        from paper_1709_03763_b300 import fuse_keyframes
         w = self.w
-        for k in range(self.K):
-            s = k * KAPPA
-            fuse_frames_into_keyframe(w.frames_depth[s:s + KAPPA], self.frame_poses[s:s + KAPPA],
-                                      self.frame_poses[s], self.intr, 0.1, self.kf_depth[k], self.kf_weight[k])
+        nf = self.K * KAPPA
+        fuse_keyframes(w.frames_depth[:nf], self.frame_poses[:nf], [f // KAPPA for f in range(nf)],
+                       self.frame_poses[:nf:KAPPA], self.intr, 0.1, self.kf_depth, self.kf_weight)
 
     def integrate(self):
+        """Reset, then integrate every keyframe at its drifted pose (one graph launch)."""
+        self.V.reset()
+        self.V.integrate_many(self.ids, self.kf_depth, self.kf_rgba, self.drift, self.intr)
+
+    def integrate_plain(self):
         self.V.reset()
         for k in range(self.K):
             self.V.integrate(k, self.kf_depth[k], self.kf_rgba[k], self.intr, self.drift[k])
@@ -343,16 +356,30 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
 
     t_setup = time.perf_counter()
-    w = make_workload(dev)
-    V = Volume(w.voxel_size, w.trunc, w.n_buckets, bucket_size=4, max_blocks=1 << 21, colour="rgba8",
+    w = make_workload(dev, args.keyframes)
+    V = Volume(w.voxel_size, w.trunc, w.n_buckets, bucket_size=4, max_blocks=args.max_blocks, colour="rgba8",
                max_keyframes=64, max_blocks_per_keyframe=1 << 17, max_batch=64)
     P = Pipeline(w, V)
-    P.capacity = 1 << 21
+    P.capacity = args.max_blocks
     P.fuse()
     P.integrate()
     torch.cuda.synchronize()
     cfg, tune_ms = V.autotune_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true, P.intr)
     setup_s = time.perf_counter() - t_setup
+
+    if args.profile_region:
+        for _ in range(args.warmup):
+            P.step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            P.step()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_region_steps": args.steps, "keyframes": P.K,
+                          "ms_per_step_host": (time.perf_counter() - t0) * 1000 / args.steps}), flush=True)
+        return
 
     # ---- the timed whole-path step
     L0 = lib().sc_kernel_launches()
@@ -383,7 +410,7 @@ def main():
     # ---- breakdown: the update alone, batched vs plain; per-kernel profile of one step
     upd_batched_ms = update_only_timing(P, 5, True)
     upd_plain_ms = update_only_timing(P, 5, False)
-    V.set_profiling(True)
+    # per-stage device time of one step (events, no profiling)
     torch.cuda.synchronize()
     s = torch.cuda.current_stream()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
@@ -399,29 +426,44 @@ def main():
     P.extract()
     ev[5].record(s)
     torch.cuda.synchronize()
-    prof = V.profile()
     stage = {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(["fuse", "integrate", "batched_update",
                                                                       "loss_adjoint", "extract"])}
+    # per-kernel profiles (library events; graph event nodes inside the batch graph)
+    P.integrate()
+    V.set_profiling(True)
+    P.update_batched()
+    prof_upd = V.profile()
+    V.set_profiling(True)
+    P.integrate()
+    prof_int = V.profile()
+    V.set_profiling(True)
+    P.integrate_plain()
+    prof_plain = V.profile()
     V.set_profiling(False)
 
     peak, peak_kind = peaks()
-    # candidate dominant kernels with their algorithmic bytes per launch
+    # kernels with their per-step time and algorithmic bytes per launch
     kernels = {}
-    if prof["update_launches"]:
-        nb = prof["update_blocks"] / prof["update_launches"]
-        kernels["update_voxels"] = (prof["update_ms"] / prof["update_launches"],
-                                    nb * 512 * VOXEL_BYTES_RW + IMG_BYTES + nb * 32, prof["update_ms"])
-    if prof["batch_launches"]:
-        u = prof["batch_union_blocks"] / prof["batch_launches"]
-        kernels["net_delta"] = (prof["batch_net_ms"] / prof["batch_launches"],
-                                u * 512 * VOXEL_BYTES_RW + P.K * IMG_BYTES + prof["batch_pairs"] * 4,
-                                prof["batch_net_ms"])
+    if prof_plain["update_launches"]:
+        nb = prof_plain["update_blocks"] / prof_plain["update_launches"]
+        kernels["update_voxels (plain integrate)"] = (prof_plain["update_ms"] / prof_plain["update_launches"],
+                                                      nb * 512 * VOXEL_BYTES_RW + IMG_BYTES + nb * 32, 0.0)
+    for name, pr in (("net_delta (pose update)", prof_upd), ("net_delta (integration)", prof_int)):
+        if pr["batch_launches"]:
+            u = pr["batch_union_blocks"] / pr["batch_launches"]
+            kernels[name] = (pr["batch_net_ms"] / pr["batch_launches"],
+                             u * 512 * VOXEL_BYTES_RW + P.K * IMG_BYTES + pr["batch_pairs"] * 4 / pr["batch_launches"],
+                             pr["batch_net_ms"])
+            kernels[name.replace("net_delta", "batch_alloc")] = (
+                pr["batch_alloc_ms"] / pr["batch_launches"], P.K * 640 * 480 * 4 + u * 32, pr["batch_alloc_ms"])
     dom = max(kernels, key=lambda k: kernels[k][2])
     t_ms, bytes_, _ = kernels[dom]
     achieved = bytes_ / (t_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_launch": bytes_, "ms_per_launch": t_ms}
+                "algorithmic_bytes_per_launch": bytes_, "ms_per_launch": t_ms,
+                "all": {k: {"ms_per_launch": v[0], "GBps": v[1] / (v[0] / 1000.0) / 1e9} for k, v in kernels.items()}}
+    prof = {"update": prof_upd, "integrate": prof_int, "plain_integrate": prof_plain}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -445,7 +487,7 @@ def main():
             "update_only": {"batched_ms": upd_batched_ms, "plain_ms": upd_plain_ms,
                             "batched_reint_per_s": P.K / (upd_batched_ms / 1000.0),
                             "plain_reint_per_s": P.K / (upd_plain_ms / 1000.0),
-                            "union_blocks": prof["batch_union_blocks"], "pairs": prof["batch_pairs"]},
+                            "union_blocks": prof_upd["batch_union_blocks"], "pairs": prof_upd["batch_pairs"]},
             "stage_ms": stage,
             "profile": prof,
             "roofline": roofline,

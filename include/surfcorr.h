@@ -160,6 +160,16 @@ int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses
                                  const sc_fusion_params* fusion, float* kf_depth, float* kf_weight,
                                  sc_stream stream);
 
+/* Eq. 1 for many keyframes in one call: frame f (device depths [n_frames][H][W],
+ * host pose frame_poses[f]) is fused into keyframe frame_kf[f] (host, 0 <= frame_kf[f]
+ * < n_kf) at pose kf_poses[frame_kf[f]] (host [n_kf]).  Outputs kf_depth and
+ * kf_weight are device [n_kf][H][W], overwritten.  Same per-keyframe result as
+ * sc_fuse_frames_into_keyframe on each keyframe's frames (up to float summation
+ * order); one fusion launch per 64 frames and one normalisation launch. */
+int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n_frames,
+                      const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* intr,
+                      const sc_fusion_params* fusion, float* kf_depth, float* kf_weight, sc_stream stream);
+
 /* ------------------------------------------------ integration (plain path) ---- */
 
 /* Integrate keyframe kf_id at pose T (Section 3 "SDF volume": voxel blocks are
@@ -198,6 +208,16 @@ int sc_deintegrate_keyframe(sc_volume* vol, int32_t kf_id, const float* depth, c
  * distinct and integrated.  Synchronises the stream to read the device status. */
 int sc_reintegrate_batch(sc_volume* vol, const sc_reint_item* items, int32_t n, const sc_intrinsics* intr,
                          sc_stream stream);
+
+/* Integrate n keyframes that are not integrated yet (Section 3 "SDF volume") in
+ * one graph launch: the allocation of every keyframe's blocks, then one
+ * read-modify-write per touched voxel with the keyframes' summed contributions.
+ * Equal to n sc_integrate_keyframe calls in order, up to float summation order.
+ * kf_ids, depths (device pointers), rgbas (device pointers), poses: host [n],
+ * 1 <= n <= max_batch, ids distinct.  Synchronises the stream. */
+int sc_integrate_keyframes(sc_volume* vol, const int32_t* kf_ids, const float* const* depths,
+                           const uint8_t* const* rgbas, const sc_pose* poses, int32_t n, const sc_intrinsics* intr,
+                           sc_stream stream);
 
 /* Set / read the launch configuration of sc_reintegrate_batch. */
 int sc_set_batch_config(sc_volume* vol, const sc_batch_config* cfg);

@@ -715,12 +715,17 @@ struct DOverlay {
     const std::unordered_map<int64_t, std::vector<double>>* over = nullptr;
 };
 
-bool voxel_at(const Vol& V, const DOverlay& ov, long ix, long iy, long iz, double* D, double* W) {
+bool voxel_at(const Vol& V, const DOverlay& ov, long ix, long iy, long iz, double* D, double* W,
+              bool* flagged = nullptr) {
     long bx = floor_div(ix, BS), by = floor_div(iy, BS), bz = floor_div(iz, BS);
     int64_t key = pack(bx, by, bz);
     auto it = V.blocks.find(key);
-    if (it == V.blocks.end()) return false;
+    if (it == V.blocks.end()) {
+        if (flagged && V.ghosts.count(key)) *flagged = true;
+        return false;
+    }
     int vi = (int)(ix - bx * BS) + BS * (int)(iy - by * BS) + BS * BS * (int)(iz - bz * BS);
+    if (flagged && (it->second.bflag || it->second.vflag[vi] || V.ghosts.count(key))) *flagged = true;
     *W = it->second.W[vi];
     *D = it->second.D[vi];
     if (ov.over) {
@@ -738,6 +743,8 @@ struct PointEval {
     double beta[8];
 };
 
+// marginal: the floor of a grid coordinate is within 1e-6 of a tie, or one of the
+// 8 corners (up to the first unobserved one) has a marginal decision
 PointEval eval_point(const Vol& V, const DOverlay& ov, const double* p) {
     PointEval E{};
     E.valid = false;
@@ -759,7 +766,8 @@ PointEval eval_point(const Vol& V, const DOverlay& ov, const double* p) {
         E.iz[c] = i0[2] + oz;
         E.beta[c] = (ox ? f[0] : 1 - f[0]) * (oy ? f[1] : 1 - f[1]) * (oz ? f[2] : 1 - f[2]);
         double D, W;
-        if (!voxel_at(V, ov, E.ix[c], E.iy[c], E.iz[c], &D, &W)) return E;
+        // a corner with a marginal decision may be observed on one side only
+        if (!voxel_at(V, ov, E.ix[c], E.iy[c], E.iz[c], &D, &W, &E.marginal)) return E;
         acc += E.beta[c] * D;
     }
     E.valid = true;

@@ -83,9 +83,12 @@ SIGNATURES = {
     "sc_status_string": (ctypes.c_char_p, [c_i32]),
     "sc_fuse_frames_into_keyframe": (c_i32, [c_p, P(Pose), c_i32, P(Pose), P(Intrinsics), P(FusionParams),
                                              c_p, c_p, c_p]),
+    "sc_fuse_keyframes": (c_i32, [c_p, P(Pose), P(c_i32), c_i32, P(Pose), c_i32, P(Intrinsics), P(FusionParams),
+                                  c_p, c_p, c_p]),
     "sc_integrate_keyframe": (c_i32, [c_p, c_i32, c_p, c_p, P(Intrinsics), P(Pose), c_p]),
     "sc_deintegrate_keyframe": (c_i32, [c_p, c_i32, c_p, c_p, P(Intrinsics), P(Pose), c_p]),
     "sc_reintegrate_batch": (c_i32, [c_p, P(ReintItem), c_i32, P(Intrinsics), c_p]),
+    "sc_integrate_keyframes": (c_i32, [c_p, P(c_i32), P(c_p), P(c_p), P(Pose), c_i32, P(Intrinsics), c_p]),
     "sc_set_batch_config": (c_i32, [c_p, P(BatchConfig)]),
     "sc_get_batch_config": (c_i32, [c_p, P(BatchConfig)]),
     "sc_autotune_batch": (c_i32, [c_p, P(ReintItem), c_i32, P(Intrinsics), c_p, P(BatchConfig), P(c_f)]),

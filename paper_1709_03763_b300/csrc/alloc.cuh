@@ -18,10 +18,11 @@
 
 namespace sc {
 
-constexpr int ALLOC_TX = 32;
-constexpr int ALLOC_TY = 8;
-constexpr int ALLOC_THREADS = ALLOC_TX * ALLOC_TY;
-constexpr int SET_SIZE = 512;        // unique blocks a tile may touch before overflow handling
+constexpr int ALLOC_TX = 32;         // pixel tile 32 x 32, one CTA of 256 threads,
+constexpr int ALLOC_TY = 32;         // 4 pixels (rows r, r+8, r+16, r+24) per thread
+constexpr int ALLOC_THREADS = 256;
+constexpr int ALLOC_PPT = ALLOC_TX * ALLOC_TY / ALLOC_THREADS;
+constexpr int SET_SIZE = 1024;       // unique blocks a tile may touch before overflow handling
 constexpr int MAX_BLOCK_SPAN = 16;   // per-axis candidate blocks of one band segment
 constexpr float MAX_DEPTH = 1.0e4f;  // metres; larger depth values are treated as invalid
 
@@ -132,6 +133,7 @@ __device__ inline void publish(const DevVolume& V, int entry, unsigned long long
 struct AllocShared {
     unsigned long long set[SET_SIZE];
     int ent[SET_SIZE];
+    int slot[SET_SIZE];  // pool slot of entries this CTA created, else -1
     int idx[SET_SIZE];   // new entries (phase B), then list appends (phase C)
     int uidx[SET_SIZE];  // union appends (batches)
     int n_new, n_app, n_uapp, overflow;
@@ -148,6 +150,7 @@ __device__ inline void append_one(const DevVolume& V, int32_t* list, int32_t* co
 
 // Process tile (tx, ty) of keyframe camera k.  The Sink provides
 //   bool list_first(slot)  : true the first time this keyframe reaches slot
+//   void mark_new(slot)    : record that this keyframe has listed a slot just created
 //   bool union_first(slot) : true the first time the batch reaches slot (batches only)
 //   int32_t* list, *count; uint32_t cap; int32_t* ulist, *ucount; uint32_t ucap
 // Must be called by all ALLOC_THREADS threads of the CTA.
@@ -164,12 +167,14 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     __syncthreads();
 
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
-    const int v = ty * ALLOC_TY + (tid / ALLOC_TX);
-    float Z = 0.f;
-    if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
-    const bool valid = Z > 0.f && Z < MAX_DEPTH;
+    const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
     bool my_ovf = false;
-    if (valid) {
+#pragma unroll 1
+    for (int r = 0; r < ALLOC_PPT; ++r) {
+        const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
+        float Z = 0.f;
+        if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
+        if (!(Z > 0.f && Z < MAX_DEPTH)) continue;
         for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
             if (!coord_ok(bx, by, bz)) {
                 set_status(V.status, SC_ERR_INVALID_ARG);
@@ -181,9 +186,10 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     if (my_ovf) sh.overflow = 1;
     __syncthreads();
 
-    // B: claim each unique key
+    // B: claim each unique key; the tile's new entries get consecutive slots
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) {
         sh.ent[i] = -1;
+        sh.slot[i] = -1;
         const unsigned long long key = sh.set[i];
         if (key == KEY_EMPTY) continue;
         bool won;
@@ -195,16 +201,30 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     __syncthreads();
     for (int i = tid; i < sh.n_new; i += ALLOC_THREADS) {
         const int j = sh.idx[i];
-        publish(V, sh.ent[j], sh.set[j], sh.pool_base + (uint32_t)i);
+        const uint32_t slot = sh.pool_base + (uint32_t)i;
+        // nobody else can list a slot before it is published: mark it for this
+        // keyframe with a plain store, then publish
+        if (slot < V.max_blocks) {
+            sk.mark_new(slot);
+            sh.slot[j] = (int)slot;
+        }
+        publish(V, sh.ent[j], sh.set[j], slot);
     }
     __syncthreads();
 
     // C: dedupe and append
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) {
         if (sh.ent[i] < 0) continue;
-        const int32_t slot = entry_slot(V, sh.ent[i]);
-        if (slot < 0) continue;
-        if (sk.list_first(slot)) sh.idx[atomicAdd(&sh.n_app, 1)] = slot;
+        int32_t slot = sh.slot[i];
+        bool first;
+        if (slot >= 0) {
+            first = true;  // created here
+        } else {
+            slot = entry_slot(V, sh.ent[i]);
+            if (slot < 0) continue;
+            first = sk.list_first(slot);
+        }
+        if (first) sh.idx[atomicAdd(&sh.n_app, 1)] = slot;
         if (Sink::kUnion && sk.union_first(slot)) sh.uidx[atomicAdd(&sh.n_uapp, 1)] = slot;
     }
     __syncthreads();
@@ -229,19 +249,25 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     // D: keys that did not fit in the shared set
     const bool ovf = sh.overflow != 0;
     if (ovf && my_ovf) {
-        for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
-            if (!coord_ok(bx, by, bz)) return;
-            const unsigned long long key = pack_key(bx, by, bz);
-            if (set_contains(sh.set, key)) return;
-            bool won;
-            const int e = hash_claim(V, key, &won);
-            if (e < 0) return;
-            if (won) publish(V, e, key, atomicAdd(V.pool_count, 1u));
-            const int32_t slot = entry_slot(V, e);
-            if (slot < 0) return;
-            if (sk.list_first(slot)) append_one(V, sk.list, sk.count, sk.cap, slot);
-            if (Sink::kUnion && sk.union_first(slot)) append_one(V, sk.ulist, sk.ucount, sk.ucap, slot);
-        });
+        for (int r = 0; r < ALLOC_PPT; ++r) {
+            const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
+            float Z = 0.f;
+            if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
+            if (!(Z > 0.f && Z < MAX_DEPTH)) continue;
+            for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
+                if (!coord_ok(bx, by, bz)) return;
+                const unsigned long long key = pack_key(bx, by, bz);
+                if (set_contains(sh.set, key)) return;
+                bool won;
+                const int e = hash_claim(V, key, &won);
+                if (e < 0) return;
+                if (won) publish(V, e, key, atomicAdd(V.pool_count, 1u));
+                const int32_t slot = entry_slot(V, e);
+                if (slot < 0) return;
+                if (sk.list_first(slot)) append_one(V, sk.list, sk.count, sk.cap, slot);
+                if (Sink::kUnion && sk.union_first(slot)) append_one(V, sk.ulist, sk.ucount, sk.ucap, slot);
+            });
+        }
     }
     __syncthreads();  // shared state is reused by the CTA's next tile
 }
@@ -257,6 +283,7 @@ struct PlainSink {
     int32_t* ucount;
     uint32_t ucap;
     __device__ bool list_first(int32_t slot) { return atomicExch(&stamp[slot], call_id) != call_id; }
+    __device__ void mark_new(int32_t slot) { stamp[slot] = call_id; }
     __device__ bool union_first(int32_t) { return false; }
 };
 

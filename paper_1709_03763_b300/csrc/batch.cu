@@ -71,6 +71,8 @@ struct BatchSink {
     __device__ bool list_first(int32_t slot) {
         return !(atomicOr(masks + (size_t)slot * mw, bit) & bit);
     }
+    // other items may set their bits on a new slot as soon as it is published
+    __device__ void mark_new(int32_t slot) { atomicOr(masks + (size_t)slot * mw, bit); }
     __device__ bool union_first(int32_t slot) { return atomicExch(&stamp[slot], call_id) != call_id; }
 };
 
@@ -278,6 +280,7 @@ __global__ void net_delta_clear_kernel(DevVolume V, uint32_t* masks, int mw, con
 
 struct BatchState {
     int mw = 0;
+    int32_t* zero = nullptr;  // a device word holding 0: the old-list length of integrate-only items
     uint32_t* masks = nullptr;
     int32_t* ulist = nullptr;
     int32_t* counters = nullptr;
@@ -303,6 +306,7 @@ void batch_destroy(sc_volume* V) {
     if (B->masks) cudaFree(B->masks);
     if (B->ulist) cudaFree(B->ulist);
     if (B->counters) cudaFree(B->counters);
+    if (B->zero) cudaFree(B->zero);
     if (B->items_d) cudaFree(B->items_d);
     if (B->hdr_d) cudaFree(B->hdr_d);
     if (B->items_h) cudaFreeHost(B->items_h);
@@ -323,6 +327,8 @@ int batch_init(sc_volume* V) {
     SC_CUDA(cudaMemset(B->masks, 0, mbytes));
     SC_CUDA(cudaMalloc((void**)&B->ulist, (size_t)V->p.max_blocks * sizeof(int32_t)));
     SC_CUDA(cudaMalloc((void**)&B->counters, 4 * sizeof(int32_t)));
+    SC_CUDA(cudaMalloc((void**)&B->zero, sizeof(int32_t)));
+    SC_CUDA(cudaMemset(B->zero, 0, sizeof(int32_t)));
     SC_CUDA(cudaMalloc((void**)&B->items_d, (size_t)V->p.max_batch * sizeof(BatchItem)));
     SC_CUDA(cudaMalloc((void**)&B->hdr_d, sizeof(BatchHeader)));
     SC_CUDA(cudaMallocHost((void**)&B->items_h, (size_t)V->p.max_batch * sizeof(BatchItem)));
@@ -411,32 +417,47 @@ int ensure_graph(sc_volume* V) {
     return SC_OK;
 }
 
-int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_intrinsics* K) {
+// One batch item as the host sees it; old == nullptr: integrate only (the keyframe is
+// not integrated and has no old footprint).
+struct ItemSpec {
+    int32_t kf_id;
+    const float* depth;
+    const uint8_t* rgba;
+    const sc_pose* oldp;
+    const sc_pose* newp;
+};
+
+bool pose_finite(const sc_pose* p) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 4; ++c)
+            if (!std::isfinite(p->m[r][c])) return false;
+    return true;
+}
+
+int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intrinsics* K) {
     if (!V || !items || n < 1 || n > V->p.max_batch || !intrinsics_ok(K)) return SC_ERR_INVALID_ARG;
     std::vector<uint8_t> seen(V->p.max_keyframes, 0);
     for (int i = 0; i < n; ++i) {
-        const sc_reint_item& it = items[i];
+        const ItemSpec& it = items[i];
         if (it.kf_id < 0 || it.kf_id >= V->p.max_keyframes || seen[it.kf_id]) return SC_ERR_INVALID_ARG;
         if (!it.depth || !it.rgba || ((uintptr_t)it.depth & 15) || ((uintptr_t)it.rgba & 15))
             return SC_ERR_INVALID_ARG;
-        for (int r = 0; r < 3; ++r)
-            for (int c = 0; c < 4; ++c)
-                if (!std::isfinite(it.old_pose.m[r][c]) || !std::isfinite(it.new_pose.m[r][c]))
-                    return SC_ERR_INVALID_ARG;
+        if (!it.newp || !pose_finite(it.newp) || (it.oldp && !pose_finite(it.oldp))) return SC_ERR_INVALID_ARG;
         seen[it.kf_id] = 1;
-        if (!V->integrated[it.kf_id]) return SC_ERR_NOT_INTEGRATED;
+        if (it.oldp && !V->integrated[it.kf_id]) return SC_ERR_NOT_INTEGRATED;
+        if (!it.oldp && V->integrated[it.kf_id]) return SC_ERR_ALREADY_INTEGRATED;
     }
     int rc = batch_init(V);
     if (rc) return rc;
     BatchState* B = V->batch;
     for (int i = 0; i < n; ++i) {
-        const sc_reint_item& it = items[i];
+        const ItemSpec& it = items[i];
         BatchItem& b = B->items_h[i];
         const int cur = V->cur[it.kf_id];
-        b.oldc = make_cam(V, K, &it.old_pose, it.depth, it.rgba);
-        b.newc = make_cam(V, K, &it.new_pose, it.depth, it.rgba);
+        b.oldc = make_cam(V, K, it.oldp ? it.oldp : it.newp, it.depth, it.rgba);
+        b.newc = make_cam(V, K, it.newp, it.depth, it.rgba);
         b.old_list = list_ptr(V, it.kf_id, cur);
-        b.old_count = count_ptr(V, it.kf_id, cur);
+        b.old_count = it.oldp ? count_ptr(V, it.kf_id, cur) : B->zero;
         b.new_list = list_ptr(V, it.kf_id, 1 - cur);
         b.new_count = count_ptr(V, it.kf_id, 1 - cur);
     }
@@ -451,6 +472,14 @@ int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_
     SC_CUDA(cudaGraphExecMemcpyNodeSetParams1D(B->exec, B->items_node, B->items_d, B->items_h,
                                                (size_t)n * sizeof(BatchItem), cudaMemcpyHostToDevice));
     return SC_OK;
+}
+
+int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_intrinsics* K) {
+    if (!items || n < 1) return SC_ERR_INVALID_ARG;
+    std::vector<ItemSpec> sp(n);
+    for (int i = 0; i < n; ++i)
+        sp[i] = ItemSpec{items[i].kf_id, items[i].depth, items[i].rgba, &items[i].old_pose, &items[i].new_pose};
+    return prepare_specs(V, sp.data(), n, K);
 }
 
 constexpr int GRAPH_KERNELS = 5;  // init, batched allocation, mark old, net-delta, clear
@@ -485,6 +514,24 @@ extern "C" int sc_reintegrate_batch(sc_volume* V, const sc_reint_item* items, in
     rc = launch_and_check(V, s);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) V->cur[items[i].kf_id] ^= 1;
+    return SC_OK;
+}
+
+extern "C" int sc_integrate_keyframes(sc_volume* V, const int32_t* kf_ids, const float* const* depths,
+                                      const uint8_t* const* rgbas, const sc_pose* poses, int32_t n,
+                                      const sc_intrinsics* K, sc_stream stream) {
+    if (!V || !kf_ids || !depths || !rgbas || !poses || n < 1) return SC_ERR_INVALID_ARG;
+    std::vector<ItemSpec> sp(n);
+    for (int i = 0; i < n; ++i) sp[i] = ItemSpec{kf_ids[i], depths[i], rgbas[i], nullptr, &poses[i]};
+    int rc = prepare_specs(V, sp.data(), n, K);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = launch_and_check(V, s);
+    if (rc) return rc;
+    for (int i = 0; i < n; ++i) {
+        V->cur[kf_ids[i]] ^= 1;
+        V->integrated[kf_ids[i]] = 1;
+    }
     return SC_OK;
 }
 

@@ -13,22 +13,38 @@
 namespace {
 
 constexpr int FUSE_MAX_FRAMES = 64;  // frames per launch (kernel parameter space)
+
+// a*b - c*d with one rounding error (fma-compensated, W. Kahan): the normal's
+// components cancel strongly for surfaces seen at grazing angles
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = c * d;
+    const float e = fmaf(-c, d, w);
+    const float f = fmaf(a, b, -w);
+    return f + e;
+}
 constexpr int FUSE_TX = 32, FUSE_TY = 8;
 
 struct FuseFrame {
     float R[9];  // keyframe_from_frame rotation  R*^T R_i
     float t[3];  // keyframe_from_frame translation R*^T (t_i - t*)
+    int kf;      // output keyframe image
 };
 
 struct FuseArgs {
     FuseFrame f[FUSE_MAX_FRAMES];
 };
 
+struct FuseCam {
+    float fx, fy, cx, cy, ifx, ify;  // ifx = 1/fx, ify = 1/fy
+    int W, H;
+    float disc_rel;
+};
+
 __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __restrict__ depths, FuseArgs a,
-                                                                 float fx, float fy, float cx, float cy, int W,
-                                                                 int H, float disc_rel, float* S, float* Wsum) {
+                                                                 FuseCam c, float* S, float* Wsum) {
     const int u = blockIdx.x * FUSE_TX + threadIdx.x;
     const int v = blockIdx.y * FUSE_TY + threadIdx.y;
+    const int W = c.W, H = c.H;
     if (u < 1 || v < 1 || u >= W - 1 || v >= H - 1) return;  // border pixels have no full neighbourhood
     const FuseFrame& F = a.f[blockIdx.z];
     const float* Z = depths + (size_t)blockIdx.z * W * H;
@@ -37,33 +53,35 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     if (!(z > 0.f)) return;
     const float zl = __ldg(Z + p - 1), zr = __ldg(Z + p + 1), zu = __ldg(Z + p - W), zd = __ldg(Z + p + W);
     if (!(zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f)) return;
-    const float lim = disc_rel * z;
+    const float lim = c.disc_rel * z;
     if (fabsf(zl - z) > lim || fabsf(zr - z) > lim || fabsf(zu - z) > lim || fabsf(zd - z) > lim) return;
     // warp into the keyframe
-    const float xn = (u - cx) / fx, yn = (v - cy) / fy;
+    const float xn = (u - c.cx) * c.ifx, yn = (v - c.cy) * c.ify;
     const float P[3] = {xn * z, yn * z, z};
     float ps[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) ps[r] = fmaf(F.R[3 * r], P[0], fmaf(F.R[3 * r + 1], P[1], fmaf(F.R[3 * r + 2], P[2], F.t[r])));
     if (!(ps[2] > 0.f)) return;
-    const float uu = fx * ps[0] / ps[2] + cx + 0.5f;
-    const float vv = fy * ps[1] / ps[2] + cy + 0.5f;
+    const float rz = __frcp_rn(ps[2]);
+    const float uu = fmaf(c.fx * ps[0], rz, c.cx) + 0.5f;
+    const float vv = fmaf(c.fy * ps[1], rz, c.cy) + 0.5f;
     if (!(uu >= 0.f && uu < (float)W && vv >= 0.f && vv < (float)H)) return;
-    const size_t q = (size_t)(int)vv * W + (int)uu;
+    const size_t q = (size_t)F.kf * W * H + (size_t)(int)vv * W + (int)uu;
     // w_z = cos(theta) / Z^2, theta from the central-difference normal
     // a = P(u+1,v) - P(u-1,v), b = P(u,v+1) - P(u,v-1), written as
     // x (z_r - z_l) + (z_r + z_l) / fx etc. so that no large terms cancel
     const float dzx = zr - zl, dzy = zd - zu;
-    const float ax = fmaf(xn, dzx, (zr + zl) / fx);
+    const float ax = fmaf(xn, dzx, (zr + zl) * c.ifx);
     const float ay = yn * dzx;
     const float az = dzx;
     const float bx = xn * dzy;
-    const float by = fmaf(yn, dzy, (zd + zu) / fy);
+    const float by = fmaf(yn, dzy, (zd + zu) * c.ify);
     const float bz = dzy;
-    const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
-    const float nn = sqrtf(nx * nx + ny * ny + nz * nz);
-    if (!(nn > 0.f)) return;
-    const float w = fabsf(nz) / nn / (z * z);
+    const float nx = diff_of_products(ay, bz, az, by), ny = diff_of_products(az, bx, ax, bz),
+                nz = diff_of_products(ax, by, ay, bx);
+    const float n2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
+    if (!(n2 > 0.f)) return;
+    const float w = fabsf(nz) * rsqrtf(n2) * __frcp_rn(z * z);
     atomicAdd(S + q, w * ps[2]);
     atomicAdd(Wsum + q, w);
 }
@@ -75,55 +93,73 @@ __global__ void fuse_normalise_kernel(float* Z, const float* Wsum, size_t n) {
     }
 }
 
+// Fuse frames [0, n) into keyframe images; frame f goes to image frame_kf[f] at pose kf_poses[frame_kf[f]].
+int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n,
+              const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* K, const sc_fusion_params* fusion,
+              float* kf_depth, float* kf_weight, cudaStream_t s) {
+    if (!depths || !frame_poses || n < 1 || !kf_poses || n_kf < 1 || !sc::intrinsics_ok(K) || !fusion ||
+        !kf_depth || !kf_weight || !(fusion->disc_rel >= 0.f))
+        return SC_ERR_INVALID_ARG;
+    if (((uintptr_t)depths & 15) || ((uintptr_t)kf_depth & 15) || ((uintptr_t)kf_weight & 15))
+        return SC_ERR_INVALID_ARG;
+    for (int f = 0; f < n; ++f) {
+        if (frame_kf && (frame_kf[f] < 0 || frame_kf[f] >= n_kf)) return SC_ERR_INVALID_ARG;
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 4; ++q)
+                if (!std::isfinite(frame_poses[f].m[r][q])) return SC_ERR_INVALID_ARG;
+    }
+    const int W = K->width, H = K->height;
+    const size_t npx = (size_t)W * H;
+    SC_CUDA(cudaMemsetAsync(kf_depth, 0, n_kf * npx * sizeof(float), s));
+    SC_CUDA(cudaMemsetAsync(kf_weight, 0, n_kf * npx * sizeof(float), s));
+    FuseCam c{K->fx, K->fy, K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), W, H, fusion->disc_rel};
+    for (int f0 = 0; f0 < n; f0 += FUSE_MAX_FRAMES) {
+        const int nf = (n - f0) < FUSE_MAX_FRAMES ? (n - f0) : FUSE_MAX_FRAMES;
+        FuseArgs a;
+        for (int f = 0; f < nf; ++f) {
+            const sc_pose& T = frame_poses[f0 + f];
+            const int kf = frame_kf ? frame_kf[f0 + f] : 0;
+            const sc_pose& Tk = kf_poses[kf];
+            // keyframe_from_frame, composed in double and rounded once
+            for (int r = 0; r < 3; ++r) {
+                for (int q = 0; q < 3; ++q) {
+                    double acc = 0;
+                    for (int k = 0; k < 3; ++k) acc += (double)Tk.m[k][r] * (double)T.m[k][q];
+                    a.f[f].R[3 * r + q] = (float)acc;
+                }
+                double acc = 0;
+                for (int k = 0; k < 3; ++k) acc += (double)Tk.m[k][r] * ((double)T.m[k][3] - (double)Tk.m[k][3]);
+                a.f[f].t[r] = (float)acc;
+            }
+            a.f[f].kf = kf;
+        }
+        dim3 block(FUSE_TX, FUSE_TY);
+        dim3 grid((W + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
+        fuse_kernel<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c, kf_depth, kf_weight);
+        sc::count_launches(1);
+        SC_CUDA(cudaGetLastError());
+    }
+    fuse_normalise_kernel<<<1024, 256, 0, s>>>(kf_depth, kf_weight, n_kf * npx);
+    sc::count_launches(1);
+    SC_CUDA(cudaGetLastError());
+    return SC_OK;
+}
+
 }  // namespace
 
 extern "C" int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses, int32_t n,
                                             const sc_pose* kf_pose, const sc_intrinsics* K,
                                             const sc_fusion_params* fusion, float* kf_depth, float* kf_weight,
                                             sc_stream stream) {
-    if (!depths || !frame_poses || n < 1 || !kf_pose || !sc::intrinsics_ok(K) || !fusion || !kf_depth ||
-        !kf_weight || !(fusion->disc_rel >= 0.f))
-        return SC_ERR_INVALID_ARG;
-    if (((uintptr_t)depths & 15) || ((uintptr_t)kf_depth & 15) || ((uintptr_t)kf_weight & 15))
-        return SC_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int W = K->width, H = K->height;
-    const size_t npx = (size_t)W * H;
-    SC_CUDA(cudaMemsetAsync(kf_depth, 0, npx * sizeof(float), s));
-    SC_CUDA(cudaMemsetAsync(kf_weight, 0, npx * sizeof(float), s));
-    // keyframe_from_frame transforms, composed in double and rounded once
-    double Rk[3][3], tk[3];
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) Rk[r][c] = kf_pose->m[r][c];
-        tk[r] = kf_pose->m[r][3];
-    }
-    for (int f0 = 0; f0 < n; f0 += FUSE_MAX_FRAMES) {
-        const int nf = (n - f0) < FUSE_MAX_FRAMES ? (n - f0) : FUSE_MAX_FRAMES;
-        FuseArgs a;
-        for (int f = 0; f < nf; ++f) {
-            const sc_pose& T = frame_poses[f0 + f];
-            for (int r = 0; r < 3; ++r) {
-                for (int c = 0; c < 3; ++c) {
-                    double acc = 0;
-                    for (int k = 0; k < 3; ++k) acc += Rk[k][r] * (double)T.m[k][c];
-                    a.f[f].R[3 * r + c] = (float)acc;
-                }
-                double acc = 0;
-                for (int k = 0; k < 3; ++k) acc += Rk[k][r] * ((double)T.m[k][3] - tk[k]);
-                a.f[f].t[r] = (float)acc;
-                for (int c = 0; c < 4; ++c)
-                    if (!std::isfinite(T.m[r][c])) return SC_ERR_INVALID_ARG;
-            }
-        }
-        dim3 block(FUSE_TX, FUSE_TY);
-        dim3 grid((W + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
-        fuse_kernel<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, K->fx, K->fy, K->cx, K->cy, W, H,
-                                           fusion->disc_rel, kf_depth, kf_weight);
-        sc::count_launches(1);
-        SC_CUDA(cudaGetLastError());
-    }
-    fuse_normalise_kernel<<<512, 256, 0, s>>>(kf_depth, kf_weight, npx);
-    sc::count_launches(1);
-    SC_CUDA(cudaGetLastError());
-    return SC_OK;
+    return fuse_impl(depths, frame_poses, nullptr, n, kf_pose, 1, K, fusion, kf_depth, kf_weight,
+                     (cudaStream_t)stream);
+}
+
+extern "C" int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf,
+                                 int32_t n_frames, const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* K,
+                                 const sc_fusion_params* fusion, float* kf_depth, float* kf_weight,
+                                 sc_stream stream) {
+    if (!frame_kf) return SC_ERR_INVALID_ARG;
+    return fuse_impl(depths, frame_poses, frame_kf, n_frames, kf_poses, n_kf, K, fusion, kf_depth, kf_weight,
+                     (cudaStream_t)stream);
 }

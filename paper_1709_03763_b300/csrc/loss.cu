@@ -11,6 +11,7 @@
 // accumulates g = dL/dD(v) / W(v) for unclamped samples into the depth-pixel
 // gradient and into four pose moments (sum g, sum g q) from which the se(3)
 // gradient follows.  Lane values are float, warp and CTA partials double.
+#include <algorithm>
 #include <cmath>
 
 #include "volume.cuh"
@@ -183,56 +184,60 @@ struct AdjItem {
     float* grad_depth;  // [H][W] or null
 };
 
-// acc [n][4]: sum g, sum g qx, sum g qy, sum g qz  (q = voxel - camera, voxel units)
-__global__ void adjoint_kernel(DevVolume V, const AdjItem* items, int n, uint32_t cap, const float* grad,
-                               double* acc) {
-    __shared__ double sh[4];
-    const int lane = threadIdx.x & 31;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    for (int k = 0; k < n; ++k) {
-        if (threadIdx.x < 4) sh[threadIdx.x] = 0.0;
-        __syncthreads();
-        const AdjItem& it = items[k];
-        const KfCam& cam = it.cam;
-        const uint32_t cnt = min((uint32_t)*it.count, cap);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        for (uint32_t b = wid; b < cnt; b += nw) {
-            const int32_t slot = it.list[b];
-            const int4 c = V.coord[slot];
+// acc [n][4]: sum g, sum g qx, sum g qy, sum g qz  (q = voxel - camera, voxel units).
+// Grid (chunks, n): blockIdx.y is the keyframe; the chunk's warps stride over its
+// block list, one warp per block (4 voxels per lane per group); lane sums are float,
+// the warp and CTA reductions double, one set of 4 atomics per CTA.
+constexpr int ADJ_THREADS = 256;
+
+__global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const AdjItem* items, uint32_t cap,
+                                                              const float* grad, double* acc) {
+    __shared__ double sh[ADJ_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.y;
+    const AdjItem& it = items[k];
+    const KfCam& cam = it.cam;
+    const uint32_t cnt = min((uint32_t)*it.count, cap);
+    const uint32_t nw = gridDim.x * (ADJ_THREADS / 32);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (uint32_t b = blockIdx.x * (ADJ_THREADS / 32) + warp; b < cnt; b += nw) {
+        const int32_t slot = it.list[b];
+        const int4 c = V.coord[slot];
 #pragma unroll 1
-            for (int g = 0; g < 4; ++g) {
-                int lx0, ly, lz;
-                lane_voxels(lane, g, lx0, ly, lz);
-                const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+        for (int g = 0; g < 4; ++g) {
+            int lx0, ly, lz;
+            lane_voxels(lane, g, lx0, ly, lz);
+            const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    float d, eta;
-                    int pix;
-                    const int ix = 8 * c.x + lx0 + j, iy = 8 * c.y + ly, iz = 8 * c.z + lz;
-                    if (!sample_voxel(cam, ix, iy, iz, d, pix, &eta)) continue;
-                    if (!(eta < cam.mu)) continue;  // clamped: no derivative
-                    const float gv = __fdiv_rn(grad[off + j], V.W[off + j]);
-                    if (gv == 0.f) continue;
-                    if (it.grad_depth) atomicAdd(it.grad_depth + pix, gv);
-                    a0 += gv;
-                    a1 = fmaf(gv, __fsub_rn((float)(ix - cam.ti[0]), cam.tf[0]), a1);
-                    a2 = fmaf(gv, __fsub_rn((float)(iy - cam.ti[1]), cam.tf[1]), a2);
-                    a3 = fmaf(gv, __fsub_rn((float)(iz - cam.ti[2]), cam.tf[2]), a3);
-                }
+            for (int j = 0; j < 4; ++j) {
+                float d, eta;
+                int pix;
+                const int ix = 8 * c.x + lx0 + j, iy = 8 * c.y + ly, iz = 8 * c.z + lz;
+                if (!sample_voxel(cam, ix, iy, iz, d, pix, &eta)) continue;
+                if (!(eta < cam.mu)) continue;  // clamped: no derivative
+                const float gv = __fdiv_rn(grad[off + j], V.W[off + j]);
+                if (gv == 0.f) continue;
+                if (it.grad_depth) atomicAdd(it.grad_depth + pix, gv);
+                a0 += gv;
+                a1 = fmaf(gv, __fsub_rn((float)(ix - cam.ti[0]), cam.tf[0]), a1);
+                a2 = fmaf(gv, __fsub_rn((float)(iy - cam.ti[1]), cam.tf[1]), a2);
+                a3 = fmaf(gv, __fsub_rn((float)(iz - cam.ti[2]), cam.tf[2]), a3);
             }
         }
-        const double s0 = warp_sum((double)a0), s1 = warp_sum((double)a1), s2 = warp_sum((double)a2),
-                     s3 = warp_sum((double)a3);
-        if (lane == 0 && (s0 != 0.0 || s1 != 0.0 || s2 != 0.0 || s3 != 0.0)) {
-            atomicAdd(&sh[0], s0);
-            atomicAdd(&sh[1], s1);
-            atomicAdd(&sh[2], s2);
-            atomicAdd(&sh[3], s3);
-        }
-        __syncthreads();
-        if (threadIdx.x < 4 && sh[threadIdx.x] != 0.0) atomicAdd(acc + 4 * k + threadIdx.x, sh[threadIdx.x]);
-        __syncthreads();
+    }
+    const double s0 = warp_sum((double)a0), s1 = warp_sum((double)a1), s2 = warp_sum((double)a2),
+                 s3 = warp_sum((double)a3);
+    if (lane == 0) {
+        sh[warp][0] = s0;
+        sh[warp][1] = s1;
+        sh[warp][2] = s2;
+        sh[warp][3] = s3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double t = 0.0;
+        for (int w = 0; w < ADJ_THREADS / 32; ++w) t += sh[w][threadIdx.x];
+        if (t != 0.0) atomicAdd(acc + 4 * k + threadIdx.x, t);
     }
 }
 
@@ -311,7 +316,7 @@ extern "C" int sc_sdf_loss(sc_volume* V, const float* points, int64_t n, float l
 extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
                               int32_t n, const sc_intrinsics* K, const float* grad_D, double* grad_xi,
                               float* grad_depth, sc_stream stream) {
-    if (!V || !kf_ids || !depths || !poses || n < 1 || !intrinsics_ok(K) || !grad_D || !grad_xi)
+    if (!V || !kf_ids || !depths || !poses || n < 1 || n > 65535 || !intrinsics_ok(K) || !grad_D || !grad_xi)
         return SC_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes || !depths[i]) return SC_ERR_INVALID_ARG;
@@ -339,7 +344,9 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
     SC_CUDA(cudaMemcpyAsync(A.poses_d, A.poses_h, n * sizeof(AdjPose), cudaMemcpyHostToDevice, s));
     SC_CUDA(cudaMemsetAsync(A.acc_d, 0, n * 4 * sizeof(double), s));
     if (grad_depth) SC_CUDA(cudaMemsetAsync(grad_depth, 0, n * img * sizeof(float), s));
-    adjoint_kernel<<<V->num_sms * 8, 256, 0, s>>>(V->dv, A.items_d, n, V->p.max_blocks_per_keyframe, grad_D, A.acc_d);
+    const int chunks = std::max(1, std::min(64, (V->num_sms * 8 + n - 1) / n));
+    adjoint_kernel<<<dim3(chunks, n), ADJ_THREADS, 0, s>>>(V->dv, A.items_d, V->p.max_blocks_per_keyframe, grad_D,
+                                                          A.acc_d);
     adjoint_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(A.poses_d, A.acc_d, n, (double)V->p.voxel_size, grad_xi);
     count_launches(2);
     SC_CUDA(cudaGetLastError());

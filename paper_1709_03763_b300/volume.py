@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (BatchConfig, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
                    VolumeParams, check, lib)
 
-__all__ = ["Volume", "fuse_frames_into_keyframe", "pose_distance", "select_topm", "select_consecutive",
+__all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "pose_distance", "select_topm", "select_consecutive",
            "pose_exp_left", "SurfcorrError", "make_intrinsics", "make_pose"]
 
 
@@ -137,6 +137,16 @@ class Volume:
               "sc_deintegrate_keyframe")
 
     # -- batched path
+    def integrate_many(self, kf_ids: Sequence[int], depths, rgbas, poses, intr, stream=None):
+        """Integrate several not-yet-integrated keyframes in one graph launch."""
+        n = len(kf_ids)
+        ids = (ctypes.c_int32 * n)(*[int(k) for k in kf_ids])
+        dp = (ctypes.c_void_p * n)(*[_dev(depths[i], torch.float32, "depth") for i in range(n)])
+        cp = (ctypes.c_void_p * n)(*[_dev(rgbas[i], torch.uint8, "rgba") for i in range(n)])
+        pz = (Pose * n)(*[make_pose(p) for p in poses])
+        check(lib().sc_integrate_keyframes(self.h, ids, dp, cp, pz, n, ctypes.byref(make_intrinsics(intr)),
+                                           _stream(stream)), "sc_integrate_keyframes")
+
     def _items(self, kf_ids, depths, rgbas, old_poses, new_poses):
         n = len(kf_ids)
         arr = (ReintItem * n)()
@@ -259,6 +269,28 @@ def fuse_frames_into_keyframe(depths: torch.Tensor, frame_poses, kf_pose, intr, 
                                              ctypes.byref(fp), _dev(out_depth, torch.float32, "out_depth"),
                                              _dev(out_weight, torch.float32, "out_weight"), _stream(stream)),
           "sc_fuse_frames_into_keyframe")
+    return out_depth, out_weight
+
+
+def fuse_keyframes(depths: torch.Tensor, frame_poses, frame_kf, kf_poses, intr, disc_rel: float = 0.1,
+                   out_depth: torch.Tensor | None = None, out_weight: torch.Tensor | None = None, stream=None):
+    """Eq. 1 for many keyframes in one call: frame f is fused into keyframe frame_kf[f].
+    depths [n,H,W]; returns (Z* [n_kf,H,W], W* [n_kf,H,W])."""
+    n, H, W = depths.shape
+    n_kf = len(kf_poses)
+    if out_depth is None:
+        out_depth = torch.empty((n_kf, H, W), dtype=torch.float32, device=depths.device)
+    if out_weight is None:
+        out_weight = torch.empty((n_kf, H, W), dtype=torch.float32, device=depths.device)
+    pz = (Pose * n)(*[make_pose(p) for p in frame_poses])
+    kz = (Pose * n_kf)(*[make_pose(p) for p in kf_poses])
+    fk = (ctypes.c_int32 * n)(*[int(k) for k in frame_kf])
+    fp = FusionParams(float(disc_rel))
+    check(lib().sc_fuse_keyframes(_dev(depths, torch.float32, "depths"), pz, fk, n, kz, n_kf,
+                                  ctypes.byref(make_intrinsics(intr)), ctypes.byref(fp),
+                                  _dev(out_depth, torch.float32, "out_depth"),
+                                  _dev(out_weight, torch.float32, "out_weight"), _stream(stream)),
+          "sc_fuse_keyframes")
     return out_depth, out_weight
 
 

@@ -128,3 +128,23 @@ def test_ragged_image_and_empty_keyframe(tiny):
     assert E.keyframe_blocks(0).numel() == 0
     E.deintegrate(0, torch.zeros_like(d).cuda(), c.cuda(), intr, w.kf_poses[2])
     E.check()
+
+
+@pytest.mark.parametrize("colour", ["f32", "rgba8"])
+def test_integrate_many_matches_oracle(tinyg, colour):
+    """sc_integrate_keyframes: all 10 keyframes in one graph launch."""
+    w, D, C = tinyg
+    it = w.intr.as_tuple()
+    V = gpu_volume(w, colour=colour)
+    O = oracle_volume(w, rgba8=(colour == "rgba8"))
+    V.integrate_many(list(range(10)), D, C, w.kf_poses, w.intr)
+    for k in range(10):
+        O.integrate(k, w.kf_depth[k], w.kf_rgba[k], it, w.kf_poses[k])
+    V.check()
+    # RGBA8: one rounding per voxel instead of one per keyframe
+    compare_volumes(V.extract(), O.export(), colour=colour, c_tol=0.5 if colour == "f32" else 2.0)
+    # and the keyframes are integrated: their lists de-integrate them again
+    for k in range(10):
+        V.deintegrate(k, D[k], C[k], w.intr, w.kf_poses[k])
+    e = V.extract()
+    assert torch.all(e["W"] == 0)
