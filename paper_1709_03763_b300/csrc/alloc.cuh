@@ -131,12 +131,14 @@ __device__ inline void publish(const DevVolume& V, int entry, unsigned long long
 }
 
 struct AllocShared {
-    unsigned long long set[SET_SIZE];
-    int ent[SET_SIZE];
-    int slot[SET_SIZE];  // pool slot of entries this CTA created, else -1
-    int idx[SET_SIZE];   // new entries (phase B), then list appends (phase C)
+    unsigned long long set[SET_SIZE];  // open-addressing set of the tile's block keys
+    int uk[SET_SIZE];    // compacted: set positions of the n_keys occupied entries
+    int ent[SET_SIZE];   // per compacted key: hash entry index (-1: failed)
+    int slot[SET_SIZE];  // per compacted key: pool slot if known, else -1
+    int idx[SET_SIZE];   // new keys (phase B), then list appends (phase C)
     int uidx[SET_SIZE];  // union appends (batches)
-    int n_new, n_app, n_uapp, overflow;
+    unsigned char mine[SET_SIZE];  // key created by this CTA
+    int n_keys, n_new, n_app, n_uapp, overflow;
     uint32_t pool_base;
     int app_base, uapp_base;
 };
@@ -159,6 +161,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     const int tid = threadIdx.x;
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY_EMPTY;
     if (tid == 0) {
+        sh.n_keys = 0;
         sh.n_new = 0;
         sh.n_app = 0;
         sh.n_uapp = 0;
@@ -166,6 +169,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     }
     __syncthreads();
 
+    // A: every pixel's band-segment blocks into the shared set
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
     const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
     bool my_ovf = false;
@@ -185,16 +189,21 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     }
     if (my_ovf) sh.overflow = 1;
     __syncthreads();
+    // compact the occupied entries so that the global phases run in one round
+    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS)
+        if (sh.set[i] != KEY_EMPTY) sh.uk[atomicAdd(&sh.n_keys, 1)] = i;
+    __syncthreads();
+    const int nk = sh.n_keys;
 
     // B: claim each unique key; the tile's new entries get consecutive slots
-    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) {
-        sh.ent[i] = -1;
-        sh.slot[i] = -1;
-        const unsigned long long key = sh.set[i];
-        if (key == KEY_EMPTY) continue;
+    for (int i = tid; i < nk; i += ALLOC_THREADS) {
         bool won;
-        sh.ent[i] = hash_claim(V, key, &won);
-        if (sh.ent[i] >= 0 && won) sh.idx[atomicAdd(&sh.n_new, 1)] = i;
+        int32_t seen;
+        const int e = hash_claim(V, sh.set[sh.uk[i]], &won, &seen);
+        sh.ent[i] = e;
+        sh.slot[i] = seen;
+        sh.mine[i] = 0;
+        if (e >= 0 && won) sh.idx[atomicAdd(&sh.n_new, 1)] = i;
     }
     __syncthreads();
     if (tid == 0 && sh.n_new > 0) sh.pool_base = atomicAdd(V.pool_count, (uint32_t)sh.n_new);
@@ -207,25 +216,22 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
         if (slot < V.max_blocks) {
             sk.mark_new(slot);
             sh.slot[j] = (int)slot;
+            sh.mine[j] = 1;
         }
-        publish(V, sh.ent[j], sh.set[j], slot);
+        publish(V, sh.ent[j], sh.set[sh.uk[j]], slot);
     }
     __syncthreads();
 
-    // C: dedupe and append
-    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) {
+    // C: dedupe and append (the two membership atomics are independent)
+    for (int i = tid; i < nk; i += ALLOC_THREADS) {
         if (sh.ent[i] < 0) continue;
         int32_t slot = sh.slot[i];
-        bool first;
-        if (slot >= 0) {
-            first = true;  // created here
-        } else {
-            slot = entry_slot(V, sh.ent[i]);
-            if (slot < 0) continue;
-            first = sk.list_first(slot);
-        }
+        if (slot < 0) slot = entry_slot(V, sh.ent[i]);
+        if (slot < 0) continue;
+        const bool first = sh.mine[i] ? true : sk.list_first(slot);
+        const bool ufirst = Sink::kUnion ? sk.union_first(slot) : false;
         if (first) sh.idx[atomicAdd(&sh.n_app, 1)] = slot;
-        if (Sink::kUnion && sk.union_first(slot)) sh.uidx[atomicAdd(&sh.n_uapp, 1)] = slot;
+        if (ufirst) sh.uidx[atomicAdd(&sh.n_uapp, 1)] = slot;
     }
     __syncthreads();
     if (tid == 0) {
@@ -259,10 +265,11 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
                 const unsigned long long key = pack_key(bx, by, bz);
                 if (set_contains(sh.set, key)) return;
                 bool won;
-                const int e = hash_claim(V, key, &won);
+                int32_t seen;
+                const int e = hash_claim(V, key, &won, &seen);
                 if (e < 0) return;
                 if (won) publish(V, e, key, atomicAdd(V.pool_count, 1u));
-                const int32_t slot = entry_slot(V, e);
+                const int32_t slot = seen >= 0 ? seen : entry_slot(V, e);
                 if (slot < 0) return;
                 if (sk.list_first(slot)) append_one(V, sk.list, sk.count, sk.cap, slot);
                 if (Sink::kUnion && sk.union_first(slot)) append_one(V, sk.ulist, sk.ucount, sk.ucap, slot);

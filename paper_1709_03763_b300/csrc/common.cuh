@@ -184,27 +184,46 @@ __device__ __forceinline__ void lane_voxels(int lane, int g, int& lx0, int& ly, 
 
 // ---------------------------------------------------------------- hashing ----
 
+// 16-byte load that bypasses stale L1 copies (key and slot of a hash entry).  The
+// words are read individually atomically; a key that matches always comes with
+// either SLOT_PENDING, SLOT_FAILED or its final slot (slots are written once).
+__device__ __forceinline__ uint4 ld_volatile_u4(const void* p) {
+    uint4 r;
+    asm volatile("ld.volatile.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
 // Lock-free insert-or-find of `key`.  Bucketed open addressing: the key's home
 // bucket, then the following buckets (wrapping) up to max_probe buckets.  An
 // empty entry is claimed with a 64-bit CAS on its key; the slot is published
-// later (SLOT_PENDING until then).  Returns the entry index, or -1 with the
-// status set (SC_ERR_HASH_FULL).  *won is set when this call created the entry.
-__device__ inline int hash_claim(const DevVolume& V, unsigned long long key, bool* won) {
+// later (SLOT_PENDING until then).  Each entry is read with one 16-byte load, so
+// for a key that exists the published slot comes back in the same round trip
+// (*slot_seen, else -1).  Returns the entry index, or -1 with the status set
+// (SC_ERR_HASH_FULL).  *won is set when this call created the entry.
+__device__ inline int hash_claim(const DevVolume& V, unsigned long long key, bool* won, int32_t* slot_seen) {
     const uint32_t b = hash_bucket(key, V.bucket_mask);
     *won = false;
+    *slot_seen = -1;
     for (uint32_t probe = 0; probe < V.max_probe; ++probe) {
         const uint32_t base = ((b + probe) & V.bucket_mask) * V.bucket_size;
         for (uint32_t e = 0; e < V.bucket_size; ++e) {
-            unsigned long long* kp = &V.table[base + e].key;
-            unsigned long long k = *((volatile unsigned long long*)kp);
+            HashEntry* ep = &V.table[base + e];
+            const uint4 w = ld_volatile_u4(ep);
+            unsigned long long k = (unsigned long long)w.x | ((unsigned long long)w.y << 32);
+            if (k == key) {
+                *slot_seen = (int32_t)w.z >= 0 ? (int32_t)w.z : -1;
+                return (int)(base + e);
+            }
             if (k == KEY_EMPTY) {
-                k = atomicCAS(kp, KEY_EMPTY, key);
+                k = atomicCAS(&ep->key, KEY_EMPTY, key);
                 if (k == KEY_EMPTY) {
                     *won = true;
                     return (int)(base + e);
                 }
+                if (k == key) return (int)(base + e);
             }
-            if (k == key) return (int)(base + e);
         }
     }
     set_status(V.status, SC_ERR_HASH_FULL);

@@ -199,10 +199,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
     const KfCam& cam = it.cam;
     const uint32_t cnt = min((uint32_t)*it.count, cap);
     const uint32_t nw = gridDim.x * (ADJ_THREADS / 32);
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    // per lane: float sums over one block's 16 voxels, then double across blocks
+    // (contributions of both signs cancel strongly in the pose moments)
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
     for (uint32_t b = blockIdx.x * (ADJ_THREADS / 32) + warp; b < cnt; b += nw) {
         const int32_t slot = it.list[b];
         const int4 c = V.coord[slot];
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 1
         for (int g = 0; g < 4; ++g) {
             int lx0, ly, lz;
@@ -224,9 +227,12 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
                 a3 = fmaf(gv, __fsub_rn((float)(iz - cam.ti[2]), cam.tf[2]), a3);
             }
         }
+        d0 += a0;
+        d1 += a1;
+        d2 += a2;
+        d3 += a3;
     }
-    const double s0 = warp_sum((double)a0), s1 = warp_sum((double)a1), s2 = warp_sum((double)a2),
-                 s3 = warp_sum((double)a3);
+    const double s0 = warp_sum(d0), s1 = warp_sum(d1), s2 = warp_sum(d2), s3 = warp_sum(d3);
     if (lane == 0) {
         sh[warp][0] = s0;
         sh[warp][1] = s1;
