@@ -79,7 +79,7 @@ def _declare(L):
     L.or_select_consecutive.restype = _i
     L.or_loss.argtypes = [_p, _p, _l, _d, _p, _p]
     L.or_loss.restype = _d
-    L.or_grad.argtypes = [_p, _i, _p, _p, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _p]
+    L.or_grad.argtypes = [_p, _i, _p, _p, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _p, _p, _p]
     L.or_grad.restype = _i
     L.or_loss_perturbed.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _l, _d]
     L.or_loss_perturbed.restype = _d
@@ -252,7 +252,9 @@ class Volume:
         L = lib().or_loss(self.h, _ptr(pts), len(pts), lam, ctypes.byref(nv), _ptr(pf))
         return L, nv.value, pf
 
-    def grad(self, kf_ids, depths, poses, intr, points, lam=0.1, with_depth=True):
+    def grad(self, kf_ids, depths, poses, intr, points, lam=0.1, with_depth=True, with_budget=False):
+        """Analytic gradient (grad_xi [K,6], grad_depth [K,H,W]); with_budget also returns the
+        error budgets (err_xi [K,6], err_depth [K,H,W]) of marginal contributions."""
         ids = np.ascontiguousarray(kf_ids, np.int32)
         d = _f32(_np(depths))
         K, H, W = d.shape
@@ -260,11 +262,15 @@ class Volume:
         pts = np.ascontiguousarray(points, np.float64)
         gx = np.zeros((K, 6))
         gd = np.zeros((K, H, W)) if with_depth else None
+        ex = np.zeros((K, 6)) if with_budget else None
+        ed = np.zeros((K, H, W)) if (with_budget and with_depth) else None
         fx, fy, cx, cy = _intr(intr)
         rc = lib().or_grad(self.h, K, _ptr(ids), _ptr(d), None, _ptr(p), fx, fy, cx, cy, W, H,
-                           _ptr(pts), len(pts), lam, _ptr(gx), _ptr(gd))
+                           _ptr(pts), len(pts), lam, _ptr(gx), _ptr(gd), _ptr(ex), _ptr(ed))
         if rc:
             raise ValueError("keyframe not integrated")
+        if with_budget:
+            return gx, gd, ex, ed
         return gx, gd
 
     def loss_perturbed(self, kf_id, depth, pose, intr, xi, points, lam=0.1, pix=-1, dz=0.0):

@@ -865,9 +865,17 @@ extern "C" double or_loss(void* vol, const double* pts, long n, double lambda, l
 // Pixel assignment, band membership and the clamp are piecewise constant in the
 // pose and depth; they contribute no derivative.
 // grad_xi [K][6] (rho then omega), grad_depth [K][H][W] (may be null).
+// err_xi [K][6] and err_depth [K][H][W] (each may be null) receive an error
+// budget: the summed magnitudes of the contributions whose decisions are marginal
+// (a voxel's rounding, band edge, clamp kink or camera plane; every voxel of a block
+// whose allocation is marginal) -- contributions a float32 evaluation may include,
+// drop or move to the neighbouring pixel.  Blocks this reference does not allocate
+// but a float32 evaluation may ("ghosts") are bounded by 512 times the largest
+// single-voxel contribution of the keyframe.
 extern "C" int or_grad(void* vol, int K_, const int* kf_ids, const float* depths, const uint8_t* rgba,
                        const float* poses, double fx, double fy, double cx, double cy, int W, int H,
-                       const double* pts, long n, double lambda, double* grad_xi, double* grad_depth) {
+                       const double* pts, long n, double lambda, double* grad_xi, double* grad_depth,
+                       double* err_xi, double* err_depth) {
     Vol& V = *(Vol*)vol;
     const Intr K{fx, fy, cx, cy, W, H};
     DOverlay ov;
@@ -903,39 +911,71 @@ extern "C" int or_grad(void* vol, int K_, const int* kf_ids, const float* depths
     for (int k = 0; k < K_; ++k) {
         double* gx = grad_xi + 6 * k;
         for (int j = 0; j < 6; ++j) gx[j] = 0.0;
+        double* ex = err_xi ? err_xi + 6 * k : nullptr;
+        if (ex)
+            for (int j = 0; j < 6; ++j) ex[j] = 0.0;
         double* gd = grad_depth ? grad_depth + k * img : nullptr;
         if (gd)
             for (long q = 0; q < img; ++q) gd[q] = 0.0;
+        double* ed = err_depth ? err_depth + k * img : nullptr;
+        if (ed)
+            for (long q = 0; q < img; ++q) ed[q] = 0.0;
         auto it = V.touched.find(kf_ids[k]);
         if (it == V.touched.end()) return -1;
         const Pose T = pose_from(poses + 12 * k);
         const float* depth = depths + k * img;
         const double r3[3] = {T.R[0][2], T.R[1][2], T.R[2][2]};  // third row of R^T
         const Touched& tl = it->second;
+        double max_term[6] = {0, 0, 0, 0, 0, 0};
+        long n_ghost = 0, n_marg_out = 0;  // marginal voxels this reference does not update
         for (size_t b = 0; b < tl.blocks.size(); ++b) {
-            if (tl.marginal[b] == 2) continue;
+            if (tl.marginal[b] == 2) {
+                ++n_ghost;
+                continue;
+            }
             long bx, by, bz;
             unpack(tl.blocks[b], &bx, &by, &bz);
             const Block& blk = V.blocks.at(tl.blocks[b]);
+            const bool bmarg = tl.marginal[b] != 0;
             const std::vector<double>& g = G.at(tl.blocks[b]);
             for (int lz = 0; lz < BS; ++lz)
                 for (int ly = 0; ly < BS; ++ly)
                     for (int lx = 0; lx < BS; ++lx) {
                         int vi = lx + BS * ly + BS * BS * lz;
                         Sample S = sample_voxel(V, depth, nullptr, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
-                        if (!S.upd || S.clamped) continue;
+                        if (!S.upd) {
+                            if (S.marginal || bmarg) ++n_marg_out;
+                            continue;
+                        }
+                        if (S.clamped && !S.marginal) continue;
                         double gv = g[vi] * 1.0 / blk.W[vi];
-                        if (gd) gd[S.pix] += gv;
                         // -dz_c/drho = r3 ; -dz_c/domega = -(r3 x p_v) = p_v x r3
                         const double* p = S.pv;
                         double cx_[3] = {p[1] * r3[2] - p[2] * r3[1], p[2] * r3[0] - p[0] * r3[2],
                                          p[0] * r3[1] - p[1] * r3[0]};
-                        for (int j = 0; j < 3; ++j) {
-                            gx[j] += gv * r3[j];
-                            gx[3 + j] += gv * cx_[j];
+                        const double term[6] = {gv * r3[0], gv * r3[1], gv * r3[2],
+                                                gv * cx_[0], gv * cx_[1], gv * cx_[2]};
+                        const bool marg = S.marginal || bmarg;
+                        if (!S.clamped) {
+                            if (gd) gd[S.pix] += gv;
+                            for (int j = 0; j < 6; ++j) gx[j] += term[j];
+                        }
+                        for (int j = 0; j < 6; ++j) max_term[j] = std::max(max_term[j], std::fabs(term[j]));
+                        if (!marg) continue;
+                        if (ex)
+                            for (int j = 0; j < 6; ++j) ex[j] += std::fabs(term[j]);
+                        if (ed) {
+                            const long px = S.pix % W, py = S.pix / W;
+                            for (long dy = -1; dy <= 1; ++dy)
+                                for (long dx = -1; dx <= 1; ++dx) {
+                                    const long yy = py + dy, xx = px + dx;
+                                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) ed[yy * W + xx] += std::fabs(gv);
+                                }
                         }
                     }
         }
+        if (ex)
+            for (int j = 0; j < 6; ++j) ex[j] += (512.0 * (double)n_ghost + (double)n_marg_out) * max_term[j];
     }
     (void)rgba;
     return 0;

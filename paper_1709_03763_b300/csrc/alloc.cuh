@@ -18,24 +18,37 @@
 
 namespace sc {
 
-constexpr int ALLOC_TX = 32;         // pixel tile 32 x 32, one CTA of 256 threads,
-constexpr int ALLOC_TY = 32;         // 4 pixels (rows r, r+8, r+16, r+24) per thread
+#ifndef SC_ALLOC_TY
+#define SC_ALLOC_TY 8
+#endif
+#ifndef SC_ALLOC_WARP_DEDUPE
+#define SC_ALLOC_WARP_DEDUPE 0
+#endif
+constexpr int ALLOC_TX = 32;           // pixel tile 32 x SC_ALLOC_TY, one CTA of 256 threads,
+constexpr int ALLOC_TY = SC_ALLOC_TY;  // SC_ALLOC_TY / 8 pixels (rows r, r+8, ...) per thread
 constexpr int ALLOC_THREADS = 256;
 constexpr int ALLOC_PPT = ALLOC_TX * ALLOC_TY / ALLOC_THREADS;
-constexpr int SET_SIZE = 1024;       // unique blocks a tile may touch before overflow handling
-constexpr int MAX_BLOCK_SPAN = 16;   // per-axis candidate blocks of one band segment
+constexpr int SET_SIZE = ALLOC_TY >= 32 ? 1024 : 512;  // unique blocks of a tile before overflow handling
+constexpr int MAX_BLOCK_WALK = 48;   // block-face crossings of one band segment
 constexpr float MAX_DEPTH = 1.0e4f;  // metres; larger depth values are treated as invalid
 
-// Blocks whose closed box meets pixel (u, v)'s band segment; calls f(bx, by, bz).
+// Blocks met by pixel (u, v)'s band segment; calls f(bx, by, bz) once per block.
 // Geometry in voxel units relative to the camera's integer voxel position ti.
+// The segment is walked from its start block to its end block across block
+// faces (3-D DDA, exactly sum |b1 - b0| steps).  That is the set of closed boxes
+// the segment meets, except where the segment passes within float error of a
+// block edge, corner or face it only touches: such decisions are marginal.
 template <typename F>
 __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, float Z, F&& f) {
-    const float xn = __fdiv_rn(__fsub_rn((float)u, k.cx), k.fx);
-    const float yn = __fdiv_rn(__fsub_rn((float)v, k.cy), k.fy);
+    const float xn = __fmul_rn(__fsub_rn((float)u, k.cx), k.ifx);
+    const float yn = __fmul_rn(__fsub_rn((float)v, k.cy), k.ify);
     const float z0 = __fsub_rn(Z, k.mu), z1 = __fadd_rn(Z, k.mu);
     const float c0[3] = {__fmul_rn(xn, z0), __fmul_rn(yn, z0), z0};
     const float c1[3] = {__fmul_rn(xn, z1), __fmul_rn(yn, z1), z1};
     float q0[3], q1[3];
+    int b[3], rem[3], step[3];
+    float tmax[3], tdel[3];
+    int n = 0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
         q0[r] = __fadd_rn(
@@ -44,61 +57,61 @@ __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, floa
         q1[r] = __fadd_rn(
             __fmaf_rn(k.Ms[3 * r + 2], c1[2], __fmaf_rn(k.Ms[3 * r + 1], c1[1], __fmul_rn(k.Ms[3 * r], c1[0]))),
             k.tf[r]);
-    }
-    // Blocks whose closed box [8b, 8b+8] (absolute voxel units) meets [lo, hi] on an
-    // axis: b from ceil(lo) - 1 >> 3 to floor(hi) >> 3 (exact for these float
-    // endpoints); the slab test then decides per block.
-    int blo[3], bhi[3];
-    float inv[3];
-    bool flat[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float lo = fminf(q0[a], q1[a]), hi = fmaxf(q0[a], q1[a]);
-        blo[a] = ((int)ceilf(lo) - 1 + k.ti[a]) >> 3;
-        bhi[a] = ((int)floorf(hi) + k.ti[a]) >> 3;
-        const float d = __fsub_rn(q1[a], q0[a]);
-        flat[a] = d == 0.f;
-        inv[a] = flat[a] ? 0.f : __frcp_rn(d);
-    }
-    // a band segment spans a handful of blocks; a larger range comes from a
-    // degenerate input and is skipped rather than looped over
-    if (bhi[0] - blo[0] > MAX_BLOCK_SPAN || bhi[1] - blo[1] > MAX_BLOCK_SPAN || bhi[2] - blo[2] > MAX_BLOCK_SPAN)
-        return;
-    // segment parameter interval [t0, t1] inside block b's slab on axis a
-    auto slab = [&](int a, int b, float& t0, float& t1) -> bool {
-        const float lo = (float)(8 * b - k.ti[a]), hi = lo + 8.f;
-        if (flat[a]) {
-            t0 = 0.f;
-            t1 = 1.f;
-            return !(q0[a] < lo || q0[a] > hi);
+        b[r] = ((int)floorf(q0[r]) + k.ti[r]) >> 3;
+        const int e = ((int)floorf(q1[r]) + k.ti[r]) >> 3;
+        rem[r] = abs(e - b[r]);
+        n += rem[r];
+        const float d = __fsub_rn(q1[r], q0[r]);
+        step[r] = d > 0.f ? 1 : -1;
+        tmax[r] = __int_as_float(0x7f800000);  // +inf: no crossing on this axis
+        tdel[r] = tmax[r];
+        if (rem[r] > 0) {
+            const float inv = __frcp_rn(d);
+            const float bound = (float)(8 * (b[r] + (step[r] > 0 ? 1 : 0)) - k.ti[r]);
+            tmax[r] = __fmul_rn(__fsub_rn(bound, q0[r]), inv);
+            tdel[r] = __fmul_rn(8.f, fabsf(inv));
         }
-        float ta = __fmul_rn(__fsub_rn(lo, q0[a]), inv[a]), tb = __fmul_rn(__fsub_rn(hi, q0[a]), inv[a]);
-        t0 = fmaxf(fminf(ta, tb), 0.f);
-        t1 = fminf(fmaxf(ta, tb), 1.f);
-        return t0 <= t1;
-    };
-    for (int bz = blo[2]; bz <= bhi[2]; ++bz) {
-        float z0, z1;
-        if (!slab(2, bz, z0, z1)) continue;
-        for (int by = blo[1]; by <= bhi[1]; ++by) {
-            float y0, y1;
-            if (!slab(1, by, y0, y1)) continue;
-            const float t0 = fmaxf(z0, y0), t1 = fminf(z1, y1);
-            if (t0 > t1) continue;
-            for (int bx = blo[0]; bx <= bhi[0]; ++bx) {
-                float x0, x1;
-                if (!slab(0, bx, x0, x1)) continue;
-                if (fmaxf(t0, x0) <= fminf(t1, x1)) f(bx, by, bz);
-            }
+    }
+    // a band segment spans a handful of blocks; a longer walk comes from a
+    // degenerate input and is skipped rather than followed
+    if (n > MAX_BLOCK_WALK) return;
+    // scalar walk state (no dynamically indexed arrays: everything stays in registers)
+    int bx = b[0], by = b[1], bz = b[2];
+    int rx = rem[0], ry = rem[1], rz = rem[2];
+    float tx = tmax[0], ty = tmax[1], tz = tmax[2];
+    f(bx, by, bz);
+    for (int i = 0; i < n; ++i) {
+        // axis with a crossing left and the nearest next face (x before y before z on ties)
+        const bool px = rx > 0 && (ry == 0 || tx <= ty) && (rz == 0 || tx <= tz);
+        const bool py = !px && ry > 0 && (rz == 0 || ty <= tz);
+        if (px) {
+            bx += step[0];
+            --rx;
+            tx = __fadd_rn(tx, tdel[0]);
+        } else if (py) {
+            by += step[1];
+            --ry;
+            ty = __fadd_rn(ty, tdel[1]);
+        } else {
+            bz += step[2];
+            --rz;
+            tz = __fadd_rn(tz, tdel[2]);
         }
+        f(bx, by, bz);
     }
 }
 
+// Insert into the CTA's shared set.  Most inserts find their key already there:
+// read before CAS so that those do not serialise on the shared atomic unit.
 __device__ inline bool set_insert(unsigned long long* set, unsigned long long key) {
     uint32_t h = hash_bucket(key, SET_SIZE - 1);
     for (int i = 0; i < SET_SIZE; ++i) {
-        const unsigned long long old = atomicCAS(&set[h], KEY_EMPTY, key);
-        if (old == KEY_EMPTY || old == key) return true;
+        unsigned long long k = ((volatile unsigned long long*)set)[h];
+        if (k == key) return true;
+        if (k == KEY_EMPTY) {
+            k = atomicCAS(&set[h], KEY_EMPTY, key);
+            if (k == KEY_EMPTY || k == key) return true;
+        }
         h = (h + 1) & (SET_SIZE - 1);
     }
     return false;
@@ -184,7 +197,15 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
                 set_status(V.status, SC_ERR_INVALID_ARG);
                 return;
             }
-            if (!set_insert(sh.set, pack_key(bx, by, bz))) my_ovf = true;
+            // neighbouring pixels of a warp mostly reach the same blocks: one insert
+            // per distinct key among the lanes active here
+            const unsigned long long key = pack_key(bx, by, bz);
+#if SC_ALLOC_WARP_DEDUPE
+            const unsigned grp = __match_any_sync(__activemask(), key);
+            if ((threadIdx.x & 31) == __ffs(grp) - 1 && !set_insert(sh.set, key)) my_ovf = true;
+#else
+            if (!set_insert(sh.set, key)) my_ovf = true;
+#endif
         });
     }
     if (my_ovf) sh.overflow = 1;

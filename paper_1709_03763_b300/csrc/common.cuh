@@ -96,6 +96,7 @@ struct KfCam {
     float tf[3];
     int ti[3];
     float fx, fy, cx, cy;
+    float ifx, ify;  // 1 / fx, 1 / fy
     int W, H;
     float mu;
     const float* depth;

@@ -58,6 +58,8 @@ KfCam make_cam(const sc_volume* V, const sc_intrinsics* K, const sc_pose* T, con
     c.fy = K->fy;
     c.cx = K->cx;
     c.cy = K->cy;
+    c.ifx = (float)(1.0 / (double)K->fx);
+    c.ify = (float)(1.0 / (double)K->fy);
     c.W = K->width;
     c.H = K->height;
     c.mu = V->p.trunc;
