@@ -365,6 +365,7 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     Sample S{};
     S.upd = false;
     S.marginal = false;
+    S.pix = -1;
     S.pv[0] = ix * V.s;
     S.pv[1] = iy * V.s;
     S.pv[2] = iz * V.s;
@@ -377,6 +378,7 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     long px = round_half_up(K.fx * pc[0] / pc[2] + K.cx, &mu_);
     long py = round_half_up(K.fy * pc[1] / pc[2] + K.cy, &mv_);
     if (mu_ < g_tau_px || mv_ < g_tau_px) S.marginal = true;
+    S.pix = std::min(std::max(py, 0L), (long)K.H - 1) * K.W + std::min(std::max(px, 0L), (long)K.W - 1);
     if (px < 0 || px >= K.W || py < 0 || py >= K.H) return S;
     long q = py * K.W + px;
     double Z = depth[q];
@@ -869,9 +871,9 @@ extern "C" double or_loss(void* vol, const double* pts, long n, double lambda, l
 // budget: the summed magnitudes of the contributions whose decisions are marginal
 // (a voxel's rounding, band edge, clamp kink or camera plane; every voxel of a block
 // whose allocation is marginal) -- contributions a float32 evaluation may include,
-// drop or move to the neighbouring pixel.  Blocks this reference does not allocate
-// but a float32 evaluation may ("ghosts") are bounded by 512 times the largest
-// single-voxel contribution of the keyframe.
+// drop or move to a neighbouring pixel.  Contributions this reference does not
+// make at all (marginal voxels it does not update, blocks it does not allocate)
+// are bounded with the largest |dL/dD / W| of the volume.
 extern "C" int or_grad(void* vol, int K_, const int* kf_ids, const float* depths, const uint8_t* rgba,
                        const float* poses, double fx, double fy, double cx, double cy, int W, int H,
                        const double* pts, long n, double lambda, double* grad_xi, double* grad_depth,
@@ -907,6 +909,12 @@ extern "C" int or_grad(void* vol, int K_, const int* kf_ids, const float* depths
             G[pack(bx, by, bz)][vi] += 2.0 / (double)P * E.Dt * E.beta[c];
         }
     }
+    // largest |dL/dD / W| of any observed voxel: bounds contributions this reference
+    // does not make but a float32 evaluation may
+    double gmax = 0.0;
+    for (auto& kv : V.blocks)
+        for (int vi = 0; vi < NV; ++vi)
+            if (kv.second.W[vi] > 0.0) gmax = std::max(gmax, std::fabs(G.at(kv.first)[vi] / kv.second.W[vi]));
     long img = (long)W * H;
     for (int k = 0; k < K_; ++k) {
         double* gx = grad_xi + 6 * k;
@@ -926,56 +934,63 @@ extern "C" int or_grad(void* vol, int K_, const int* kf_ids, const float* depths
         const float* depth = depths + k * img;
         const double r3[3] = {T.R[0][2], T.R[1][2], T.R[2][2]};  // third row of R^T
         const Touched& tl = it->second;
-        double max_term[6] = {0, 0, 0, 0, 0, 0};
-        long n_ghost = 0, n_marg_out = 0;  // marginal voxels this reference does not update
-        for (size_t b = 0; b < tl.blocks.size(); ++b) {
-            if (tl.marginal[b] == 2) {
-                ++n_ghost;
-                continue;
+        auto budget = [&](const Sample& S, double gv_abs) {
+            const double* p = S.pv;
+            const double cx_[3] = {p[1] * r3[2] - p[2] * r3[1], p[2] * r3[0] - p[0] * r3[2],
+                                   p[0] * r3[1] - p[1] * r3[0]};
+            if (ex)
+                for (int j = 0; j < 3; ++j) {
+                    ex[j] += gv_abs * std::fabs(r3[j]);
+                    ex[3 + j] += gv_abs * std::fabs(cx_[j]);
+                }
+            if (ed && S.pix >= 0) {
+                const long px = S.pix % W, py = S.pix / W;
+                for (long dy = -1; dy <= 1; ++dy)
+                    for (long dx = -1; dx <= 1; ++dx) {
+                        const long yy = py + dy, xx = px + dx;
+                        if (yy >= 0 && yy < H && xx >= 0 && xx < W) ed[yy * W + xx] += gv_abs;
+                    }
             }
+        };
+        for (size_t b = 0; b < tl.blocks.size(); ++b) {
             long bx, by, bz;
             unpack(tl.blocks[b], &bx, &by, &bz);
-            const Block& blk = V.blocks.at(tl.blocks[b]);
+            const bool ghost = tl.marginal[b] == 2;
             const bool bmarg = tl.marginal[b] != 0;
-            const std::vector<double>& g = G.at(tl.blocks[b]);
+            const Block* blk = ghost ? nullptr : &V.blocks.at(tl.blocks[b]);
+            const std::vector<double>* g = ghost ? nullptr : &G.at(tl.blocks[b]);
             for (int lz = 0; lz < BS; ++lz)
                 for (int ly = 0; ly < BS; ++ly)
                     for (int lx = 0; lx < BS; ++lx) {
                         int vi = lx + BS * ly + BS * BS * lz;
                         Sample S = sample_voxel(V, depth, nullptr, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
-                        if (!S.upd) {
-                            if (S.marginal || bmarg) ++n_marg_out;
+                        if (ghost) {
+                            // a block only a float32 evaluation may allocate for this keyframe
+                            if (S.upd || S.marginal) budget(S, gmax);
                             continue;
                         }
-                        if (S.clamped && !S.marginal) continue;
-                        double gv = g[vi] * 1.0 / blk.W[vi];
-                        // -dz_c/drho = r3 ; -dz_c/domega = -(r3 x p_v) = p_v x r3
-                        const double* p = S.pv;
-                        double cx_[3] = {p[1] * r3[2] - p[2] * r3[1], p[2] * r3[0] - p[0] * r3[2],
-                                         p[0] * r3[1] - p[1] * r3[0]};
-                        const double term[6] = {gv * r3[0], gv * r3[1], gv * r3[2],
-                                                gv * cx_[0], gv * cx_[1], gv * cx_[2]};
+                        if (!S.upd) {
+                            if (S.marginal || bmarg) budget(S, gmax);
+                            continue;
+                        }
                         const bool marg = S.marginal || bmarg;
+                        if (S.clamped && !marg) continue;
+                        const double gv = (*g)[vi] * 1.0 / blk->W[vi];
                         if (!S.clamped) {
+                            // -dz_c/drho = r3 ; -dz_c/domega = -(r3 x p_v) = p_v x r3
+                            const double* p = S.pv;
+                            const double cx_[3] = {p[1] * r3[2] - p[2] * r3[1], p[2] * r3[0] - p[0] * r3[2],
+                                                   p[0] * r3[1] - p[1] * r3[0]};
                             if (gd) gd[S.pix] += gv;
-                            for (int j = 0; j < 6; ++j) gx[j] += term[j];
+                            for (int j = 0; j < 3; ++j) {
+                                gx[j] += gv * r3[j];
+                                gx[3 + j] += gv * cx_[j];
+                            }
                         }
-                        for (int j = 0; j < 6; ++j) max_term[j] = std::max(max_term[j], std::fabs(term[j]));
-                        if (!marg) continue;
-                        if (ex)
-                            for (int j = 0; j < 6; ++j) ex[j] += std::fabs(term[j]);
-                        if (ed) {
-                            const long px = S.pix % W, py = S.pix / W;
-                            for (long dy = -1; dy <= 1; ++dy)
-                                for (long dx = -1; dx <= 1; ++dx) {
-                                    const long yy = py + dy, xx = px + dx;
-                                    if (yy >= 0 && yy < H && xx >= 0 && xx < W) ed[yy * W + xx] += std::fabs(gv);
-                                }
-                        }
+                        // a marginal voxel's W may differ by one on the float32 side
+                        if (marg) budget(S, std::max(std::fabs(gv), gmax));
                     }
         }
-        if (ex)
-            for (int j = 0; j < 6; ++j) ex[j] += (512.0 * (double)n_ghost + (double)n_marg_out) * max_term[j];
     }
     (void)rgba;
     return 0;
