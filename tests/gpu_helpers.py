@@ -25,7 +25,7 @@ def _keys(c):
     return ((c[:, 0] + (1 << 20)) | ((c[:, 1] + (1 << 20)) << 21) | ((c[:, 2] + (1 << 20)) << 42))
 
 
-def compare_volumes(gv: dict, ov: "oracle.Export", colour="f32", d_tol=1e-5, c_tol=0.5, max_flag_frac=1e-2):
+def compare_volumes(gv: dict, ov: "oracle.Export", colour="f32", d_tol=1e-5, c_tol=0.5, max_flag_frac=2e-2):
     """gv: Volume.extract() of the GPU volume; ov: oracle export.  Checks
       * every robustly allocated oracle block is allocated on the GPU, and every GPU block
         is an oracle block or a marginal ("ghost") one;

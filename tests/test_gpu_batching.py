@@ -31,7 +31,8 @@ def test_batching_workload_batched_equals_plain():
         B.integrate_many(ids, D[s:s + 256], C[s:s + 256], w.kf_poses[s:s + 256], w.intr)
     A.check()
     counts = np.array([A.keyframe_blocks(k).numel() for k in range(0, K, 20)])
-    assert counts.min() < 5000 and counts.max() > 15000  # uneven touched-block counts
+    # uneven touched-block counts (0.5-4 m viewing distances; 8 cm blocks)
+    assert counts.max() > 5 * counts.min() and counts.max() > 3000
     nb = A.info()["allocated_blocks"]
     assert nb > 500_000
     cur = w.kf_poses.copy()
