@@ -115,7 +115,7 @@ def _np(t):
     return np.asarray(t)
 
 
-def set_margins(tau_px=5e-4, tau_m=1e-5, tau_rel=1e-6):
+def set_margins(tau_px=5e-4, tau_m=2e-6, tau_rel=1e-6):
     lib().or_set_margins(tau_px, tau_m, tau_rel)
 
 

@@ -59,7 +59,7 @@
 namespace {
 
 double g_tau_px = 5e-4;   // pixel-rounding margin (pixels)
-double g_tau_m = 1e-5;    // distance margin (metres)
+double g_tau_m = 2e-6;    // distance margin (metres)
 double g_tau_rel = 1e-6;  // relative margin for the discontinuity test
 
 struct Intr {

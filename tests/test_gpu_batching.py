@@ -22,7 +22,9 @@ def test_batching_workload_batched_equals_plain():
     w = synthetic.workload_batching(device="cuda")
     K = len(w.kf_poses)
     D, C = w.kf_depth, w.kf_rgba
-    mk = lambda: Volume(w.voxel_size, w.trunc, w.n_buckets, colour="rgba8", max_blocks=1 << 21,
+    # RGB_F32 colour: both paths then carry unrounded colour (in RGBA8 the per-keyframe
+    # path rounds after every de-integration, which divides the rounding error by W'/W)
+    mk = lambda: Volume(w.voxel_size, w.trunc, w.n_buckets, colour="f32", max_blocks=1 << 21,
                         max_keyframes=K, max_blocks_per_keyframe=1 << 16, max_batch=256)
     A, B = mk(), mk()
     for s in range(0, K, 256):
@@ -53,6 +55,4 @@ def test_batching_workload_batched_equals_plain():
     assert torch.equal(ea["W"], eb["W"])
     obs = eb["W"] > 0
     assert (ea["D"] - eb["D"])[obs].abs().max().item() <= 1e-5
-    # RGBA8: the batch rounds once per voxel and update, the plain path per keyframe
-    dc = (ea["C"][..., :3].int() - eb["C"][..., :3].int()).abs()
-    assert dc.max().item() <= 8 and (dc > 1).float().mean().item() < 1e-3
+    assert (ea["C"] - eb["C"])[obs].abs().max().item() <= 0.5
