@@ -279,6 +279,24 @@ int sc_sdf_adjoint(sc_volume* vol, const int32_t* kf_ids, const float* const* de
                    int32_t n, const sc_intrinsics* intr, const float* grad_D, double* grad_xi, float* grad_depth,
                    sc_stream stream);
 
+/* sc_sdf_adjoint without any device-memory allocation by the library (the paper has
+ * no counterpart; this is a deployment variant).  For callers that cannot call
+ * cudaMalloc once running -- a real-time thread with a memory budget fixed at
+ * start-up, code running while a CUDA graph is captured, an application whose
+ * device memory belongs to another allocator.  Same arguments and results as
+ * sc_sdf_adjoint (the caller still passes grad_D, grad_xi and grad_depth); its
+ * keyframe table and accumulators live in a file-scope device array of about 60 KB
+ * that every GPU loading the library holds until the process exits.
+ *   - n <= 256 keyframes; more returns SC_ERR_CAPACITY and launches nothing.
+ *   - The first call on a device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - All calls share the array: calls whose work overlaps on the GPU (other
+ *     streams, other host threads, same device) race and give wrong results;
+ *     serialise them.  Each call clears the accumulators it uses. */
+int sc_sdf_adjoint_noalloc(sc_volume* vol, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
+                           int32_t n, const sc_intrinsics* intr, const float* grad_D, double* grad_xi,
+                           float* grad_depth, sc_stream stream);
+
 /* ------------------------------------------------ keyframe selection (host) ---- */
 
 /* ||s t - s t'|| (Section 4.3) with t = (Z-Y-X Euler angles of R in radians,

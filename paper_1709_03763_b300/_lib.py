@@ -96,6 +96,7 @@ SIGNATURES = {
     "sc_get_keyframe_blocks": (c_i32, [c_p, c_i32, c_p, c_i32, P(c_i32), c_p]),
     "sc_sdf_loss": (c_i32, [c_p, c_p, c_i64, c_f, c_p, c_p, c_p]),
     "sc_sdf_adjoint": (c_i32, [c_p, P(c_i32), P(c_p), P(Pose), c_i32, P(Intrinsics), c_p, c_p, c_p, c_p]),
+    "sc_sdf_adjoint_noalloc": (c_i32, [c_p, P(c_i32), P(c_p), P(Pose), c_i32, P(Intrinsics), c_p, c_p, c_p, c_p]),
     "sc_pose_distance": (c_d, [P(Pose), P(Pose)]),
     "sc_select_topm": (c_i32, [P(c_d), c_i32, c_i32, P(c_i32)]),
     "sc_select_consecutive": (c_i32, [P(c_d), c_i32, c_i32]),

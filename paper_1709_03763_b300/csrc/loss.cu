@@ -359,3 +359,83 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
     V->last_stream = s;
     return SC_OK;
 }
+
+// ---------------------------------------------- allocation-free adjoint ----
+//
+// The same adjoint kernels, with their keyframe table, pose table and double
+// accumulators in a file-scope device array instead of memory this library
+// allocates.  For callers that must not allocate device memory once running: a
+// real-time tracking thread whose memory budget is fixed at start-up, code that
+// runs while a CUDA graph is being captured (cudaMalloc is not allowed there), or
+// a host application whose device memory is owned by another allocator.
+
+namespace {
+
+constexpr int ADJ_STATIC_MAX = 256;  // keyframes per call
+
+struct AdjStatic {
+    AdjItem items[ADJ_STATIC_MAX];
+    AdjPose poses[ADJ_STATIC_MAX];
+    double acc[4 * ADJ_STATIC_MAX];
+};
+
+// host-side device addresses of the scratch array below, one per device (the
+// array's name in host code is a stand-in, not a device address)
+void* g_adj_static_ptr[64] = {nullptr};
+
+}  // namespace
+
+// about 60 KB on every GPU that loads the library, held until the process exits
+static __device__ __align__(256) unsigned char g_adj_static[sizeof(AdjStatic)];
+
+extern "C" int sc_sdf_adjoint_noalloc(sc_volume* V, const int32_t* kf_ids, const float* const* depths,
+                                      const sc_pose* poses, int32_t n, const sc_intrinsics* K, const float* grad_D,
+                                      double* grad_xi, float* grad_depth, sc_stream stream) {
+    if (!V || !kf_ids || !depths || !poses || n < 1 || !intrinsics_ok(K) || !grad_D || !grad_xi)
+        return SC_ERR_INVALID_ARG;
+    if (n > ADJ_STATIC_MAX) return SC_ERR_CAPACITY;
+    for (int i = 0; i < n; ++i) {
+        if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes || !depths[i]) return SC_ERR_INVALID_ARG;
+        if (!V->integrated[kf_ids[i]]) return SC_ERR_NOT_INTEGRATED;
+    }
+    int dev = 0;
+    SC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SC_ERR_INVALID_ARG;
+    if (!g_adj_static_ptr[dev]) {
+        // once per device, with that device current
+        void* p = nullptr;
+        SC_CUDA(cudaGetSymbolAddress(&p, g_adj_static));
+        g_adj_static_ptr[dev] = p;
+    }
+    AdjStatic* S = static_cast<AdjStatic*>(g_adj_static_ptr[dev]);
+    cudaStream_t s = (cudaStream_t)stream;
+    // host tables in pageable memory: cudaMemcpyAsync from pageable memory returns
+    // once the data has been staged, so the buffers can be reused at once
+    static thread_local AdjItem items_h[ADJ_STATIC_MAX];
+    static thread_local AdjPose poses_h[ADJ_STATIC_MAX];
+    const size_t img = (size_t)K->width * K->height;
+    for (int i = 0; i < n; ++i) {
+        const int kf = kf_ids[i];
+        items_h[i].cam = make_cam(V, K, &poses[i], depths[i], nullptr);
+        items_h[i].list = list_ptr(V, kf, V->cur[kf]);
+        items_h[i].count = count_ptr(V, kf, V->cur[kf]);
+        items_h[i].grad_depth = grad_depth ? grad_depth + i * img : nullptr;
+        for (int r = 0; r < 3; ++r) {
+            poses_h[i].r3[r] = (double)poses[i].m[r][2];
+            poses_h[i].t[r] = (double)poses[i].m[r][3];
+        }
+    }
+    SC_CUDA(cudaMemcpyAsync(S->items, items_h, n * sizeof(AdjItem), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaMemcpyAsync(S->poses, poses_h, n * sizeof(AdjPose), cudaMemcpyHostToDevice, s));
+    // the array keeps the previous call's contents: the accumulators start at zero
+    SC_CUDA(cudaMemsetAsync(S->acc, 0, n * 4 * sizeof(double), s));
+    if (grad_depth) SC_CUDA(cudaMemsetAsync(grad_depth, 0, n * img * sizeof(float), s));
+    const int chunks = std::max(1, std::min(64, (V->num_sms * 8 + n - 1) / n));
+    adjoint_kernel<<<dim3(chunks, n), ADJ_THREADS, 0, s>>>(V->dv, S->items, V->p.max_blocks_per_keyframe, grad_D,
+                                                          S->acc);
+    adjoint_finalize_kernel<<<(n + 127) / 128, 128, 0, s>>>(S->poses, S->acc, n, (double)V->p.voxel_size, grad_xi);
+    count_launches(2);
+    SC_CUDA(cudaGetLastError());
+    V->last_stream = s;
+    return SC_OK;
+}
