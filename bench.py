@@ -407,13 +407,14 @@ def main():
     clocks = clk.summary()
     value = ws * P.K / (ms / 1000.0)
 
-    # ---- end to end through the public API with host buffers: per step, the 600 frames
-    # (depth + colour) go host -> device from pinned memory and the loss / block count
-    # come back
+    # ---- end to end through the public API with host buffers: per step, the 600 depth
+    # frames and the 60 keyframe colour images (the only colour the path reads: the
+    # keyframe's colour is its own frame's) go host -> device from pinned memory, and
+    # the loss and block count come back
     h_depth = w.frames_depth.cpu().pin_memory()
-    h_rgba = w.frames_rgba.cpu().pin_memory()
+    h_rgba = P.kf_rgba.cpu().pin_memory()
     h_out = torch.empty(6, dtype=torch.float64).pin_memory()
-    d_depth, d_rgba = w.frames_depth, w.frames_rgba
+    d_depth, d_rgba = w.frames_depth, P.kf_rgba
 
     def e2e_step():
         d_depth.copy_(h_depth, non_blocking=True)
@@ -495,7 +496,7 @@ def main():
             "config": {"workload": "kinect-scale: 600 frames 640x480 fused 10 per keyframe into 60 keyframes, "
                                    "voxel 1 cm, trunc 4 cm, 2^20 buckets, one pose update of all 60, "
                                    "1M-point SDF loss + adjoint, block-list extraction",
-                       "l2": "inputs (1.47 GB frames, ~2 GB voxel state) exceed L2; no flush",
+                       "l2": "inputs (737 MB of depth frames, 74 MB of keyframe colour, 0.3 GB voxel state) exceed L2; no flush",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "colour": "rgba8", "batch_config": cfg},
             "e2e": {"value": ws * P.K / (e2e_ms / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
