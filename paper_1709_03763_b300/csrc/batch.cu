@@ -133,10 +133,64 @@ __global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const
     }
 }
 
+// The part of a keyframe camera the net-delta kernel samples with, kept in shared
+// memory (96 bytes; old cameras of items 0..n-1, then their new cameras).
+struct __align__(16) NdCam {
+    float M[9];
+    float tf[3];
+    int ti[3];
+    float fx, fy, cx, cy, mu;
+    int W, H;
+    const uint2* tex;
+};
+
+__device__ __forceinline__ void load_ndcam(NdCam& o, const KfCam& k) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o.M[i] = k.M[i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        o.tf[i] = k.tf[i];
+        o.ti[i] = k.ti[i];
+    }
+    o.fx = k.fx;
+    o.fy = k.fy;
+    o.cx = k.cx;
+    o.cy = k.cy;
+    o.mu = k.mu;
+    o.W = k.W;
+    o.H = k.H;
+    o.tex = k.tex;
+}
+
+// Packed copies of the items' keyframes: (depth bits, RGBA8) per pixel, so that a
+// sample reads depth and colour with one 8-byte gather.
+__global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr, uint2* tex, uint32_t npx) {
+    const uint32_t q = npx / 4;  // 640 x 480 and every width multiple of 4: float4 / uint4 loads
+    const size_t total = (size_t)hdr->n * q;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int it = (int)(i / q);
+        const uint32_t p = (uint32_t)(i - (size_t)it * q) * 4;
+        const KfCam& k = items[it].newc;
+        const float4 d = __ldg(reinterpret_cast<const float4*>(k.depth + p));
+        const uint4 c = __ldg(reinterpret_cast<const uint4*>(k.rgba + p));
+        uint4* o = reinterpret_cast<uint4*>(tex + (size_t)it * npx + p);
+        o[0] = make_uint4(__float_as_uint(d.x), c.x, __float_as_uint(d.y), c.y);
+        o[1] = make_uint4(__float_as_uint(d.z), c.z, __float_as_uint(d.w), c.w);
+    }
+    // remainder pixels (npx % 4)
+    const uint32_t r0 = q * 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)hdr->n * (npx - r0);
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int it = (int)(i / (npx - r0));
+        const uint32_t p = r0 + (uint32_t)(i % (npx - r0));
+        const KfCam& k = items[it].newc;
+        tex[(size_t)it * npx + p] = make_uint2(__float_as_uint(k.depth[p]), k.rgba[p]);
+    }
+}
+
 // Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over every item whose
 // bit is set in the slot's mask (old bits subtract, new bits add), in item order.
-template <bool F32>
-__device__ __forceinline__ void net_delta_group(const BatchItem* items, const int4 c, int lx0, int ly, int lz,
+__device__ __forceinline__ void net_delta_group(const NdCam* cams, int n, const int4 c, int lx0, int ly, int lz,
                                                 uint32_t mw0, uint32_t mw1, int mw, float aD[4], float aW[4],
                                                 float aC[4][3], bool& touched) {
     const int half = mw / 2;
@@ -147,18 +201,22 @@ __device__ __forceinline__ void net_delta_group(const BatchItem* items, const in
             const int b = __ffs(word) - 1;
             word &= word - 1;
             const int item = ((w < half ? w : w - half) << 5) + b;
-            const KfCam& k = w < half ? items[item].oldc : items[item].newc;
+            const NdCam& k = cams[w < half ? item : n + item];
+            Proj4 P;
+            project4(k, 8 * c.x + lx0, 8 * c.y + ly, 8 * c.z + lz, P);
+            uint2 t[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float d;
-                int pix;
-                if (sample_voxel(k, 8 * c.x + lx0 + j, 8 * c.y + ly, 8 * c.z + lz, d, pix)) {
+                float d, eta;
+                if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
                     touched = true;
                     aD[j] = __fmaf_rn(sgn, d, aD[j]);
                     aW[j] = __fadd_rn(aW[j], sgn);
-                    const uint32_t cc = __ldg(k.rgba + pix);
 #pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) aC[j][ch] = __fmaf_rn(sgn, (float)((cc >> (8 * ch)) & 255u), aC[j][ch]);
+                    for (int ch = 0; ch < 3; ++ch)
+                        aC[j][ch] = __fmaf_rn(sgn, (float)((t[j].y >> (8 * ch)) & 255u), aC[j][ch]);
                 }
             }
         }
@@ -167,9 +225,19 @@ __device__ __forceinline__ void net_delta_group(const BatchItem* items, const in
 
 // Work unit u = (union block u / 4, voxel group u % 4): one warp, 128 voxels, four
 // per lane.  Units come from a queue in chunks of `grab`.
+#ifndef SC_ND_MIN_BLOCKS
+#define SC_ND_MIN_BLOCKS 4  // CTAs of 256 threads per SM the register budget must allow
+#endif
+
 template <bool F32>
-__global__ void net_delta_kernel(DevVolume V, const BatchItem* items, const BatchHeader* hdr, uint32_t* masks,
+__global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVolume V, const BatchItem* items, const BatchHeader* hdr, uint32_t* masks,
                                  int mw, const int32_t* ulist, int32_t* counters, int grab, uint32_t list_cap) {
+    extern __shared__ __align__(16) unsigned char nd_smem[];
+    NdCam* cams = reinterpret_cast<NdCam*>(nd_smem);
+    const int n_items = hdr->n;
+    for (int i = threadIdx.x; i < 2 * n_items; i += blockDim.x)
+        load_ndcam(cams[i], i < n_items ? items[i].oldc : items[i - n_items].newc);
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t n_union = min((uint32_t)counters[0], V.max_blocks);
     const uint32_t n_units = 4 * n_union;
@@ -199,7 +267,7 @@ __global__ void net_delta_kernel(DevVolume V, const BatchItem* items, const Batc
             float aD[4] = {0.f, 0.f, 0.f, 0.f}, aW[4] = {0.f, 0.f, 0.f, 0.f};
             float aC[4][3] = {};
             bool touched = false;
-            net_delta_group<F32>(items, c, lx0, ly, lz, mw0, mw1, mw, aD, aW, aC, touched);
+            net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, aD, aW, aC, touched);
             if (!touched && !fresh) continue;
             const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
             float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
@@ -281,6 +349,8 @@ __global__ void net_delta_clear_kernel(DevVolume V, uint32_t* masks, int mw, con
 struct BatchState {
     int mw = 0;
     int32_t* zero = nullptr;  // a device word holding 0: the old-list length of integrate-only items
+    uint2* tex = nullptr;     // packed keyframe images [max_batch][tex_px]
+    uint32_t tex_px = 0;
     uint32_t* masks = nullptr;
     int32_t* ulist = nullptr;
     int32_t* counters = nullptr;
@@ -307,6 +377,7 @@ void batch_destroy(sc_volume* V) {
     if (B->ulist) cudaFree(B->ulist);
     if (B->counters) cudaFree(B->counters);
     if (B->zero) cudaFree(B->zero);
+    if (B->tex) cudaFree(B->tex);
     if (B->items_d) cudaFree(B->items_d);
     if (B->hdr_d) cudaFree(B->hdr_d);
     if (B->items_h) cudaFreeHost(B->items_h);
@@ -316,6 +387,8 @@ void batch_destroy(sc_volume* V) {
 }
 
 namespace {
+
+size_t nd_smem_bytes(sc_volume* V);
 
 int batch_init(sc_volume* V) {
     if (V->batch) return SC_OK;
@@ -334,16 +407,24 @@ int batch_init(sc_volume* V) {
     SC_CUDA(cudaMallocHost((void**)&B->items_h, (size_t)V->p.max_batch * sizeof(BatchItem)));
     SC_CUDA(cudaMallocHost((void**)&B->hdr_h, sizeof(BatchHeader)));
     SC_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+    const size_t smem = nd_smem_bytes(V);
+    if (smem > 48 * 1024) {
+        SC_CUDA(cudaFuncSetAttribute(net_delta_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        SC_CUDA(cudaFuncSetAttribute(net_delta_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    }
     V->device_bytes += mbytes + (size_t)V->p.max_blocks * 4 + (size_t)V->p.max_batch * sizeof(BatchItem);
     return SC_OK;
 }
 
+size_t nd_smem_bytes(sc_volume* V) { return (size_t)2 * V->p.max_batch * sizeof(NdCam); }
+
 int ctas_per_sm_clamped(sc_volume* V, const sc_batch_config& c) {
     int occ = 0;
     const int threads = 32 * c.warps_per_cta;
+    const size_t smem = nd_smem_bytes(V);
     cudaError_t e = V->p.colour_format == SC_RGB_F32
-                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_delta_kernel<true>, threads, 0)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_delta_kernel<false>, threads, 0);
+                        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_delta_kernel<true>, threads, smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, net_delta_kernel<false>, threads, smem);
     if (e != cudaSuccess || occ < 1) occ = 1;
     return std::max(1, std::min(c.ctas_per_sm, occ));
 }
@@ -366,6 +447,7 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
         *items_node = deps[0];
     }
     batch_init_kernel<<<4, 256, 0, s>>>(B->items_d, B->hdr_d, B->counters);
+    batch_pack_kernel<<<V->num_sms * 8, 256, 0, s>>>(B->items_d, B->hdr_d, B->tex, B->tex_px);
     if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[0], s, cudaEventRecordExternal);
     batch_alloc_kernel<<<V->num_sms * ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
         V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
@@ -377,11 +459,11 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
     const int grid = V->num_sms * ctas_per_sm_clamped(V, c);
     const uint32_t cap = V->p.max_blocks_per_keyframe;
     if (V->p.colour_format == SC_RGB_F32)
-        net_delta_kernel<true><<<grid, 32 * c.warps_per_cta, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw,
-                                                                    B->ulist, B->counters, c.blocks_per_grab, cap);
+        net_delta_kernel<true><<<grid, 32 * c.warps_per_cta, nd_smem_bytes(V), s>>>(
+            V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, c.blocks_per_grab, cap);
     else
-        net_delta_kernel<false><<<grid, 32 * c.warps_per_cta, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw,
-                                                                     B->ulist, B->counters, c.blocks_per_grab, cap);
+        net_delta_kernel<false><<<grid, 32 * c.warps_per_cta, nd_smem_bytes(V), s>>>(
+            V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, c.blocks_per_grab, cap);
     if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[3], s, cudaEventRecordExternal);
     net_delta_clear_kernel<<<V->num_sms * 4, 256, 0, s>>>(V->dv, B->masks, B->mw, B->ulist, B->counters);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -450,6 +532,19 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
     int rc = batch_init(V);
     if (rc) return rc;
     BatchState* B = V->batch;
+    const uint32_t npx = (uint32_t)K->width * (uint32_t)K->height;
+    if (npx != B->tex_px) {
+        // packed keyframe images for this image size; the graph captured the old buffer
+        if (B->tex) cudaFree(B->tex);
+        B->tex = nullptr;
+        B->tex_px = 0;
+        SC_CUDA(cudaMalloc((void**)&B->tex, (size_t)V->p.max_batch * npx * sizeof(uint2)));
+        B->tex_px = npx;
+        if (B->exec) {
+            cudaGraphExecDestroy(B->exec);
+            B->exec = nullptr;
+        }
+    }
     for (int i = 0; i < n; ++i) {
         const ItemSpec& it = items[i];
         BatchItem& b = B->items_h[i];
@@ -460,6 +555,7 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         b.old_count = it.oldp ? count_ptr(V, it.kf_id, cur) : B->zero;
         b.new_list = list_ptr(V, it.kf_id, 1 - cur);
         b.new_count = count_ptr(V, it.kf_id, 1 - cur);
+        b.oldc.tex = b.newc.tex = B->tex + (size_t)i * npx;
     }
     if (++V->call_id == 0) V->call_id = 1;  // (plain calls reset stamps on wrap)
     B->hdr_h->n = n;
@@ -482,7 +578,7 @@ int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_
     return prepare_specs(V, sp.data(), n, K);
 }
 
-constexpr int GRAPH_KERNELS = 5;  // init, batched allocation, mark old, net-delta, clear
+constexpr int GRAPH_KERNELS = 6;  // init, pack, batched allocation, mark old, net-delta, clear
 
 int launch_and_check(sc_volume* V, cudaStream_t s) {
     SC_CUDA(cudaGraphLaunch(V->batch->exec, s));

@@ -101,34 +101,50 @@ struct KfCam {
     float mu;
     const float* depth;
     const uint32_t* rgba;  // RGBA8 as one 32-bit word per pixel
+    const uint2* tex;      // (depth bits, RGBA8) per pixel, where a packed copy exists
 };
 
-// Projective sample of voxel (ix, iy, iz) in the keyframe: returns true when the
-// voxel is updated, with d = min(eta, mu) and the sampled pixel.  Every
-// operation is an explicit round-to-nearest intrinsic so that integration,
-// de-integration, the batched net-delta kernel and the adjoint reach bit-identical
-// decisions and distances for the same keyframe and pose.
-__device__ __forceinline__ bool sample_voxel(const KfCam& k, int ix, int iy, int iz, float& d, int& pix,
-                                             float* eta_out = nullptr) {
-    const float qx = __fsub_rn((float)(ix - k.ti[0]), k.tf[0]);
+// Projection of the 4 voxels (ix0 + j, iy, iz), j = 0..3, that one thread owns.
+// Every operation is an explicit round-to-nearest intrinsic, in one fixed order, so
+// that integration, de-integration, the batched net-delta kernel and the adjoint
+// reach bit-identical decisions and distances for the same keyframe and pose.
+// ok[j]: in front of the camera and the nearest pixel (halves rounded up) inside
+// the image; pix[j] is only meaningful when ok[j].  Computing all four first lets
+// the caller issue the four depth gathers back to back.
+struct Proj4 {
+    float pz[4];
+    int pix[4];
+    bool ok[4];
+};
+
+template <typename Cam>
+__device__ __forceinline__ void project4(const Cam& k, int ix0, int iy, int iz, Proj4& p) {
     const float qy = __fsub_rn((float)(iy - k.ti[1]), k.tf[1]);
     const float qz = __fsub_rn((float)(iz - k.ti[2]), k.tf[2]);
-    const float pz = __fmaf_rn(k.M[8], qz, __fmaf_rn(k.M[7], qy, __fmul_rn(k.M[6], qx)));
-    if (!(pz > 0.f)) return false;
-    const float px = __fmaf_rn(k.M[2], qz, __fmaf_rn(k.M[1], qy, __fmul_rn(k.M[0], qx)));
-    const float py = __fmaf_rn(k.M[5], qz, __fmaf_rn(k.M[4], qy, __fmul_rn(k.M[3], qx)));
-    const float rz = __frcp_rn(pz);
-    // nearest pixel, halves rounded up: floor(u + 1/2); NaN / inf fail the range test
-    const float uu = __fadd_rn(__fmaf_rn(__fmul_rn(k.fx, px), rz, k.cx), 0.5f);
-    const float vv = __fadd_rn(__fmaf_rn(__fmul_rn(k.fy, py), rz, k.cy), 0.5f);
-    if (!(uu >= 0.f && uu < (float)k.W && vv >= 0.f && vv < (float)k.H)) return false;
-    pix = (int)vv * k.W + (int)uu;
-    const float Z = __ldg(k.depth + pix);
-    if (!(Z > 0.f)) return false;
-    const float eta = __fsub_rn(Z, pz);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float qx = __fsub_rn((float)(ix0 + j - k.ti[0]), k.tf[0]);
+        const float pz = __fmaf_rn(k.M[8], qz, __fmaf_rn(k.M[7], qy, __fmul_rn(k.M[6], qx)));
+        const float px = __fmaf_rn(k.M[2], qz, __fmaf_rn(k.M[1], qy, __fmul_rn(k.M[0], qx)));
+        const float py = __fmaf_rn(k.M[5], qz, __fmaf_rn(k.M[4], qy, __fmul_rn(k.M[3], qx)));
+        const float rz = __frcp_rn(pz);
+        // NaN / inf fail the range test
+        const float uu = __fadd_rn(__fmaf_rn(__fmul_rn(k.fx, px), rz, k.cx), 0.5f);
+        const float vv = __fadd_rn(__fmaf_rn(__fmul_rn(k.fy, py), rz, k.cy), 0.5f);
+        p.pz[j] = pz;
+        p.ok[j] = pz > 0.f && uu >= 0.f && uu < (float)k.W && vv >= 0.f && vv < (float)k.H;
+        p.pix[j] = p.ok[j] ? (int)vv * k.W + (int)uu : 0;
+    }
+}
+
+// The update decision for one projected voxel given the keyframe depth Z at its
+// pixel: updated iff Z > 0 and eta = Z - z_c >= -mu; then d = min(eta, mu).
+template <typename Cam>
+__device__ __forceinline__ bool decide(const Cam& k, bool ok, float Z, float pz, float& d, float& eta) {
+    if (!ok || !(Z > 0.f)) return false;
+    eta = __fsub_rn(Z, pz);
     if (eta < -k.mu) return false;
     d = fminf(eta, k.mu);
-    if (eta_out) *eta_out = eta;
     return true;
 }
 

@@ -211,12 +211,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
             int lx0, ly, lz;
             lane_voxels(lane, g, lx0, ly, lz);
             const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+            const int iy = 8 * c.y + ly, iz = 8 * c.z + lz;
+            Proj4 P;
+            project4(cam, 8 * c.x + lx0, iy, iz, P);
+            float Z[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Z[j] = P.ok[j] ? __ldg(cam.depth + P.pix[j]) : 0.f;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 float d, eta;
-                int pix;
-                const int ix = 8 * c.x + lx0 + j, iy = 8 * c.y + ly, iz = 8 * c.z + lz;
-                if (!sample_voxel(cam, ix, iy, iz, d, pix, &eta)) continue;
+                const int pix = P.pix[j];
+                const int ix = 8 * c.x + lx0 + j;
+                if (!decide(cam, P.ok[j], Z[j], P.pz[j], d, eta)) continue;
                 if (!(eta < cam.mu)) continue;  // clamped: no derivative
                 const float gv = __fdiv_rn(grad[off + j], V.W[off + j]);
                 if (gv == 0.f) continue;

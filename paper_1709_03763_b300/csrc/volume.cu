@@ -65,6 +65,7 @@ KfCam make_cam(const sc_volume* V, const sc_intrinsics* K, const sc_pose* T, con
     c.mu = V->p.trunc;
     c.depth = depth;
     c.rgba = (const uint32_t*)rgba;
+    c.tex = nullptr;
     return c;
 }
 
@@ -127,16 +128,22 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam 
             __syncthreads();  // every thread has read the flag before it is cleared
             if (fresh && t == 0) V.flags[slot] = 0;
         }
-        float d[4];
-        int pix[4];
+        Proj4 P;
+        project4(k, 8 * c.x + lx0, 8 * c.y + ly, 8 * c.z + lz, P);
+        float Z[4], d[4], eta;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) Z[j] = P.ok[j] ? __ldg(k.depth + P.pix[j]) : 0.f;
         bool up[4];
         bool any = false;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            up[j] = sample_voxel(k, 8 * c.x + lx0 + j, 8 * c.y + ly, 8 * c.z + lz, d[j], pix[j]);
+            up[j] = decide(k, P.ok[j], Z[j], P.pz[j], d[j], eta);
             any |= up[j];
         }
         if (!any && !fresh) continue;
+        uint32_t cc[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cc[j] = up[j] ? __ldg(k.rgba + P.pix[j]) : 0u;
         const size_t off = (size_t)slot * NVOX + 4 * t;
         float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
         if (!fresh) {
@@ -155,10 +162,9 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!up[j]) continue;
-                const uint32_t cc = __ldg(k.rgba + pix[j]);
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch)
-                    (&Cv[ch].x)[j] = update_cf((&Cv[ch].x)[j], Wp[j], (float)((cc >> (8 * ch)) & 255u), SIGN);
+                    (&Cv[ch].x)[j] = update_cf((&Cv[ch].x)[j], Wp[j], (float)((cc[j] >> (8 * ch)) & 255u), SIGN);
                 update_dw(Dp[j], Wp[j], d[j], SIGN);
             }
 #pragma unroll
@@ -170,8 +176,7 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam 
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (!up[j]) continue;
-                const uint32_t cc = __ldg(k.rgba + pix[j]);
-                Cp[j] = update_c8(Cp[j], Wp[j], cc, SIGN);
+                Cp[j] = update_c8(Cp[j], Wp[j], cc[j], SIGN);
                 update_dw(Dp[j], Wp[j], d[j], SIGN);
             }
             *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
