@@ -24,6 +24,9 @@ namespace sc {
 #ifndef SC_ALLOC_WARP_DEDUPE
 #define SC_ALLOC_WARP_DEDUPE 0
 #endif
+#ifndef SC_ALLOC_CTAS_PER_SM
+#define SC_ALLOC_CTAS_PER_SM 8  // resident allocation CTAs per SM (caps registers at 32)
+#endif
 constexpr int ALLOC_TX = 32;           // pixel tile 32 x SC_ALLOC_TY, one CTA of 256 threads,
 constexpr int ALLOC_TY = SC_ALLOC_TY;  // SC_ALLOC_TY / 8 pixels (rows r, r+8, ...) per thread
 constexpr int ALLOC_THREADS = 256;
@@ -191,22 +194,14 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
         const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
         float Z = 0.f;
         if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
-        if (!(Z > 0.f && Z < MAX_DEPTH)) continue;
-        for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
+        auto ins = [&](int bx, int by, int bz) {
             if (!coord_ok(bx, by, bz)) {
                 set_status(V.status, SC_ERR_INVALID_ARG);
                 return;
             }
-            // neighbouring pixels of a warp mostly reach the same blocks: one insert
-            // per distinct key among the lanes active here
-            const unsigned long long key = pack_key(bx, by, bz);
-#if SC_ALLOC_WARP_DEDUPE
-            const unsigned grp = __match_any_sync(__activemask(), key);
-            if ((threadIdx.x & 31) == __ffs(grp) - 1 && !set_insert(sh.set, key)) my_ovf = true;
-#else
-            if (!set_insert(sh.set, key)) my_ovf = true;
-#endif
-        });
+            if (!set_insert(sh.set, pack_key(bx, by, bz))) my_ovf = true;
+        };
+        if (Z > 0.f && Z < MAX_DEPTH) for_each_segment_block(k, u, v, Z, ins);
     }
     if (my_ovf) sh.overflow = 1;
     __syncthreads();

@@ -53,7 +53,7 @@ struct BatchHeader {
     int32_t tiles;
 };
 
-constexpr int ALLOC_CTAS_PER_SM = 4;
+constexpr int ALLOC_CTAS_PER_SM = SC_ALLOC_CTAS_PER_SM;  // persistent allocation CTAs per SM
 
 struct BatchSink {
     static constexpr bool kUnion = true;
@@ -82,7 +82,7 @@ __global__ void batch_init_kernel(const BatchItem* items, const BatchHeader* hdr
     if (blockIdx.x == 0 && threadIdx.x < 4) counters[threadIdx.x] = 0;
 }
 
-__global__ void __launch_bounds__(ALLOC_THREADS) batch_alloc_kernel(DevVolume V, const BatchItem* items,
+__global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) batch_alloc_kernel(DevVolume V, const BatchItem* items,
                                                                     const BatchHeader* hdr, uint32_t* masks, int mw,
                                                                     int32_t* ulist, int32_t* counters,
                                                                     uint32_t list_cap) {
