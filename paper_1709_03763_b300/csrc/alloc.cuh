@@ -104,10 +104,15 @@ __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, floa
     }
 }
 
+// Slot of a key in the CTA's shared set (Fibonacci hashing: one multiply).
+__device__ __forceinline__ uint32_t set_hash(unsigned long long key) {
+    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (SET_SIZE - 1);
+}
+
 // Insert into the CTA's shared set.  Most inserts find their key already there:
 // read before CAS so that those do not serialise on the shared atomic unit.
 __device__ inline bool set_insert(unsigned long long* set, unsigned long long key) {
-    uint32_t h = hash_bucket(key, SET_SIZE - 1);
+    uint32_t h = set_hash(key);
     for (int i = 0; i < SET_SIZE; ++i) {
         unsigned long long k = ((volatile unsigned long long*)set)[h];
         if (k == key) return true;
@@ -121,7 +126,7 @@ __device__ inline bool set_insert(unsigned long long* set, unsigned long long ke
 }
 
 __device__ inline bool set_contains(const unsigned long long* set, unsigned long long key) {
-    uint32_t h = hash_bucket(key, SET_SIZE - 1);
+    uint32_t h = set_hash(key);
     for (int i = 0; i < SET_SIZE; ++i) {
         const unsigned long long k = set[h];
         if (k == key) return true;

@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
 #pragma unroll
     for (int r = 0; r < 3; ++r) ps[r] = fmaf(F.R[3 * r], P[0], fmaf(F.R[3 * r + 1], P[1], fmaf(F.R[3 * r + 2], P[2], F.t[r])));
     if (!(ps[2] > 0.f)) return;
-    const float rz = __frcp_rn(ps[2]);
+    // approximate reciprocal (2 ulp): a few 1e-5 px at the nearest-pixel rounding
+    const float rz = __fdividef(1.f, ps[2]);
     const float uu = fmaf(c.fx * ps[0], rz, c.cx) + 0.5f;
     const float vv = fmaf(c.fy * ps[1], rz, c.cy) + 0.5f;
     if (!(uu >= 0.f && uu < (float)W && vv >= 0.f && vv < (float)H)) return;
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
                 nz = diff_of_products(ax, by, ay, bx);
     const float n2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
     if (!(n2 > 0.f)) return;
-    const float w = fabsf(nz) * rsqrtf(n2) * __frcp_rn(z * z);
+    const float w = __fdividef(fabsf(nz) * rsqrtf(n2), z * z);
     atomicAdd(S + q, w * ps[2]);
     atomicAdd(Wsum + q, w);
 }
