@@ -5,7 +5,7 @@
 // x*, and accumulated as sum(w_z Z*_p) and sum(w_z) with w_z = cos(theta) / Z^2.
 // Applying Eq. 1 sequentially gives exactly that ratio of sums, so the kernel
 // scatters both sums with float atomics (order-free up to rounding) and a second
-// pass divides.  One thread per (frame pixel); all frames of a call in one launch.
+// pass divides.  One thread per 4 pixels of a frame row; up to 64 frames per launch.
 #include <cmath>
 
 #include "volume.cuh"
@@ -38,20 +38,14 @@ struct FuseCam {
     float fx, fy, cx, cy, ifx, ify;  // ifx = 1/fx, ify = 1/fy
     int W, H;
     float disc_rel;
+    float* S;     // sum w_z Z*_p (in the Z* output until normalised)
+    float* Wsum;  // sum w_z (the W* output)
 };
 
-__global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __restrict__ depths, FuseArgs a,
-                                                                 FuseCam c, float* S, float* Wsum) {
-    const int u = blockIdx.x * FUSE_TX + threadIdx.x;
-    const int v = blockIdx.y * FUSE_TY + threadIdx.y;
-    const int W = c.W, H = c.H;
-    if (u < 1 || v < 1 || u >= W - 1 || v >= H - 1) return;  // border pixels have no full neighbourhood
-    const FuseFrame& F = a.f[blockIdx.z];
-    const float* Z = depths + (size_t)blockIdx.z * W * H;
-    const size_t p = (size_t)v * W + u;
-    const float z = __ldg(Z + p);
+// Eq. 1 contribution of one frame pixel (u, v) with depth z and 4-neighbours.
+__device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c, int u, int v, float z, float zl,
+                                           float zr, float zu, float zd, float* S, float* Wsum) {
     if (!(z > 0.f)) return;
-    const float zl = __ldg(Z + p - 1), zr = __ldg(Z + p + 1), zu = __ldg(Z + p - W), zd = __ldg(Z + p + W);
     if (!(zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f)) return;
     const float lim = c.disc_rel * z;
     if (fabsf(zl - z) > lim || fabsf(zr - z) > lim || fabsf(zu - z) > lim || fabsf(zd - z) > lim) return;
@@ -66,8 +60,8 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     const float rz = __fdividef(1.f, ps[2]);
     const float uu = fmaf(c.fx * ps[0], rz, c.cx) + 0.5f;
     const float vv = fmaf(c.fy * ps[1], rz, c.cy) + 0.5f;
-    if (!(uu >= 0.f && uu < (float)W && vv >= 0.f && vv < (float)H)) return;
-    const size_t q = (size_t)F.kf * W * H + (size_t)(int)vv * W + (int)uu;
+    if (!(uu >= 0.f && uu < (float)c.W && vv >= 0.f && vv < (float)c.H)) return;
+    const size_t q = (size_t)F.kf * c.W * c.H + (size_t)(int)vv * c.W + (int)uu;
     // w_z = cos(theta) / Z^2, theta from the central-difference normal
     // a = P(u+1,v) - P(u-1,v), b = P(u,v+1) - P(u,v-1), written as
     // x (z_r - z_l) + (z_r + z_l) / fx etc. so that no large terms cancel
@@ -85,6 +79,44 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     const float w = __fdividef(fabsf(nz) * rsqrtf(n2), z * z);
     atomicAdd(S + q, w * ps[2]);
     atomicAdd(Wsum + q, w);
+}
+
+// One thread per 4 consecutive pixels of a row (u0 = 4 * thread): the row and its two
+// neighbour rows come in as float4 loads plus the two pixels beyond the ends.
+// Border pixels have no full neighbourhood and are skipped.  Width multiple of 4.
+__global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __restrict__ depths, FuseArgs a,
+                                                                 FuseCam c) {
+    const int W = c.W, H = c.H;
+    const int u0 = 4 * (blockIdx.x * FUSE_TX + threadIdx.x);
+    const int v = blockIdx.y * FUSE_TY + threadIdx.y;
+    if (u0 >= W || v < 1 || v >= H - 1) return;
+    const FuseFrame F = a.f[blockIdx.z];
+    const float* Z = depths + (size_t)blockIdx.z * W * H + (size_t)v * W + u0;
+    const float4 row = __ldg(reinterpret_cast<const float4*>(Z));
+    const float4 up = __ldg(reinterpret_cast<const float4*>(Z - W));
+    const float4 dn = __ldg(reinterpret_cast<const float4*>(Z + W));
+    const float left = u0 > 0 ? __ldg(Z - 1) : 0.f;
+    const float right = u0 + 4 < W ? __ldg(Z + 4) : 0.f;
+    float* S = c.S;
+    float* Ws = c.Wsum;
+    if (u0 > 0) fuse_pixel(F, c, u0, v, row.x, left, row.y, up.x, dn.x, S, Ws);
+    fuse_pixel(F, c, u0 + 1, v, row.y, row.x, row.z, up.y, dn.y, S, Ws);
+    fuse_pixel(F, c, u0 + 2, v, row.z, row.y, row.w, up.z, dn.z, S, Ws);
+    if (u0 + 4 < W) fuse_pixel(F, c, u0 + 3, v, row.w, row.z, right, up.w, dn.w, S, Ws);
+}
+
+// Any width: one thread per pixel.
+__global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel_any(const float* __restrict__ depths, FuseArgs a,
+                                                                     FuseCam c) {
+    const int u = blockIdx.x * FUSE_TX + threadIdx.x;
+    const int v = blockIdx.y * FUSE_TY + threadIdx.y;
+    const int W = c.W, H = c.H;
+    if (u < 1 || v < 1 || u >= W - 1 || v >= H - 1) return;
+    const FuseFrame& F = a.f[blockIdx.z];
+    const float* Z = depths + (size_t)blockIdx.z * W * H;
+    const size_t p = (size_t)v * W + u;
+    fuse_pixel(F, c, u, v, __ldg(Z + p), __ldg(Z + p - 1), __ldg(Z + p + 1), __ldg(Z + p - W), __ldg(Z + p + W), c.S,
+               c.Wsum);
 }
 
 __global__ void fuse_normalise_kernel(float* Z, const float* Wsum, size_t n) {
@@ -113,7 +145,8 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
     const size_t npx = (size_t)W * H;
     SC_CUDA(cudaMemsetAsync(kf_depth, 0, n_kf * npx * sizeof(float), s));
     SC_CUDA(cudaMemsetAsync(kf_weight, 0, n_kf * npx * sizeof(float), s));
-    FuseCam c{K->fx, K->fy, K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), W, H, fusion->disc_rel};
+    FuseCam c{K->fx, K->fy, K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), W, H, fusion->disc_rel,
+              kf_depth, kf_weight};
     for (int f0 = 0; f0 < n; f0 += FUSE_MAX_FRAMES) {
         const int nf = (n - f0) < FUSE_MAX_FRAMES ? (n - f0) : FUSE_MAX_FRAMES;
         FuseArgs a;
@@ -135,8 +168,13 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
             a.f[f].kf = kf;
         }
         dim3 block(FUSE_TX, FUSE_TY);
-        dim3 grid((W + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
-        fuse_kernel<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c, kf_depth, kf_weight);
+        if (W % 4 == 0) {
+            dim3 grid((W / 4 + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
+            fuse_kernel<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c);
+        } else {
+            dim3 grid((W + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
+            fuse_kernel_any<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c);
+        }
         sc::count_launches(1);
         SC_CUDA(cudaGetLastError());
     }
