@@ -336,6 +336,12 @@ typedef struct {
     int64_t batch_pairs;        /* sum over batches of old + new block-list lengths */
 } sc_profile;
 
+/* Process-wide timing of the fusion launches: enable 1 / 0 resets the counters and
+ * switches timing on / off, -1 only reads.  Outputs (host, may be NULL): summed
+ * milliseconds, fusion launches and frames since the last reset.  Synchronises on
+ * the recorded events. */
+int sc_fusion_profile(int32_t enable, double* ms, int64_t* launches, int64_t* frames);
+
 /* Enable (1) or disable (0) timing; either way the counters are reset. */
 int sc_set_profiling(sc_volume* vol, int32_t enabled);
 /* Read the counters (synchronises the volume's last stream). */

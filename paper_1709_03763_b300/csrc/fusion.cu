@@ -7,6 +7,8 @@
 // scatters both sums with float atomics (order-free up to rounding) and a second
 // pass divides.  One thread per 4 pixels of a frame row; up to 64 frames per launch.
 #include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "volume.cuh"
 
@@ -33,6 +35,23 @@ struct FuseFrame {
 struct FuseArgs {
     FuseFrame f[FUSE_MAX_FRAMES];
 };
+
+// process-wide timing of the fusion launches (sc_fusion_profile)
+struct FuseProf {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> ev;  // pairs around each fuse_kernel launch
+    std::vector<int> frames;
+    double ms = 0.0;
+    int64_t launches = 0, nframes = 0;
+} g_fprof;
+
+cudaEvent_t fprof_event(cudaStream_t s) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    cudaEventRecord(e, s);
+    return e;
+}
 
 struct FuseCam {
     float fx, fy, cx, cy, ifx, ify;  // ifx = 1/fx, ify = 1/fy
@@ -168,12 +187,23 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
             a.f[f].kf = kf;
         }
         dim3 block(FUSE_TX, FUSE_TY);
+        cudaEvent_t e0 = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(g_fprof.mu);
+            if (g_fprof.on) e0 = fprof_event(s);
+        }
         if (W % 4 == 0) {
             dim3 grid((W / 4 + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
             fuse_kernel<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c);
         } else {
             dim3 grid((W + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
             fuse_kernel_any<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c);
+        }
+        if (e0) {
+            std::lock_guard<std::mutex> lock(g_fprof.mu);
+            g_fprof.ev.push_back(e0);
+            g_fprof.ev.push_back(fprof_event(s));
+            g_fprof.frames.push_back(nf);
         }
         sc::count_launches(1);
         SC_CUDA(cudaGetLastError());
@@ -185,6 +215,33 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
 }
 
 }  // namespace
+
+extern "C" int sc_fusion_profile(int32_t enable, double* ms, int64_t* launches, int64_t* frames) {
+    std::lock_guard<std::mutex> lock(g_fprof.mu);
+    for (size_t i = 0; i + 1 < g_fprof.ev.size(); i += 2) {
+        SC_CUDA(cudaEventSynchronize(g_fprof.ev[i + 1]));
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, g_fprof.ev[i], g_fprof.ev[i + 1]) == cudaSuccess) {
+            g_fprof.ms += t;
+            g_fprof.launches += 1;
+            g_fprof.nframes += g_fprof.frames[i / 2];
+        }
+        cudaEventDestroy(g_fprof.ev[i]);
+        cudaEventDestroy(g_fprof.ev[i + 1]);
+    }
+    g_fprof.ev.clear();
+    g_fprof.frames.clear();
+    if (ms) *ms = g_fprof.ms;
+    if (launches) *launches = g_fprof.launches;
+    if (frames) *frames = g_fprof.nframes;
+    if (enable >= 0) {  // -1: read only; 0 / 1: reset and switch off / on
+        g_fprof.on = enable != 0;
+        g_fprof.ms = 0.0;
+        g_fprof.launches = 0;
+        g_fprof.nframes = 0;
+    }
+    return SC_OK;
+}
 
 extern "C" int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses, int32_t n,
                                             const sc_pose* kf_pose, const sc_intrinsics* K,

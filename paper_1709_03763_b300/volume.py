@@ -330,6 +330,16 @@ def fuse_keyframes(depths: torch.Tensor, frame_poses=None, frame_kf=None, kf_pos
     return out_depth, out_weight
 
 
+def fusion_profile(enable: int = -1) -> dict:
+    """Fusion launch timing: enable=1 resets and starts, 0 resets and stops, -1 reads."""
+    ms = ctypes.c_double(0)
+    n = ctypes.c_int64(0)
+    f = ctypes.c_int64(0)
+    check(lib().sc_fusion_profile(int(enable), ctypes.byref(ms), ctypes.byref(n), ctypes.byref(f)),
+          "sc_fusion_profile")
+    return {"ms": ms.value, "launches": n.value, "frames": f.value}
+
+
 def pose_distance(a, b) -> float:
     pa, pb = make_pose(a), make_pose(b)
     return lib().sc_pose_distance(ctypes.byref(pa), ctypes.byref(pb))
