@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=20, help="keyframe re-integrations the oracle times")
+    ap.add_argument("--cpu-sample", type=int, default=60, help="keyframe re-integrations the oracle times per step")
     ap.add_argument("--profile-region", action="store_true",
                     help="run --steps steps between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints only the timing")
@@ -91,7 +91,7 @@ def _busy_wait(seconds):
 
 
 class Clocks:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 50 ms while the timed region runs."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -107,7 +107,7 @@ class Clocks:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                          "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -341,11 +341,12 @@ def oracle_reintegration(n_kf, steps=1, warmup=0, w=None):
     return statistics.median(times), oracle.get_threads()
 
 
-def cpu_baseline(n_kf, w):
-    dt, cores = oracle_reintegration(n_kf, w=w)
+def cpu_baseline(n_kf, w, reps=3):
+    dt, cores = oracle_reintegration(n_kf, steps=reps, w=w)
     return {"value": n_kf / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_kf} keyframe re-integrations (de-integrate at drifted pose + integrate at true pose, "
-                      f"allocation included) of the 640x480 / 1 cm workload, RGBA8 colour, FP64, {dt:.1f} s"}
+                      f"allocation included) of the 640x480 / 1 cm workload, RGBA8 colour, FP64; median of "
+                      f"{reps} passes, {dt:.1f} s each"}
 
 
 def run_reference(args):
