@@ -83,6 +83,14 @@ def _declare(L):
     L.or_grad.restype = _i
     L.or_loss_perturbed.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _l, _d]
     L.or_loss_perturbed.restype = _d
+    L.or_colour_unsharp.argtypes = [_p, _i, _i, _p]
+    L.or_colour_blurriness.argtypes = [_p, _i, _i]
+    L.or_colour_blurriness.restype = _d
+    L.or_weighted_median.argtypes = [_p, _p, _i]
+    L.or_weighted_median.restype = _d
+    L.or_fuse_colour.argtypes = [_p, _p, _p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _d, _d,
+                                 _p, _p, _p, _p, _p, _p, _p]
+    L.or_fuse_colour.restype = _i
 
 
 def _ptr(a):
@@ -140,6 +148,57 @@ def fuse(depths, poses, kf_pose, intr, disc_rel=0.1):
     fx, fy, cx, cy = _intr(intr)
     lib().or_fuse(_ptr(d), _ptr(p), n, _ptr(k), fx, fy, cx, cy, W, H, f32(disc_rel), _ptr(Zs), _ptr(Ws), _ptr(fl))
     return Zs, Ws, fl
+
+
+def unsharp(rgba):
+    """Unsharp masking of one [H,W,4] uint8 image -> [H,W,3] f64 in [0, 255]."""
+    c = _u8(_np(rgba))
+    H, W = c.shape[:2]
+    S = np.zeros((H, W, 3), np.float64)
+    lib().or_colour_unsharp(_ptr(c), W, H, _ptr(S))
+    return S
+
+
+def blurriness(rgba) -> float:
+    """Blurriness in [0, 1] of one [H,W,4] uint8 image (0 = sharp); w_b = 1 - blurriness."""
+    c = _u8(_np(rgba))
+    H, W = c.shape[:2]
+    return lib().or_colour_blurriness(_ptr(c), W, H)
+
+
+def weighted_median(values, weights) -> float:
+    v = np.ascontiguousarray(values, np.float64)
+    w = np.ascontiguousarray(weights, np.float64)
+    return lib().or_weighted_median(_ptr(v), _ptr(w), len(v))
+
+
+@dataclass
+class ColourFusion:
+    median: np.ndarray   # [H,W,3] f64 weighted median per channel
+    err: np.ndarray      # [H,W,3] f64 bound on its move under tau_px sample moves
+    rgba: np.ndarray     # [H,W,4] u8 keyframe colour C*
+    nobs: np.ndarray     # [H,W] i32 observations per pixel
+    wsum: np.ndarray     # [H,W] f64 total colour weight
+    flag: np.ndarray     # [H,W] u8 marginal decision
+    wb: np.ndarray       # [n] f64 per-frame weight w_b
+
+
+def fuse_colour(rgba, depths, poses, kf_depth, kf_pose, intr, disc_rel=0.1, occl_rel=0.05) -> ColourFusion:
+    """Colour keyframe fusion of frames (rgba [n,H,W,4] u8, depths [n,H,W], poses [n,3,4])
+    into the keyframe with depth kf_depth [H,W] at kf_pose."""
+    c = _u8(_np(rgba))
+    n, H, W = c.shape[:3]
+    d = _f32(_np(depths)).reshape(n, H, W)
+    p = _f32(_np(poses)).reshape(n, 12)
+    kd = _f32(_np(kf_depth)).reshape(H, W)
+    kp = _f32(_np(kf_pose)).reshape(12)
+    out = ColourFusion(np.zeros((H, W, 3)), np.zeros((H, W, 3)), np.zeros((H, W, 4), np.uint8),
+                       np.zeros((H, W), np.int32), np.zeros((H, W)), np.zeros((H, W), np.uint8), np.zeros(n))
+    fx, fy, cx, cy = _intr(intr)
+    lib().or_fuse_colour(_ptr(c), _ptr(d), _ptr(p), n, _ptr(kd), _ptr(kp), fx, fy, cx, cy, W, H,
+                         f32(disc_rel), f32(occl_rel), _ptr(out.median), _ptr(out.err), _ptr(out.rgba),
+                         _ptr(out.nobs), _ptr(out.wsum), _ptr(out.flag), _ptr(out.wb))
+    return out
 
 
 def allocation_set(depth, pose, intr, voxel_size, trunc):

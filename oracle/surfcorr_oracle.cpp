@@ -27,6 +27,15 @@
 //   or_pose_distance,        Keyframe selection (Section 4.3, Eq. 3, Fig. 4).
 //   or_select_topm,          Pinned: the Fig. 4 worked example.
 //   or_select_consecutive
+//   or_colour_unsharp,       Colour keyframe fusion (Section 3 "Keyframe Fusion", colour
+//   or_colour_blurriness,    paragraph): unsharp masking, blurriness weight, back-warp,
+//   or_weighted_median,      bilinear sampling, weighted median.  Pinned: the binomial's
+//   or_fuse_colour           variance on x^2 images, linear images unchanged, the clamp;
+//                            blurriness of ramp edges (width s: s/9 up to 5) and the luma
+//                            weights; the weighted median as the smallest L1 minimiser;
+//                            translated views of a ramp (sign and size of the warp, exact
+//                            bilinear samples), w_z = cos(theta)/z^2 on a tilted plane,
+//                            dropped occluded / out-of-view samples.
 //   or_loss, or_grad,        Loss on the fused SDF and its analytic gradient with
 //   or_loss_perturbed        respect to keyframe se(3) poses and depth pixels (this
 //                            extension has no counterpart in the paper).  Pinned: a
@@ -1037,4 +1046,276 @@ extern "C" double or_loss_perturbed(void* vol, int kf_id, const float* depth, co
     DOverlay ov;
     ov.over = &over;
     return loss_impl(V, ov, pts, n, lambda, nullptr, nullptr);
+}
+
+// ============================================================================
+// Colour keyframe fusion (Section 3 "Keyframe Fusion", colour paragraph)
+// ============================================================================
+//
+// Three steps, in the order the paper gives them:
+//  1. every input colour image C_i is deblurred by unsharp masking;
+//  2. a blurriness measure of C_i gives the per-frame weight w_b;
+//  3. each keyframe pixel x* is warped back into every frame i of its group with
+//     the keyframe depth Z*, the deblurred colour is sampled there bilinearly and
+//     weighted by w_c = w_b * w_z; C*(x*) is the weighted median of the samples.
+//
+// Readings (the paper names the operations, not their parameters):
+//  * unsharp masking: S = I + (I - G*I), G the 5x5 binomial filter (1 4 6 4 1)/16
+//    on each axis (variance 1 per axis), amount 1, image borders replicated, S
+//    clamped to [0, 255]; R, G, B separately.
+//  * blurriness: the no-reference blur measure of Crete-Roffet et al. (2007) on the
+//    luma Y = (77 R + 150 G + 29 B) / 256 of the input image.  Per direction e:
+//    B = 9-tap box mean of Y along e (borders replicated), D_F = |Y(p) - Y(p - e)|,
+//    D_B = |B(p) - B(p - e)|, V = max(0, D_F - D_B), summed over every pixel p whose
+//    p - e is inside the image; b_e = (sum D_F - sum V) / sum D_F, and b_e = 0 when
+//    sum D_F = 0 (no edge, no evidence of blur).  b = max(b_vertical, b_horizontal)
+//    lies in [0, 1]; w_b = 1 - b.
+//  * w_z = cos(theta) / z_i^2 as in Eq. 1: z_i the depth of the point in frame i,
+//    theta the angle between frame i's optical axis and the surface normal.  The
+//    normal is Eq. 1's central-difference normal of Z* at x* (same neighbour and
+//    discontinuity test), rotated into frame i.  A keyframe pixel with Z* <= 0 or
+//    without a valid normal gets no colour.
+//  * an observation is valid if z_i > 0, the sample point (u, v) lies in
+//    [0, W-1] x [0, H-1], and frame i's depth at the nearest pixel agrees with the
+//    point: Z_i > 0 and |Z_i - z_i| <= occl_rel * z_i (occlusion test).  Frames with
+//    w_b = 0 contribute nothing.
+//  * weighted median, per channel: the smallest sample value m with
+//    sum_{j : c_j <= m} w_j >= (sum_j w_j) / 2.  The colour is m rounded to the
+//    nearest integer, halves up, alpha 255; no observation gives (0, 0, 0, 0).
+//
+// Margins: flag marks keyframe pixels where a float32 evaluation may take another
+// discrete decision (normal test, z_i sign, footprint bounds, occlusion pixel or
+// threshold, which sample crosses half the weight).  err bounds, per channel, how
+// far an unflagged median can move when every sample point moves by tau_px pixels:
+// bilinear sampling is Lipschitz in the position with the cell's largest
+// differences, and the weighted median moves by at most the largest sample move.
+
+namespace {
+
+constexpr int kBinom[5] = {1, 4, 6, 4, 1};
+
+inline long clampl(long a, long lo, long hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+// Unsharp masking of one RGBA8 image into S[H][W][3] (double, exact: every value is
+// a multiple of 1/256).  The 5x5 filter is applied as one 2-D sum.
+void unsharp(const uint8_t* rgba, int W, int H, double* S) {
+#pragma omp parallel for schedule(static)
+    for (long y = 0; y < H; ++y)
+        for (long x = 0; x < W; ++x)
+            for (int c = 0; c < 3; ++c) {
+                double blur = 0.0;
+                for (int b = -2; b <= 2; ++b)
+                    for (int a = -2; a <= 2; ++a) {
+                        const long yy = clampl(y + b, 0, H - 1), xx = clampl(x + a, 0, W - 1);
+                        blur += (double)(kBinom[a + 2] * kBinom[b + 2]) * rgba[(yy * W + xx) * 4 + c];
+                    }
+                blur /= 256.0;
+                const double I = rgba[(y * W + x) * 4 + c];
+                double s = I + (I - blur);
+                S[(y * W + x) * 3 + c] = s < 0.0 ? 0.0 : (s > 255.0 ? 255.0 : s);
+            }
+}
+
+// Crete-Roffet blurriness of one RGBA8 image, in [0, 1].
+double blurriness(const uint8_t* rgba, int W, int H) {
+    std::vector<double> Y((size_t)W * H);
+    for (long p = 0; p < (long)W * H; ++p)
+        Y[p] = (77.0 * rgba[p * 4] + 150.0 * rgba[p * 4 + 1] + 29.0 * rgba[p * 4 + 2]) / 256.0;
+    double b_dir[2];
+    for (int dir = 0; dir < 2; ++dir) {  // 0: vertical (e = one row), 1: horizontal (e = one column)
+        const int ex = dir == 1, ey = dir == 0;
+        std::vector<double> B((size_t)W * H);
+        for (long y = 0; y < H; ++y)
+            for (long x = 0; x < W; ++x) {
+                double s = 0.0;
+                for (int k = -4; k <= 4; ++k) {
+                    const long yy = clampl(y + k * ey, 0, H - 1), xx = clampl(x + k * ex, 0, W - 1);
+                    s += Y[yy * W + xx];
+                }
+                B[y * W + x] = s / 9.0;
+            }
+        double sF = 0.0, sV = 0.0;
+        for (long y = ey; y < H; ++y)
+            for (long x = ex; x < W; ++x) {
+                const long p = y * W + x, q = (y - ey) * W + (x - ex);
+                const double dF = std::fabs(Y[p] - Y[q]);
+                const double dB = std::fabs(B[p] - B[q]);
+                sF += dF;
+                sV += std::max(0.0, dF - dB);
+            }
+        b_dir[dir] = sF > 0.0 ? (sF - sV) / sF : 0.0;
+    }
+    return std::max(b_dir[0], b_dir[1]);
+}
+
+// Lower weighted median of (c_j, w_j): sort by value, walk the cumulative weight.
+// near_tie reports whether some cumulative sum at a change of value lies within
+// tol * total of half the total.
+double weighted_median(std::vector<std::pair<double, double>> obs, double tol, bool* near_tie) {
+    std::sort(obs.begin(), obs.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+    double total = 0.0;
+    for (const auto& o : obs) total += o.second;
+    const double half = 0.5 * total;
+    double cum = 0.0, m = obs.back().first;
+    bool found = false;
+    *near_tie = false;
+    for (size_t k = 0; k < obs.size(); ++k) {
+        cum += obs[k].second;
+        const bool last_of_value = k + 1 == obs.size() || obs[k + 1].first != obs[k].first;
+        if (!last_of_value) continue;
+        if (k + 1 < obs.size() && std::fabs(cum - half) <= tol * total) *near_tie = true;
+        if (!found && cum >= half) {
+            m = obs[k].first;
+            found = true;
+        }
+    }
+    return m;
+}
+
+double g_tau_w = 1e-5;  // relative margin of the weighted-median threshold
+
+}  // namespace
+
+extern "C" void or_colour_unsharp(const uint8_t* rgba, int W, int H, double* S) { unsharp(rgba, W, H, S); }
+
+extern "C" double or_colour_blurriness(const uint8_t* rgba, int W, int H) { return blurriness(rgba, W, H); }
+
+extern "C" double or_weighted_median(const double* c, const double* w, int n) {
+    std::vector<std::pair<double, double>> obs;
+    for (int j = 0; j < n; ++j) obs.emplace_back(c[j], w[j]);
+    bool nt;
+    return n > 0 ? weighted_median(obs, 0.0, &nt) : NAN;
+}
+
+extern "C" int or_fuse_colour(const uint8_t* rgba, const float* depths, const float* poses, int n,
+                              const float* kf_depth, const float* kf_pose, double fx, double fy, double cx,
+                              double cy, int W, int H, double disc_rel, double occl_rel, double* med, double* err,
+                              uint8_t* out_rgba, int32_t* nobs, double* wsum, uint8_t* flag, double* wb_out) {
+    const Intr K{fx, fy, cx, cy, W, H};
+    const Pose Tk = pose_from(kf_pose);
+    // steps 1 and 2, per frame
+    std::vector<double> S((size_t)n * W * H * 3);
+    std::vector<double> wb(n);
+    for (int i = 0; i < n; ++i) {
+        const uint8_t* img = rgba + (size_t)i * W * H * 4;
+        unsharp(img, W, H, S.data() + (size_t)i * W * H * 3);
+        wb[i] = 1.0 - blurriness(img, W, H);
+        if (wb_out) wb_out[i] = wb[i];
+    }
+    std::vector<Pose> Tf(n);
+    for (int i = 0; i < n; ++i) Tf[i] = pose_from(poses + 12 * i);
+    // step 3, per keyframe pixel
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long v = 0; v < H; ++v)
+        for (long u = 0; u < W; ++u) {
+            const long p = v * W + u;
+            for (int c = 0; c < 3; ++c) med[p * 3 + c] = err[p * 3 + c] = 0.0;
+            for (int c = 0; c < 4; ++c) out_rgba[p * 4 + c] = 0;
+            nobs[p] = 0;
+            wsum[p] = 0.0;
+            flag[p] = 0;
+            const double z = kf_depth[p];
+            if (!(z > 0.0)) continue;
+            if (u == 0 || v == 0 || u == W - 1 || v == H - 1) continue;
+            const double zn[4] = {kf_depth[p - 1], kf_depth[p + 1], kf_depth[p - W], kf_depth[p + W]};
+            if (!(zn[0] > 0.0 && zn[1] > 0.0 && zn[2] > 0.0 && zn[3] > 0.0)) continue;
+            bool keep = true, marginal = false;
+            for (int k = 0; k < 4; ++k) {
+                const double gap = std::fabs(zn[k] - z) - disc_rel * z;
+                if (std::fabs(gap) < g_tau_rel * z) marginal = true;
+                if (gap > 0.0) keep = false;
+            }
+            if (marginal) flag[p] = 1;
+            if (!keep) continue;
+            // keyframe normal (camera coordinates of the keyframe), then world
+            double Pl[3], Pr[3], Pu[3], Pd[3], P[3];
+            backproject(K, u - 1, v, zn[0], Pl);
+            backproject(K, u + 1, v, zn[1], Pr);
+            backproject(K, u, v - 1, zn[2], Pu);
+            backproject(K, u, v + 1, zn[3], Pd);
+            backproject(K, u, v, z, P);
+            const double a[3] = {Pr[0] - Pl[0], Pr[1] - Pl[1], Pr[2] - Pl[2]};
+            const double b[3] = {Pd[0] - Pu[0], Pd[1] - Pu[1], Pd[2] - Pu[2]};
+            const double nk[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+            const double nn = std::sqrt(nk[0] * nk[0] + nk[1] * nk[1] + nk[2] * nk[2]);
+            if (!(nn > 0.0)) continue;
+            double nw[3];
+            for (int r = 0; r < 3; ++r) nw[r] = Tk.R[r][0] * nk[0] + Tk.R[r][1] * nk[1] + Tk.R[r][2] * nk[2];
+            double pw[3];
+            apply(Tk, P, pw);
+            std::vector<std::pair<double, double>> obs[3];
+            double e[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < n; ++i) {
+                if (!(wb[i] > 0.0)) continue;
+                // p_i = g(T_i^-1, g(T*, pi^-1(x*, Z*(x*))))
+                double pi[3];
+                apply_inv(Tf[i], pw, pi);
+                if (std::fabs(pi[2]) < g_tau_m) flag[p] = 1;
+                if (!(pi[2] > 0.0)) continue;
+                const double us = K.fx * pi[0] / pi[2] + K.cx, vs = K.fy * pi[1] / pi[2] + K.cy;
+                // footprint bounds (decision + margin)
+                const double mb = std::min(std::min(std::fabs(us), std::fabs(us - (W - 1))),
+                                           std::min(std::fabs(vs), std::fabs(vs - (H - 1))));
+                if (mb < g_tau_px) flag[p] = 1;
+                if (!(us >= 0.0 && us <= W - 1 && vs >= 0.0 && vs <= H - 1)) continue;
+                // occlusion test at the nearest pixel; a marginal rounding flags the pixel
+                // when the neighbour across the tie decides differently
+                const float* Zi = depths + (size_t)i * W * H;
+                auto visible = [&](long xx, long yy, bool* thr_marg) {
+                    if (xx < 0 || yy < 0 || xx >= W || yy >= H) return false;
+                    const double zi = Zi[yy * W + xx];
+                    if (!(zi > 0.0)) return false;
+                    const double gap = std::fabs(zi - pi[2]) - occl_rel * pi[2];
+                    if (std::fabs(gap) < g_tau_m + g_tau_rel * pi[2]) *thr_marg = true;
+                    return gap <= 0.0;
+                };
+                double mu_, mv_;
+                const long xr = round_half_up(us, &mu_), yr = round_half_up(vs, &mv_);
+                bool thr = false;
+                const bool vis = visible(xr, yr, &thr);
+                if (thr) flag[p] = 1;
+                if (mu_ < g_tau_px || mv_ < g_tau_px) {
+                    const long ax = mu_ < g_tau_px ? (us + 0.5 - std::floor(us + 0.5) < 0.5 ? xr - 1 : xr + 1) : xr;
+                    const long ay = mv_ < g_tau_px ? (vs + 0.5 - std::floor(vs + 0.5) < 0.5 ? yr - 1 : yr + 1) : yr;
+                    bool t2 = false;
+                    if (visible(ax, yr, &t2) != vis || visible(xr, ay, &t2) != vis || visible(ax, ay, &t2) != vis || t2)
+                        flag[p] = 1;
+                }
+                if (!vis) continue;
+                // w_c = w_b * w_z, w_z = cos(theta) / z_i^2 with the normal in frame i
+                double ni[3];
+                for (int r = 0; r < 3; ++r) ni[r] = Tf[i].R[0][r] * nw[0] + Tf[i].R[1][r] * nw[1] + Tf[i].R[2][r] * nw[2];
+                const double cos_theta = std::fabs(ni[2]) / nn;
+                const double wc = wb[i] * cos_theta / (pi[2] * pi[2]);
+                if (!(wc > 0.0)) continue;
+                // bilinear sample of the deblurred image
+                const double* Si = S.data() + (size_t)i * W * H * 3;
+                long x0 = (long)std::floor(us), y0 = (long)std::floor(vs);
+                if (x0 > W - 2) x0 = W - 2;
+                if (y0 > H - 2) y0 = H - 2;
+                const double ax_ = us - x0, ay_ = vs - y0;
+                for (int c = 0; c < 3; ++c) {
+                    const double s00 = Si[(y0 * W + x0) * 3 + c], s01 = Si[(y0 * W + x0 + 1) * 3 + c];
+                    const double s10 = Si[((y0 + 1) * W + x0) * 3 + c], s11 = Si[((y0 + 1) * W + x0 + 1) * 3 + c];
+                    const double val = (1.0 - ay_) * ((1.0 - ax_) * s00 + ax_ * s01) + ay_ * ((1.0 - ax_) * s10 + ax_ * s11);
+                    obs[c].emplace_back(val, wc);
+                    const double lip = std::max(std::fabs(s01 - s00), std::fabs(s11 - s10)) +
+                                       std::max(std::fabs(s10 - s00), std::fabs(s11 - s01));
+                    e[c] = std::max(e[c], g_tau_px * lip);
+                }
+                wsum[p] += wc;
+            }
+            nobs[p] = (int32_t)obs[0].size();
+            if (obs[0].empty()) continue;
+            for (int c = 0; c < 3; ++c) {
+                bool nt = false;
+                const double m = weighted_median(obs[c], g_tau_w, &nt);
+                if (nt) flag[p] = 1;
+                med[p * 3 + c] = m;
+                err[p * 3 + c] = e[c];
+                out_rgba[p * 4 + c] = (uint8_t)std::floor(m + 0.5);
+            }
+            out_rgba[p * 4 + 3] = 255;
+        }
+    return 0;
 }
