@@ -15,7 +15,10 @@ One step = one pass of the whole hot path over that input:
   surface points + adjoint for all 60 keyframes -> extract the block list.
 value = 60 re-integrations / step time.  The JSON line also reports the update
 alone, batched (one graph) vs plain (120 per-keyframe calls), the roofline of the
-dominant kernel, the oracle on the host cores, clocks and the kernel count.
+dominant kernel, the oracle on the host cores, clocks and the kernel count, and,
+under "rows", colour keyframe fusion of the 600 textured frames into the 60
+keyframes (its CUDA-event time, HBM roofline and the oracle beside it), measured
+outside the step.
 
 --gpus N > 1 (under torchrun) runs N independent replicas (the path does not
 shard across GPUs in this build); value sums the replicas' throughput.
@@ -68,6 +71,8 @@ def parse():
     ap.add_argument("--profile-region", action="store_true",
                     help="run --steps steps between cudaProfilerStart/Stop and exit (for ncu "
                          "--profile-from-start off); prints only the timing")
+    ap.add_argument("--profile-colour", action="store_true",
+                    help="run colour fusion steps between cudaProfilerStart/Stop (for ncu) and exit")
     ap.add_argument("--keyframes", type=int, default=60, help="keyframes of the workload (small ncu cases)")
     ap.add_argument("--max-blocks", type=int, default=1 << 21)
     return ap.parse_args()
@@ -185,7 +190,8 @@ def max_over_ranks(x, ws):
 def make_workload(device, keyframes=60):
     import torch
     from paper_1709_03763_b300 import synthetic
-    w = synthetic.workload_kinect(device=device, n_frames=N_FRAMES, kappa=KAPPA, render_frames=keyframes * KAPPA)
+    w = synthetic.workload_kinect(device=device, n_frames=N_FRAMES, kappa=KAPPA, render_frames=keyframes * KAPPA,
+                                  textured=True)
     w.kf_poses = w.kf_poses[:keyframes]
     w.new_poses = w.new_poses[:keyframes]
     w.kf_rgba = w.kf_rgba[:keyframes].contiguous()
@@ -223,6 +229,10 @@ class Pipeline:
         self.prep_int = vol.prepare_integrate_many(self.ids, self.kf_depth, self.kf_rgba, self.drift)
         self.prep_upd = vol.prepare_batch(self.ids, self.kf_depth, self.kf_rgba, self.drift, self.true)
         self.prep_adj = vol.prepare_adjoint(self.ids, self.kf_depth, self.true)
+        from paper_1709_03763_b300 import prepare_colour
+        self.prep_col = prepare_colour(self.frame_poses[:nf], [f // KAPPA for f in range(nf)],
+                                       self.frame_poses[:nf:KAPPA], w.intr.width, w.intr.height, dev)
+        self.kf_colour = torch.empty((K, w.intr.height, w.intr.width, 4), dtype=torch.uint8, device=dev)
         self.loss_out = torch.empty(5, dtype=torch.float64, device=dev)
         self.gx = torch.empty((K, 6), dtype=torch.float64, device=dev)
         self.gd = torch.empty((K, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
@@ -233,6 +243,13 @@ class Pipeline:
         nf = self.K * KAPPA
         fuse_keyframes(self.w.frames_depth[:nf], intr=self.intr, disc_rel=0.1, out_depth=self.kf_depth,
                        out_weight=self.kf_weight, prepared=self.prep_fuse)
+
+    def colour(self):
+        """Colour keyframe fusion of all 600 frames into the 60 keyframes (Section 3)."""
+        from paper_1709_03763_b300 import fuse_colour_keyframes
+        nf = self.K * KAPPA
+        fuse_colour_keyframes(self.w.frames_rgba[:nf], self.w.frames_depth[:nf], self.kf_depth, intr=self.intr,
+                              out_rgba=self.kf_colour, prepared=self.prep_col)
 
     def integrate(self):
         """Reset, then integrate every keyframe at its drifted pose (one graph launch)."""
@@ -305,6 +322,49 @@ def update_only_timing(P, steps, batched: bool):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     return statistics.median(ts)
+
+
+# algorithmic bytes of colour fusion: its inputs and outputs -- per frame, the RGBA read
+# and the depth read by the occlusion test; per keyframe, Z* read and C* written.  The
+# unsharp texels are an intermediate that the library keeps in L2 (32-frame chunks).
+def colour_bytes(n_frames, n_kf, H, W):
+    px = H * W
+    return n_frames * px * (4 + 4) + n_kf * px * (4 + 4)
+
+
+def colour_timing(P, reps, warmup):
+    """CUDA-event time of one colour fusion call over the whole workload (median)."""
+    import torch
+    for _ in range(warmup):
+        P.colour()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        P.colour()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def oracle_colour(w, kf_depth, n_kf=3):
+    """The oracle's colour fusion of the first n_kf keyframes (10 frames each) on the host
+    cores: (keyframes per second, threads)."""
+    import oracle
+    oracle.build()
+    it = w.intr.as_tuple()
+    rgba = w.frames_rgba[:n_kf * KAPPA].cpu().numpy()
+    depth = w.frames_depth[:n_kf * KAPPA].cpu().numpy()
+    kd = kf_depth[:n_kf].cpu().numpy()
+    t0 = time.perf_counter()
+    for k in range(n_kf):
+        sl = slice(k * KAPPA, (k + 1) * KAPPA)
+        oracle.fuse_colour(rgba[sl], depth[sl], w.frame_poses[sl], kd[k], w.frame_poses[k * KAPPA], it)
+    dt = time.perf_counter() - t0
+    return n_kf / dt, oracle.get_threads(), dt
 
 
 def oracle_reintegration(n_kf, steps=1, warmup=0, w=None):
@@ -396,6 +456,18 @@ def main():
     P.prep_upd = V.prepare_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true)
     setup_s = time.perf_counter() - t_setup
 
+    if args.profile_colour:
+        for _ in range(args.warmup):
+            P.colour()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            P.colour()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_colour_steps": args.steps, "keyframes": P.K}), flush=True)
+        return
+
     if args.profile_region:
         for _ in range(args.warmup):
             P.step()
@@ -478,6 +550,18 @@ def main():
 
     hbm_peak, peak_kind = peaks()
     sm_mhz = clocks.get("sm_mhz") or 2032.0
+
+    # ---- colour keyframe fusion, measured on its own (the step integrates the keyframes'
+    # own colour images, as the depth-only path defines it)
+    nf = P.K * KAPPA
+    col_ms = colour_timing(P, 10, 3)
+    col_b = colour_bytes(nf, P.K, w.intr.height, w.intr.width)
+    col_gbs = col_b / (col_ms / 1e3) / 1e9
+    colour_row = {"ms_per_call": col_ms, "frames": nf, "keyframes": P.K,
+                  "keyframes_per_s": ws * P.K / (col_ms / 1e3),
+                  "roofline": {"bound": "hbm", "achieved": col_gbs, "peak": hbm_peak, "unit": "GB/s",
+                               "frac": col_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                               "algorithmic_bytes": col_b}}
     issue_peak = SMS * SCHEDULERS * LANES * sm_mhz * 1e6 / 1e12  # Tinst/s (lane instructions)
     # per-step time of the big kernels: (ms per launch, launches per step, units per launch)
     cand = {
@@ -519,6 +603,10 @@ def main():
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample, w)
+        kps, threads, dt = oracle_colour(w, P.kf_depth)
+        colour_row["cpu_baseline"] = {"value": kps, "unit": "keyframes/s", "cores": threads, "kind": "oracle",
+                                      "sample": f"colour fusion of 3 keyframes (10 frames each, 640x480), FP64, "
+                                                f"{dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -543,6 +631,7 @@ def main():
             "profile": prof,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "rows": {"colour_fusion": colour_row},
             "clocks": clocks,
             "setup_s": setup_s,
         }

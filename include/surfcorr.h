@@ -93,6 +93,11 @@ typedef struct {
     float disc_rel; /* drop pixels whose 4-neighbour depth differs by more than disc_rel * Z */
 } sc_fusion_params;
 
+typedef struct {
+    float disc_rel; /* keyframe normal: Z* neighbours must lie within disc_rel * Z* (as in Eq. 1) */
+    float occl_rel; /* a sample is visible if the frame's depth at its nearest pixel is within occl_rel * z */
+} sc_colour_params;
+
 /* One keyframe of a pose-graph update: de-integrate at old_pose, re-integrate at new_pose. */
 typedef struct {
     const float* depth;   /* device [H][W] keyframe depth (same as at its integration) */
@@ -169,6 +174,49 @@ int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses
 int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n_frames,
                       const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* intr,
                       const sc_fusion_params* fusion, float* kf_depth, float* kf_weight, sc_stream stream);
+
+/* ------------------------------------------------- colour keyframe fusion ---- */
+
+/* Device workspace sc_fuse_colour_keyframes needs for width x height images:
+ * 64 frames of 8-byte unsharp texels plus the blurriness sums.  0 for sizes out of
+ * range (width or height < 2 or > 16384). */
+uint64_t sc_colour_workspace_bytes(int32_t width, int32_t height);
+
+/* Colour keyframe fusion (Section 3 "Keyframe Fusion", colour paragraph) for many
+ * keyframes in one call.  Frame f (colour rgba, depth depths, pose frame_poses[f])
+ * belongs to keyframe frame_kf[f] (depth Z* in kf_depth, pose kf_poses[...]).
+ *  1. each frame's colour is deblurred by unsharp masking, S = I + (I - G*I) with G
+ *     the 5x5 binomial (1 4 6 4 1)/16 per axis, borders replicated, clamped to
+ *     [0, 255] (computed exactly, in 1/256 units);
+ *  2. each frame gets w_b = 1 - b, b the Crete-Roffet blurriness of its luma
+ *     Y = (77 R + 150 G + 29 B) / 256: per direction, with a 9-tap box mean B,
+ *     b_e = (sum|dY| - sum max(0, |dY| - |dB|)) / sum|dY| (0 if sum|dY| = 0),
+ *     b = max of the two directions;
+ *  3. each keyframe pixel x* with Z*(x*) > 0 and a valid Eq. 1 normal (4-neighbours
+ *     valid and within disc_rel * Z*; border pixels have none) is warped into every
+ *     frame of its group, p_i = g(T_i^-1, g(T*, pi^-1(x*, Z*(x*)))).  A sample is
+ *     kept if z_i > 0, pi(p_i) lies in [0, W-1] x [0, H-1], and the frame's depth at
+ *     the nearest pixel (halves up) is > 0 and within occl_rel * z_i of z_i.  Its
+ *     value is the bilinear sample of S, its weight w_c = w_b cos(theta) / z_i^2
+ *     (theta between the normal, rotated into frame i, and its optical axis);
+ *  4. C*(x*) per channel is the lower weighted median: the smallest sample value m
+ *     with sum of the weights of samples <= m at least half the total weight;
+ *     output (round(m_R), round(m_G), round(m_B), 255), halves up, or (0, 0, 0, 0)
+ *     without samples.
+ * rgba device [n_frames][H][W][4]; depths device [n_frames][H][W]; frame_poses and
+ * frame_kf host [n_frames] (0 <= frame_kf[f] < n_kf, at most 64 frames per
+ * keyframe); kf_depth device [n_kf][H][W]; kf_poses host [n_kf]; workspace device,
+ * 256-byte aligned, at least sc_colour_workspace_bytes(W, H) bytes (SC_ERR_CAPACITY
+ * otherwise), owned by the caller and not shared with a call that may overlap on the
+ * GPU.  Outputs (device, overwritten): kf_rgba [n_kf][H][W][4]; kf_colour
+ * [n_kf][H][W][3] float medians before rounding, or NULL; frame_weight [n_frames]
+ * w_b, or NULL.  Device images 16-byte aligned.  Two launches per chunk of whole
+ * keyframe groups of at most 64 frames. */
+int sc_fuse_colour_keyframes(const uint8_t* rgba, const float* depths, const sc_pose* frame_poses,
+                             const int32_t* frame_kf, int32_t n_frames, const float* kf_depth,
+                             const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* intr,
+                             const sc_colour_params* params, void* workspace, uint64_t workspace_bytes,
+                             uint8_t* kf_rgba, float* kf_colour, float* frame_weight, sc_stream stream);
 
 /* ------------------------------------------------ integration (plain path) ---- */
 

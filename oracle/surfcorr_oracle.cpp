@@ -1085,8 +1085,9 @@ extern "C" double or_loss_perturbed(void* vol, int kf_id, const float* depth, co
 //
 // Margins: flag marks keyframe pixels where a float32 evaluation may take another
 // discrete decision (normal test, z_i sign, footprint bounds, occlusion pixel or
-// threshold, which sample crosses half the weight).  err bounds, per channel, how
-// far an unflagged median can move when every sample point moves by tau_px pixels:
+// threshold, which sample crosses half the weight given the weights' float32
+// error).  err bounds, per channel, how far an unflagged median can move when
+// every sample point moves by tau_px pixels:
 // bilinear sampling is Lipschitz in the position with the cell's largest
 // differences, and the weighted median moves by at most the largest sample move.
 
@@ -1150,7 +1151,7 @@ double blurriness(const uint8_t* rgba, int W, int H) {
 
 // Lower weighted median of (c_j, w_j): sort by value, walk the cumulative weight.
 // near_tie reports whether some cumulative sum at a change of value lies within
-// tol * total of half the total.
+// tol of half the total.
 double weighted_median(std::vector<std::pair<double, double>> obs, double tol, bool* near_tie) {
     std::sort(obs.begin(), obs.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
     double total = 0.0;
@@ -1163,7 +1164,7 @@ double weighted_median(std::vector<std::pair<double, double>> obs, double tol, b
         cum += obs[k].second;
         const bool last_of_value = k + 1 == obs.size() || obs[k + 1].first != obs[k].first;
         if (!last_of_value) continue;
-        if (k + 1 < obs.size() && std::fabs(cum - half) <= tol * total) *near_tie = true;
+        if (k + 1 < obs.size() && std::fabs(cum - half) <= tol) *near_tie = true;
         if (!found && cum >= half) {
             m = obs[k].first;
             found = true;
@@ -1172,7 +1173,11 @@ double weighted_median(std::vector<std::pair<double, double>> obs, double tol, b
     return m;
 }
 
-double g_tau_w = 1e-5;  // relative margin of the weighted-median threshold
+// Weight margins of the weighted median: a float32 evaluation of w_c = w_b cos(theta) / z^2
+// carries a relative error (g_tau_w) and, through the normal, an absolute error in
+// cos(theta) (g_tau_cos) that dominates at grazing angles.
+double g_tau_w = 1e-5;
+double g_tau_cos = 1e-5;
 
 }  // namespace
 
@@ -1245,6 +1250,7 @@ extern "C" int or_fuse_colour(const uint8_t* rgba, const float* depths, const fl
             apply(Tk, P, pw);
             std::vector<std::pair<double, double>> obs[3];
             double e[3] = {0.0, 0.0, 0.0};
+            double w_err = 0.0;  // bound on the summed weight error of all samples
             for (int i = 0; i < n; ++i) {
                 if (!(wb[i] > 0.0)) continue;
                 // p_i = g(T_i^-1, g(T*, pi^-1(x*, Z*(x*))))
@@ -1304,12 +1310,13 @@ extern "C" int or_fuse_colour(const uint8_t* rgba, const float* depths, const fl
                     e[c] = std::max(e[c], g_tau_px * lip);
                 }
                 wsum[p] += wc;
+                w_err += g_tau_w * wc + wb[i] * g_tau_cos / (pi[2] * pi[2]);
             }
             nobs[p] = (int32_t)obs[0].size();
             if (obs[0].empty()) continue;
             for (int c = 0; c < 3; ++c) {
                 bool nt = false;
-                const double m = weighted_median(obs[c], g_tau_w, &nt);
+                const double m = weighted_median(obs[c], w_err, &nt);
                 if (nt) flag[p] = 1;
                 med[p * 3 + c] = m;
                 err[p * 3 + c] = e[c];

@@ -8,5 +8,5 @@ for a loss on the fused SDF.  All compute is in libsurfcorr.so (C ABI in
 include/surfcorr.h); this package marshals torch tensors into it.
 """
 from ._lib import SurfcorrError, lib  # noqa: F401
-from .volume import (Volume, fuse_frames_into_keyframe, fuse_keyframes, make_intrinsics, prepare_fuse, make_pose, pose_distance,  # noqa: F401
+from .volume import (Volume, fuse_colour_keyframes, fuse_frames_into_keyframe, fuse_keyframes, prepare_colour, make_intrinsics, prepare_fuse, make_pose, pose_distance,  # noqa: F401
                      pose_exp_left, select_consecutive, select_topm)

@@ -51,6 +51,10 @@ class FusionParams(ctypes.Structure):
     _fields_ = [("disc_rel", c_f)]
 
 
+class ColourParams(ctypes.Structure):
+    _fields_ = [("disc_rel", c_f), ("occl_rel", c_f)]
+
+
 class ReintItem(ctypes.Structure):
     _fields_ = [("depth", c_p), ("rgba", c_p), ("old_pose", Pose), ("new_pose", Pose), ("kf_id", c_i32)]
 
@@ -85,6 +89,9 @@ SIGNATURES = {
                                              c_p, c_p, c_p]),
     "sc_fuse_keyframes": (c_i32, [c_p, P(Pose), P(c_i32), c_i32, P(Pose), c_i32, P(Intrinsics), P(FusionParams),
                                   c_p, c_p, c_p]),
+    "sc_colour_workspace_bytes": (c_u64, [c_i32, c_i32]),
+    "sc_fuse_colour_keyframes": (c_i32, [c_p, c_p, P(Pose), P(c_i32), c_i32, c_p, P(Pose), c_i32, P(Intrinsics),
+                                         P(ColourParams), c_p, c_u64, c_p, c_p, c_p, c_p]),
     "sc_integrate_keyframe": (c_i32, [c_p, c_i32, c_p, c_p, P(Intrinsics), P(Pose), c_p]),
     "sc_deintegrate_keyframe": (c_i32, [c_p, c_i32, c_p, c_p, P(Intrinsics), P(Pose), c_p]),
     "sc_reintegrate_batch": (c_i32, [c_p, P(ReintItem), c_i32, P(Intrinsics), c_p]),

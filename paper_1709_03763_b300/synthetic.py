@@ -33,7 +33,7 @@ import numpy as np
 import torch
 
 SEED_BASE = 1709_03763
-STREAM_SCENE, STREAM_TRAJ, STREAM_NOISE, STREAM_MASK, STREAM_PERTURB, STREAM_POINTS = range(6)
+STREAM_SCENE, STREAM_TRAJ, STREAM_NOISE, STREAM_MASK, STREAM_PERTURB, STREAM_POINTS, STREAM_BLUR = range(7)
 
 # Depth sensor model (Kinect-class): valid range and axial noise sigma(z).
 Z_MIN, Z_MAX = 0.4, 4.0
@@ -150,11 +150,13 @@ def _slab(o, d_inv, lo, hi):
 
 
 def render(scene: Scene, intr: Intrinsics, poses, *, device="cpu", dtype=torch.float64,
-           chunk_prims: int = 64):
+           chunk_prims: int = 64, texture: bool = False):
     """Ray-cast z-depth and colour for each pose.
 
     poses: [n,3,4] world_from_camera.  Returns (depth [n,H,W] float32 torch on
     `device`, rgba [n,H,W,4] uint8 torch on `device`), noise-free, 0 where no hit.
+    texture=True modulates each surface colour by a smooth procedural pattern of the
+    world position (the same surface point has the same colour in every view).
     """
     poses = np.asarray(poses, np.float64).reshape(-1, 3, 4)
     H, W = intr.height, intr.width
@@ -251,9 +253,46 @@ def render(scene: Scene, intr: Intrinsics, poses, *, device="cpu", dtype=torch.f
 
         z = torch.where(torch.isfinite(best), best, torch.zeros_like(best))
         depth_out[k] = z.reshape(H, W).to(torch.float32)
+        if texture:
+            p = o + z[:, None] * d
+            g = texture_gain(p[:, 0], p[:, 1], p[:, 2])
+            col = torch.clamp(torch.round(col.to(dtype) * g[:, None]), 0, 255).to(torch.int32)
         rgba_out[k, ..., :3] = col.reshape(H, W, 3).to(torch.uint8)
         rgba_out[k, ..., 3] = 255
     return depth_out, rgba_out
+
+
+def texture_gain(x, y, z):
+    """Procedural surface texture in [0.23, 1.15]: two smooth waves (periods of
+    0.5-2 m) and a fine one (about 0.15 m)."""
+    return 1.15 * (0.6 + 0.25 * torch.sin(9.1 * x + 4.3 * y) * torch.cos(7.7 * z - 2.9 * x)
+                   + 0.15 * torch.sin(31.0 * x + 27.0 * y + 23.0 * z))
+
+
+def motion_blur(rgba: torch.Tensor, length: int) -> torch.Tensor:
+    """Horizontal box blur of odd `length` pixels (borders replicated), rounded to
+    uint8: the colour of a frame taken during a sideways camera motion."""
+    if length <= 1:
+        return rgba.clone()
+    r = length // 2
+    x = rgba[..., :3].to(torch.float64)
+    pad = torch.cat([x[..., :1, :].expand(*x.shape[:-2], r, 3), x, x[..., -1:, :].expand(*x.shape[:-2], r, 3)], -2)
+    c = torch.cumsum(torch.nn.functional.pad(pad, (0, 0, 1, 0)), dim=-2)
+    box = (c[..., length:, :] - c[..., :-length, :]) / length
+    out = rgba.clone()
+    out[..., :3] = torch.clamp(torch.round(box), 0, 255).to(torch.uint8)
+    return out
+
+
+def colour_frames(scene: Scene, intr: Intrinsics, poses, config: int, *, device="cpu") -> torch.Tensor:
+    """Textured colour frames [n,H,W,4] u8; about 40 % of them motion-blurred by 3-9
+    pixels (seeded per config), as in hand-held RGB-D sequences."""
+    _, rgba = render(scene, intr, poses, device=device, texture=True)
+    g = rng(config, STREAM_BLUR)
+    for k in range(rgba.shape[0]):
+        if g.random() < 0.4:
+            rgba[k] = motion_blur(rgba[k], int(g.choice([3, 5, 7, 9])))
+    return rgba
 
 
 def add_sensor_noise(depth: torch.Tensor, config: int, *, first_frame: int = 0) -> torch.Tensor:
@@ -493,16 +532,23 @@ def drift_poses(poses, angle, shift, g) -> np.ndarray:
     return np.stack(out)
 
 
-def workload_kinect(device="cpu", n_frames=600, kappa=10, render_frames=None) -> Workload:
+def workload_kinect(device="cpu", n_frames=600, kappa=10, render_frames=None, textured=False) -> Workload:
     """Plain method at Kinect scale: 600 raw 640x480 frames fused 10 per keyframe into 60
     keyframes (keyframe pose = first frame of its group), integrated at drifted poses
     (0.2 deg / 0.5 cm random walk per keyframe); one pose update moves all 60 to their
     true poses.  Voxel 1 cm, truncation 4 cm, 2^20 buckets.  render_frames renders only
-    that many leading frames (the poses of all frames and keyframes are still made)."""
+    that many leading frames (the poses of all frames and keyframes are still made).
+    textured=True gives the frames the colour of colour_frames (texture, seeded motion
+    blur)."""
     scene, _ = scene_kinect()
     frame_poses = kinect_trajectory(n_frames)
     nr = n_frames if render_frames is None else render_frames
-    fd, fr = render(scene, KINECT, frame_poses[:nr], device=device)
+    fd, fr = render(scene, KINECT, frame_poses[:nr], device=device, texture=textured)
+    if textured:
+        g = rng(2, STREAM_BLUR)
+        for k in range(fr.shape[0]):
+            if g.random() < 0.4:
+                fr[k] = motion_blur(fr[k], int(g.choice([3, 5, 7, 9])))
     fd = add_sensor_noise(fd, 2)
     kf_true = frame_poses[::kappa]
     g = rng(2, STREAM_PERTURB)

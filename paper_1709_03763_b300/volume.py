@@ -13,10 +13,11 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (BatchConfig, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
+from ._lib import (BatchConfig, ColourParams, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
                    VolumeParams, check, lib)
 
-__all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "pose_distance", "select_topm", "select_consecutive",
+__all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
+           "prepare_colour", "pose_distance", "select_topm", "select_consecutive",
            "pose_exp_left", "SurfcorrError", "make_intrinsics", "make_pose"]
 
 
@@ -328,6 +329,55 @@ def fuse_keyframes(depths: torch.Tensor, frame_poses=None, frame_kf=None, kf_pos
                                   _dev(out_weight, torch.float32, "out_weight"), _stream(stream)),
           "sc_fuse_keyframes")
     return out_depth, out_weight
+
+
+def prepare_colour(frame_poses, frame_kf, kf_poses, width: int, height: int, device=None):
+    """Argument arrays and the device workspace for fuse_colour_keyframes, built once
+    and reusable (the workspace must not be shared by calls that overlap on the GPU)."""
+    n, n_kf = len(frame_poses), len(kf_poses)
+    pz = (Pose * n)(*[make_pose(p) for p in frame_poses])
+    kz = (Pose * n_kf)(*[make_pose(p) for p in kf_poses])
+    fk = (ctypes.c_int32 * n)(*[int(k) for k in frame_kf])
+    nbytes = int(lib().sc_colour_workspace_bytes(int(width), int(height)))
+    if nbytes == 0:
+        raise ValueError("image size out of range for colour fusion")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device if device is not None else torch.cuda.current_device())
+    return (pz, fk, kz, ws)
+
+
+def fuse_colour_keyframes(rgba: torch.Tensor, depths: torch.Tensor, kf_depth: torch.Tensor, frame_poses=None,
+                          frame_kf=None, kf_poses=None, intr=None, disc_rel: float = 0.1, occl_rel: float = 0.05,
+                          out_rgba: torch.Tensor | None = None, out_colour: torch.Tensor | bool | None = None,
+                          out_weight: torch.Tensor | bool | None = None, stream=None, prepared=None):
+    """Colour keyframe fusion (unsharp masking, blurriness weight, back-warp with bilinear
+    sampling, weighted median) of frames rgba [n,H,W,4] u8 / depths [n,H,W] into the
+    keyframes with depth kf_depth [n_kf,H,W].  Returns (C* [n_kf,H,W,4] u8, medians
+    [n_kf,H,W,3] f32 or None, w_b [n] f32 or None); out_colour / out_weight = True
+    allocate those outputs."""
+    n, H, W = depths.shape
+    if prepared is None:
+        prepared = prepare_colour(frame_poses, frame_kf, kf_poses, W, H, depths.device)
+    pz, fk, kz, ws = prepared
+    n_kf = len(kz)
+    if len(pz) != n or rgba.shape != (n, H, W, 4) or kf_depth.shape != (n_kf, H, W):
+        raise ValueError("frame / keyframe shapes do not match")
+    if out_rgba is None:
+        out_rgba = torch.empty((n_kf, H, W, 4), dtype=torch.uint8, device=depths.device)
+    if out_colour is True:
+        out_colour = torch.empty((n_kf, H, W, 3), dtype=torch.float32, device=depths.device)
+    if out_weight is True:
+        out_weight = torch.empty(n, dtype=torch.float32, device=depths.device)
+    cp = ColourParams(float(disc_rel), float(occl_rel))
+    col_ptr = _dev(out_colour, torch.float32, "out_colour") if isinstance(out_colour, torch.Tensor) else None
+    w_ptr = _dev(out_weight, torch.float32, "out_weight") if isinstance(out_weight, torch.Tensor) else None
+    check(lib().sc_fuse_colour_keyframes(_dev(rgba, torch.uint8, "rgba"), _dev(depths, torch.float32, "depths"),
+                                         pz, fk, n, _dev(kf_depth, torch.float32, "kf_depth"), kz, n_kf,
+                                         ctypes.byref(make_intrinsics(intr)), ctypes.byref(cp),
+                                         _dev(ws, torch.uint8, "workspace"), ws.numel(),
+                                         _dev(out_rgba, torch.uint8, "out_rgba"), col_ptr, w_ptr, _stream(stream)),
+          "sc_fuse_colour_keyframes")
+    return (out_rgba, out_colour if isinstance(out_colour, torch.Tensor) else None,
+            out_weight if isinstance(out_weight, torch.Tensor) else None)
 
 
 def fusion_profile(enable: int = -1) -> dict:

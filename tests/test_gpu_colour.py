@@ -1,0 +1,139 @@
+"""GPU colour keyframe fusion (Section 3 "Keyframe Fusion", colour paragraph) against the
+oracle: Kinect-scale groups of 10 textured, partly motion-blurred frames, ragged image
+sizes, empty and large keyframe groups (every kernel instantiation), chunking, and
+argument errors."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1709_03763_b300 import SurfcorrError, fuse_colour_keyframes, synthetic
+
+pytestmark = pytest.mark.gpu
+
+SLACK = 2e-3  # float32 bilinear arithmetic on values <= 255 (few ulp of 65280 / 256)
+
+
+def _compare(out_rgba, out_col, O, max_flag=0.02):
+    """GPU keyframe colour vs the oracle's ColourFusion on the same inputs."""
+    r = out_rgba.cpu().numpy()
+    m = out_col.cpu().numpy().astype(np.float64)
+    unfl = O.flag == 0
+    assert 1.0 - unfl.mean() <= max_flag
+    obs_o = O.nobs > 0
+    assert np.array_equal((r[..., 3] == 255)[unfl], obs_o[unfl])
+    both = unfl & obs_o
+    assert np.all(r[~obs_o & unfl] == 0)
+    if not both.any():
+        return 0
+    d = np.abs(m - O.median)[both]
+    bound = O.err[both] + SLACK
+    if not np.all(d <= bound):
+        i = int(np.argmax((d - bound).max(-1)))
+        yx = np.argwhere(both)[i]
+        raise AssertionError(f"median off by {float((d - bound).max())} beyond its bound at {tuple(yx)}: "
+                             f"gpu {m[tuple(yx)]} oracle {O.median[tuple(yx)]} err {O.err[tuple(yx)]} "
+                             f"nobs {O.nobs[tuple(yx)]} wsum {O.wsum[tuple(yx)]}")
+    frac = O.median - np.floor(O.median)
+    near = np.abs(frac - 0.5) <= O.err + SLACK
+    exact = both[..., None] & ~near
+    assert np.array_equal(r[..., :3][exact], O.rgba[..., :3][exact])
+    assert np.abs(r[..., :3].astype(int) - O.rgba[..., :3].astype(int))[both].max() <= 1
+    return int(both.sum())
+
+
+def test_colour_fusion_matches_oracle_kinect():
+    kappa, nk = 10, 2
+    w = synthetic.workload_kinect(device="cuda", n_frames=600, kappa=kappa, render_frames=nk * kappa)
+    it = w.intr.as_tuple()
+    n = nk * kappa
+    fd = w.frames_depth[:n].contiguous()
+    poses = w.frame_poses[:n]
+    rgba = synthetic.colour_frames(w.scene, w.intr, poses, 2, device="cuda")
+    kf_poses = poses[::kappa]
+    Zs = [oracle.fuse(fd[k * kappa:(k + 1) * kappa].cpu(), poses[k * kappa:(k + 1) * kappa], kf_poses[k], it)[0]
+          for k in range(nk)]
+    kf_depth = torch.from_numpy(np.stack(Zs).astype(np.float32)).cuda()
+    frame_kf = np.repeat(np.arange(nk), kappa)
+    out, col, wb = fuse_colour_keyframes(rgba, fd, kf_depth, poses, frame_kf, kf_poses, w.intr,
+                                         out_colour=True, out_weight=True)
+    torch.cuda.synchronize()
+    for k in range(nk):
+        sl = slice(k * kappa, (k + 1) * kappa)
+        O = oracle.fuse_colour(rgba[sl].cpu(), fd[sl].cpu(), poses[sl], kf_depth[k].cpu(), kf_poses[k], it)
+        assert np.abs(wb[sl].cpu().numpy() - O.wb).max() <= 1e-6
+        assert 0.0 < O.wb.min() and O.wb.max() < 1.0
+        n_cmp = _compare(out[k], col[k], O)
+        assert n_cmp > 0.5 * O.nobs.size
+        # several frames observe most pixels
+        assert np.median(O.nobs[O.nobs > 0]) >= kappa // 2
+
+
+def _small_case(counts, H=23, W=37, seed=11):
+    """Keyframes of the tiny room with counts[k] frames each near keyframe pose k,
+    rendered at a ragged W x H; Z* from the oracle's Eq. 1."""
+    scene = synthetic.scene_tiny()
+    intr = synthetic.Intrinsics(0.1 * 262.5, 0.1 * 262.5, 18.2, 11.1, W, H)
+    base = synthetic.workload_tiny().kf_poses
+    g = np.random.default_rng(seed)
+    frame_poses, frame_kf = [], []
+    for k, c in enumerate(counts):
+        for j in range(c):
+            frame_poses.append(base[k] if j == 0 else
+                               synthetic.perturb_pose(base[k], math.radians(1.5), 0.02, g).astype(np.float32))
+            frame_kf.append(k)
+    frame_poses = np.stack(frame_poses).astype(np.float32)
+    kf_poses = base[:len(counts)]
+    d, _ = synthetic.render(scene, intr, frame_poses)
+    d = synthetic.add_sensor_noise(d, 1)
+    rgba = synthetic.colour_frames(scene, intr, frame_poses, 1)
+    it = intr.as_tuple()
+    Z = []
+    for k, c in enumerate(counts):
+        sel = [f for f in range(len(frame_kf)) if frame_kf[f] == k]
+        if sel:
+            Z.append(oracle.fuse(d[sel], frame_poses[sel], kf_poses[k], it)[0])
+        else:
+            Z.append(synthetic.render(scene, intr, kf_poses[k:k + 1])[0][0].numpy().astype(np.float64))
+    kf_depth = np.stack(Z).astype(np.float32)
+    return intr, d, rgba, frame_poses, np.array(frame_kf), kf_poses, kf_depth
+
+
+@pytest.mark.parametrize("counts", [[3, 2, 4], [3, 2, 8], [11, 2], [14, 1], [20, 3], [5, 0, 1, 17, 40, 12, 30]])
+def test_colour_fusion_ragged_groups_and_chunks(counts):
+    # the kernel is instantiated for 4, 8, 10, 12, 16, 24, 32 and 64 samples; each case
+    # reaches one of them (10: the Kinect test).  [5, 0, 1, 17, 40, 12, 30]: an empty
+    # keyframe and four chunks (23, 40, 12 and 30 frames: the 24-, 64-, 12- and 32-sample
+    # kernels; a group larger than the 32-frame chunk budget gets a chunk of its own)
+    intr, d, rgba, fp, fk, kp, kd = _small_case(counts)
+    it = intr.as_tuple()
+    out, col, wb = fuse_colour_keyframes(rgba.cuda(), d.cuda(), torch.from_numpy(kd).cuda(), fp, fk, kp, intr,
+                                         out_colour=True, out_weight=True)
+    torch.cuda.synchronize()
+    compared = 0
+    for k, c in enumerate(counts):
+        sel = np.nonzero(fk == k)[0]
+        if len(sel) == 0:
+            assert torch.all(out[k] == 0) and torch.all(col[k] == 0)
+            continue
+        O = oracle.fuse_colour(rgba[sel], d[sel], fp[sel], kd[k], kp[k], it)
+        assert np.abs(wb.cpu().numpy()[sel] - O.wb).max() <= 1e-6
+        compared += _compare(out[k], col[k], O, max_flag=0.1)
+    assert compared > 0
+
+
+def test_colour_fusion_argument_errors():
+    intr, d, rgba, fp, fk, kp, kd = _small_case([2, 2])
+    dg, cg, kg = d.cuda(), rgba.cuda(), torch.from_numpy(kd).cuda()
+    with pytest.raises(SurfcorrError):   # frame assigned to a keyframe that does not exist
+        fuse_colour_keyframes(cg, dg, kg, fp, [0, 0, 1, 2], kp, intr)
+    from paper_1709_03763_b300 import prepare_colour
+    pz, fkk, kz, ws = prepare_colour(fp, fk, kp, intr.width, intr.height)
+    with pytest.raises(SurfcorrError):   # workspace too small
+        fuse_colour_keyframes(cg, dg, kg, intr=intr, prepared=(pz, fkk, kz, ws[:ws.numel() // 2]))
+    many = np.stack([fp[0]] * 65)
+    with pytest.raises(SurfcorrError):   # more than 64 frames for one keyframe
+        fuse_colour_keyframes(cg[:1].expand(65, -1, -1, -1).contiguous(), dg[:1].expand(65, -1, -1).contiguous(),
+                              kg[:1].contiguous(), many, [0] * 65, kp[:1], intr)
