@@ -136,26 +136,24 @@ __global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const
 // The part of a keyframe camera the net-delta kernel samples with, kept in shared
 // memory (96 bytes; old cameras of items 0..n-1, then their new cameras).
 struct __align__(16) NdCam {
-    float M[9];
+    float Pr[9];
     float tf[3];
     int ti[3];
-    float fx, fy, cx, cy, mu;
+    float cxh, cyh, mu;
     int W, H;
     const uint2* tex;
 };
 
 __device__ __forceinline__ void load_ndcam(NdCam& o, const KfCam& k) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) o.M[i] = k.M[i];
+    for (int i = 0; i < 9; ++i) o.Pr[i] = k.Pr[i];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         o.tf[i] = k.tf[i];
         o.ti[i] = k.ti[i];
     }
-    o.fx = k.fx;
-    o.fy = k.fy;
-    o.cx = k.cx;
-    o.cy = k.cy;
+    o.cxh = k.cxh;
+    o.cyh = k.cyh;
     o.mu = k.mu;
     o.W = k.W;
     o.H = k.H;
@@ -188,38 +186,60 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
     }
 }
 
-// Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over every item whose
-// bit is set in the slot's mask (old bits subtract, new bits add), in item order.
-__device__ __forceinline__ void net_delta_group(const NdCam* cams, int n, const int4 c, int lx0, int ly, int lz,
-                                                uint32_t mw0, uint32_t mw1, int mw, float aD[4], float aW[4],
-                                                float aC[4][3], bool& touched) {
-    const int half = mw / 2;
-    for (int w = 0; w < mw; ++w) {
-        uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        const float sgn = w < half ? -1.f : 1.f;
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            const int item = ((w < half ? w : w - half) << 5) + b;
-            const NdCam& k = cams[w < half ? item : n + item];
-            Proj4 P;
-            project4(k, 8 * c.x + lx0, 8 * c.y + ly, 8 * c.z + lz, P);
-            uint2 t[4];
+// Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over the items whose
+// bits are set in mask word `word` (items ibase .. ibase + 31 of the camera table
+// `cams`), with sign SIGN (-1: old bits, de-integration; +1: new bits).  Weights and
+// colours are integer sums (exactly the float sums of the same integers); distances
+// are summed in float in item order.
+template <int SIGN>
+__device__ __forceinline__ void net_delta_word(const NdCam* cams, uint32_t word, const int4 c, int lx0, int ly,
+                                               int lz, float aD[4], int aW[4], int aC[4][3], bool& touched) {
+    while (word) {
+        const int b = __ffs(word) - 1;
+        word &= word - 1;
+        const NdCam& k = cams[b];
+        Proj4 P;
+        project4(k, 8 * c.x + lx0, 8 * c.y + ly, 8 * c.z + lz, P);
+        uint2 t[4];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
+        for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                float d, eta;
-                if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
-                    touched = true;
-                    aD[j] = __fmaf_rn(sgn, d, aD[j]);
-                    aW[j] = __fadd_rn(aW[j], sgn);
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch)
-                        aC[j][ch] = __fmaf_rn(sgn, (float)((t[j].y >> (8 * ch)) & 255u), aC[j][ch]);
+        for (int j = 0; j < 4; ++j) {
+            float d, eta;
+            if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
+                touched = true;
+                const uint32_t cw = t[j].y;
+                if (SIGN > 0) {
+                    aD[j] = __fadd_rn(aD[j], d);
+                    aW[j] += 1;
+                    aC[j][0] += (int)(cw & 255u);
+                    aC[j][1] += (int)((cw >> 8) & 255u);
+                    aC[j][2] += (int)((cw >> 16) & 255u);
+                } else {
+                    aD[j] = __fsub_rn(aD[j], d);
+                    aW[j] -= 1;
+                    aC[j][0] -= (int)(cw & 255u);
+                    aC[j][1] -= (int)((cw >> 8) & 255u);
+                    aC[j][2] -= (int)((cw >> 16) & 255u);
                 }
             }
         }
+    }
+}
+
+// All items of the slot's mask: old bits (first half of the words) subtract, new
+// bits add, in item order.
+__device__ __forceinline__ void net_delta_group(const NdCam* cams, int n, const int4 c, int lx0, int ly, int lz,
+                                                uint32_t mw0, uint32_t mw1, int mw, float aD[4], int aW[4],
+                                                int aC[4][3], bool& touched) {
+    const int half = mw / 2;
+    for (int w = 0; w < half; ++w) {
+        const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
+        net_delta_word<-1>(cams + (w << 5), word, c, lx0, ly, lz, aD, aW, aC, touched);
+    }
+    for (int w = half; w < mw; ++w) {
+        const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
+        net_delta_word<1>(cams + n + ((w - half) << 5), word, c, lx0, ly, lz, aD, aW, aC, touched);
     }
 }
 
@@ -264,11 +284,19 @@ __global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVol
             const uint32_t mw1 = lane + 32 < mw ? mp[lane + 32] : 0u;
             int lx0, ly, lz;
             lane_voxels(lane, g, lx0, ly, lz);
-            float aD[4] = {0.f, 0.f, 0.f, 0.f}, aW[4] = {0.f, 0.f, 0.f, 0.f};
-            float aC[4][3] = {};
+            float aD[4] = {0.f, 0.f, 0.f, 0.f};
+            int iW[4] = {0, 0, 0, 0};
+            int iC[4][3] = {};
             bool touched = false;
-            net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, aD, aW, aC, touched);
+            net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, aD, iW, iC, touched);
             if (!touched && !fresh) continue;
+            float aW[4], aC[4][3];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                aW[j] = (float)iW[j];
+#pragma unroll
+                for (int ch = 0; ch < 3; ++ch) aC[j][ch] = (float)iC[j][ch];
+            }
             const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
             float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
             if (!fresh) {

@@ -89,13 +89,15 @@ __device__ inline void set_status(int32_t* status, int32_t code) { atomicCAS(sta
 // pose in double precision and rounded once:
 //   q = (i - ti) - tf   voxel index relative to the camera position (voxel units)
 //   p_c = M q           camera coordinates (metres), M = voxel_size * R^T
+//   Pr = diag(fx, fy, 1) M   the projection rows: pi(p_c) = (Pr_0 q, Pr_1 q) / (Pr_2 q) + (cx, cy)
 //   segment endpoint in relative voxel units: Ms * pi^-1(x, z) + tf, Ms = R / voxel_size
 struct KfCam {
-    float M[9];
+    float Pr[9];
     float Ms[9];
     float tf[3];
     int ti[3];
     float fx, fy, cx, cy;
+    float cxh, cyh;  // cx + 1/2, cy + 1/2: nearest pixel = floor(u + 1/2)
     float ifx, ify;  // 1 / fx, 1 / fy
     int W, H;
     float mu;
@@ -104,13 +106,21 @@ struct KfCam {
     const uint2* tex;      // (depth bits, RGBA8) per pixel, where a packed copy exists
 };
 
+// 1/x to about 1 ulp (the MUFU reciprocal); denormal x flushes to zero (1/x = inf).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Projection of the 4 voxels (ix0 + j, iy, iz), j = 0..3, that one thread owns.
-// Every operation is an explicit round-to-nearest intrinsic, in one fixed order, so
-// that integration, de-integration, the batched net-delta kernel and the adjoint
-// reach bit-identical decisions and distances for the same keyframe and pose.
-// ok[j]: in front of the camera and the nearest pixel (halves rounded up) inside
-// the image; pix[j] is only meaningful when ok[j].  Computing all four first lets
-// the caller issue the four depth gathers back to back.
+// Every operation is an explicit round-to-nearest intrinsic (or the one approximate
+// reciprocal), in one fixed order, so that integration, de-integration, the batched
+// net-delta kernel and the adjoint reach bit-identical decisions and distances for
+// the same keyframe and pose.  Voxel j + 1 adds the x column of Pr to voxel j's
+// projective coordinates.  ok[j]: in front of the camera and the nearest pixel
+// (halves rounded up) inside the image; pix[j] is only meaningful when ok[j].
+// Computing all four first lets the caller issue the four depth gathers back to back.
 struct Proj4 {
     float pz[4];
     int pix[4];
@@ -119,18 +129,23 @@ struct Proj4 {
 
 template <typename Cam>
 __device__ __forceinline__ void project4(const Cam& k, int ix0, int iy, int iz, Proj4& p) {
+    const float qx = __fsub_rn((float)(ix0 - k.ti[0]), k.tf[0]);
     const float qy = __fsub_rn((float)(iy - k.ti[1]), k.tf[1]);
     const float qz = __fsub_rn((float)(iz - k.ti[2]), k.tf[2]);
+    float pz = __fmaf_rn(k.Pr[8], qz, __fmaf_rn(k.Pr[7], qy, __fmul_rn(k.Pr[6], qx)));
+    float px = __fmaf_rn(k.Pr[2], qz, __fmaf_rn(k.Pr[1], qy, __fmul_rn(k.Pr[0], qx)));
+    float py = __fmaf_rn(k.Pr[5], qz, __fmaf_rn(k.Pr[4], qy, __fmul_rn(k.Pr[3], qx)));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float qx = __fsub_rn((float)(ix0 + j - k.ti[0]), k.tf[0]);
-        const float pz = __fmaf_rn(k.M[8], qz, __fmaf_rn(k.M[7], qy, __fmul_rn(k.M[6], qx)));
-        const float px = __fmaf_rn(k.M[2], qz, __fmaf_rn(k.M[1], qy, __fmul_rn(k.M[0], qx)));
-        const float py = __fmaf_rn(k.M[5], qz, __fmaf_rn(k.M[4], qy, __fmul_rn(k.M[3], qx)));
-        const float rz = __frcp_rn(pz);
+        if (j > 0) {
+            pz = __fadd_rn(pz, k.Pr[6]);
+            px = __fadd_rn(px, k.Pr[0]);
+            py = __fadd_rn(py, k.Pr[3]);
+        }
+        const float rz = rcp_approx(pz);
         // NaN / inf fail the range test
-        const float uu = __fadd_rn(__fmaf_rn(__fmul_rn(k.fx, px), rz, k.cx), 0.5f);
-        const float vv = __fadd_rn(__fmaf_rn(__fmul_rn(k.fy, py), rz, k.cy), 0.5f);
+        const float uu = __fmaf_rn(px, rz, k.cxh);
+        const float vv = __fmaf_rn(py, rz, k.cyh);
         p.pz[j] = pz;
         p.ok[j] = pz > 0.f && uu >= 0.f && uu < (float)k.W && vv >= 0.f && vv < (float)k.H;
         p.pix[j] = p.ok[j] ? (int)vv * k.W + (int)uu : 0;

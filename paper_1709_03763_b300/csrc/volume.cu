@@ -43,10 +43,11 @@ KfCam make_cam(const sc_volume* V, const sc_intrinsics* K, const sc_pose* T, con
         for (int q = 0; q < 3; ++q) R[r][q] = (double)T->m[r][q];
         t[r] = (double)T->m[r][3];
     }
+    const double fk[3] = {(double)K->fx, (double)K->fy, 1.0};
     for (int r = 0; r < 3; ++r)
         for (int q = 0; q < 3; ++q) {
-            c.M[r * 3 + q] = (float)(s * R[q][r]);   // s R^T
-            c.Ms[r * 3 + q] = (float)(R[r][q] / s);  // R / s
+            c.Pr[r * 3 + q] = (float)(fk[r] * s * R[q][r]);  // diag(fx, fy, 1) s R^T
+            c.Ms[r * 3 + q] = (float)(R[r][q] / s);          // R / s
         }
     for (int a = 0; a < 3; ++a) {
         const double tv = t[a] / s;
@@ -58,6 +59,8 @@ KfCam make_cam(const sc_volume* V, const sc_intrinsics* K, const sc_pose* T, con
     c.fy = K->fy;
     c.cx = K->cx;
     c.cy = K->cy;
+    c.cxh = (float)((double)K->cx + 0.5);
+    c.cyh = (float)((double)K->cy + 0.5);
     c.ifx = (float)(1.0 / (double)K->fx);
     c.ify = (float)(1.0 / (double)K->fy);
     c.W = K->width;
