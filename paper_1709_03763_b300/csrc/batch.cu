@@ -138,7 +138,7 @@ __global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const
 struct __align__(16) NdCam {
     float Pr[9];
     float tf[3];
-    int ti[3];
+    float tiF[3];
     float cxh, cyh, mu;
     int W, H;
     const uint2* tex;
@@ -150,7 +150,7 @@ __device__ __forceinline__ void load_ndcam(NdCam& o, const KfCam& k) {
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         o.tf[i] = k.tf[i];
-        o.ti[i] = k.ti[i];
+        o.tiF[i] = k.tiF[i];
     }
     o.cxh = k.cxh;
     o.cyh = k.cyh;
@@ -192,14 +192,14 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
 // colours are integer sums (exactly the float sums of the same integers); distances
 // are summed in float in item order.
 template <int SIGN>
-__device__ __forceinline__ void net_delta_word(const NdCam* cams, uint32_t word, const int4 c, int lx0, int ly,
-                                               int lz, float aD[4], int aW[4], int aC[4][3], bool& touched) {
+__device__ __forceinline__ void net_delta_word(const NdCam* cams, uint32_t word, float vx, float vy, float vz,
+                                               float aD[4], int aW[4], int aC[4][3], bool& touched) {
     while (word) {
         const int b = __ffs(word) - 1;
         word &= word - 1;
         const NdCam& k = cams[b];
         Proj4 P;
-        project4(k, 8 * c.x + lx0, 8 * c.y + ly, 8 * c.z + lz, P);
+        project4(k, vx, vy, vz, P);
         uint2 t[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
@@ -233,13 +233,14 @@ __device__ __forceinline__ void net_delta_group(const NdCam* cams, int n, const 
                                                 uint32_t mw0, uint32_t mw1, int mw, float aD[4], int aW[4],
                                                 int aC[4][3], bool& touched) {
     const int half = mw / 2;
+    const float vx = (float)(8 * c.x + lx0), vy = (float)(8 * c.y + ly), vz = (float)(8 * c.z + lz);
     for (int w = 0; w < half; ++w) {
         const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        net_delta_word<-1>(cams + (w << 5), word, c, lx0, ly, lz, aD, aW, aC, touched);
+        net_delta_word<-1>(cams + (w << 5), word, vx, vy, vz, aD, aW, aC, touched);
     }
     for (int w = half; w < mw; ++w) {
         const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        net_delta_word<1>(cams + n + ((w - half) << 5), word, c, lx0, ly, lz, aD, aW, aC, touched);
+        net_delta_word<1>(cams + n + ((w - half) << 5), word, vx, vy, vz, aD, aW, aC, touched);
     }
 }
 

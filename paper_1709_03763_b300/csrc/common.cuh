@@ -96,6 +96,7 @@ struct KfCam {
     float Ms[9];
     float tf[3];
     int ti[3];
+    float tiF[3];    // ti as floats (exact: |ti| < 2^21)
     float fx, fy, cx, cy;
     float cxh, cyh;  // cx + 1/2, cy + 1/2: nearest pixel = floor(u + 1/2)
     float ifx, ify;  // 1 / fx, 1 / fy
@@ -113,7 +114,12 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// Projection of the 4 voxels (ix0 + j, iy, iz), j = 0..3, that one thread owns.
+// floor(x) for 0 <= x < 2^23 without a conversion instruction: adding 2^23 rounded
+// down leaves floor(x) in the mantissa.
+__device__ __forceinline__ int floor_small(float x) { return __float_as_int(__fadd_rd(x, 8388608.f)) - 0x4b000000; }
+
+// Projection of the 4 voxels (ix0 + j, iy, iz), j = 0..3, that one thread owns,
+// given as floats (exact integers).
 // Every operation is an explicit round-to-nearest intrinsic (or the one approximate
 // reciprocal), in one fixed order, so that integration, de-integration, the batched
 // net-delta kernel and the adjoint reach bit-identical decisions and distances for
@@ -128,10 +134,11 @@ struct Proj4 {
 };
 
 template <typename Cam>
-__device__ __forceinline__ void project4(const Cam& k, int ix0, int iy, int iz, Proj4& p) {
-    const float qx = __fsub_rn((float)(ix0 - k.ti[0]), k.tf[0]);
-    const float qy = __fsub_rn((float)(iy - k.ti[1]), k.tf[1]);
-    const float qz = __fsub_rn((float)(iz - k.ti[2]), k.tf[2]);
+__device__ __forceinline__ void project4(const Cam& k, float ix0, float iy, float iz, Proj4& p) {
+    // (i - ti) is exact in float, so this is the relative index (i - ti) - tf rounded once
+    const float qx = __fsub_rn(__fsub_rn(ix0, k.tiF[0]), k.tf[0]);
+    const float qy = __fsub_rn(__fsub_rn(iy, k.tiF[1]), k.tf[1]);
+    const float qz = __fsub_rn(__fsub_rn(iz, k.tiF[2]), k.tf[2]);
     float pz = __fmaf_rn(k.Pr[8], qz, __fmaf_rn(k.Pr[7], qy, __fmul_rn(k.Pr[6], qx)));
     float px = __fmaf_rn(k.Pr[2], qz, __fmaf_rn(k.Pr[1], qy, __fmul_rn(k.Pr[0], qx)));
     float py = __fmaf_rn(k.Pr[5], qz, __fmaf_rn(k.Pr[4], qy, __fmul_rn(k.Pr[3], qx)));
@@ -148,7 +155,7 @@ __device__ __forceinline__ void project4(const Cam& k, int ix0, int iy, int iz, 
         const float vv = __fmaf_rn(py, rz, k.cyh);
         p.pz[j] = pz;
         p.ok[j] = pz > 0.f && uu >= 0.f && uu < (float)k.W && vv >= 0.f && vv < (float)k.H;
-        p.pix[j] = p.ok[j] ? (int)vv * k.W + (int)uu : 0;
+        p.pix[j] = p.ok[j] ? floor_small(vv) * k.W + floor_small(uu) : 0;
     }
 }
 

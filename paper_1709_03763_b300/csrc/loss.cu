@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
             const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
             const int iy = 8 * c.y + ly, iz = 8 * c.z + lz;
             Proj4 P;
-            project4(cam, 8 * c.x + lx0, iy, iz, P);
+            project4(cam, (float)(8 * c.x + lx0), (float)iy, (float)iz, P);
             float Z[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) Z[j] = P.ok[j] ? __ldg(cam.depth + P.pix[j]) : 0.f;

@@ -53,6 +53,7 @@ KfCam make_cam(const sc_volume* V, const sc_intrinsics* K, const sc_pose* T, con
         const double tv = t[a] / s;
         const double fl = std::floor(tv);
         c.ti[a] = (int)fl;
+        c.tiF[a] = (float)fl;
         c.tf[a] = (float)(tv - fl);
     }
     c.fx = K->fx;
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam 
             if (fresh && t == 0) V.flags[slot] = 0;
         }
         Proj4 P;
-        project4(k, 8 * c.x + lx0, 8 * c.y + ly, 8 * c.z + lz, P);
+        project4(k, (float)(8 * c.x + lx0), (float)(8 * c.y + ly), (float)(8 * c.z + lz), P);
         float Z[4], d[4], eta;
 #pragma unroll
         for (int j = 0; j < 4; ++j) Z[j] = P.ok[j] ? __ldg(k.depth + P.pix[j]) : 0.f;
