@@ -91,6 +91,10 @@ def _declare(L):
     L.or_fuse_colour.argtypes = [_p, _p, _p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _d, _d,
                                  _p, _p, _p, _p, _p, _p, _p]
     L.or_fuse_colour.restype = _i
+    L.or_marching_cubes.argtypes = [_p, _p, _p, _l, _d, _p, _p, _l]
+    L.or_marching_cubes.restype = _l
+    L.or_mc_case.argtypes = [_i, _p]
+    L.or_mc_case.restype = _i
 
 
 def _ptr(a):
@@ -199,6 +203,28 @@ def fuse_colour(rgba, depths, poses, kf_depth, kf_pose, intr, disc_rel=0.1, occl
                          f32(disc_rel), f32(occl_rel), _ptr(out.median), _ptr(out.err), _ptr(out.rgba),
                          _ptr(out.nobs), _ptr(out.wsum), _ptr(out.flag), _ptr(out.wb))
     return out
+
+
+def mc_case(mask: int) -> np.ndarray:
+    """Triangles (edge triples [t,3]) of one cube whose inside corners are the bits of mask."""
+    e = np.zeros((12, 3), np.int32)
+    t = lib().or_mc_case(int(mask), _ptr(e))
+    return e[:t].copy()
+
+
+def marching_cubes(coords, D, W, voxel_size):
+    """Marching Cubes over blocks (coords [n,3] int32, D, W [n,512] f32).  Returns
+    (triangles [t,3,3] f64 metres, cube [t,4] int32 = first corner voxel + triangle number)."""
+    c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+    d = _f32(D).reshape(-1, 512)
+    w = _f32(W).reshape(-1, 512)
+    n = len(c)
+    vs = f32(voxel_size)
+    cnt = lib().or_marching_cubes(_ptr(c), _ptr(d), _ptr(w), n, vs, None, None, 0)
+    tri = np.zeros((max(cnt, 1), 3, 3))
+    cube = np.zeros((max(cnt, 1), 4), np.int32)
+    lib().or_marching_cubes(_ptr(c), _ptr(d), _ptr(w), n, vs, _ptr(tri), _ptr(cube), cnt)
+    return tri[:cnt], cube[:cnt]
 
 
 def allocation_set(depth, pose, intr, voxel_size, trunc):

@@ -55,6 +55,7 @@
 // the parity tests leave flagged items out of exact comparisons.
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -1325,4 +1326,211 @@ extern "C" int or_fuse_colour(const uint8_t* rgba, const float* depths, const fl
             out_rgba[p * 4 + 3] = 255;
         }
     return 0;
+}
+
+// ============================================================================
+// Marching Cubes iso-surface extraction (Section 3 "SDF volume")
+// ============================================================================
+//
+// The paper extracts the zero level set of D with Marching Cubes.  The cube of
+// voxel (x, y, z) has corners (x + i0, y + i1, z + i2), i the three bits of the
+// corner number; it is meshed only if all 8 corner voxels exist and are observed
+// (W > 0).  A corner is inside when D < 0.  Every cube edge whose corners differ
+// carries one vertex, linearly interpolated to D = 0.
+//
+// Reading of the triangulation (the paper cites Marching Cubes without a case
+// table; this is a rule, applied cube by cube):
+//  * on each face, walking its four corners in cyclic order, the crossed edges are
+//    joined by segments: two crossed edges form one segment; with four (inside
+//    corners diagonal) each inside corner is cut off by the segment joining its two
+//    edges, so inside corners never connect across a face;
+//  * every crossed edge lies on two faces, so the segments close into loops;
+//  * a loop is oriented so that its Newell normal, computed on the edge midpoints,
+//    points along the sum over its edges of the edge direction from the inside
+//    corner to the outside one: triangle normals point to D > 0 (free space);
+//  * a loop is fanned from its smallest edge number: (e0, e_i, e_i+1); loops in
+//    order of their smallest edge number.
+// Edge numbering: axis a = e / 4 (x, y, z); r = e % 4 gives the corner bits of the
+// two other axes (lower axis in bit 0).
+
+namespace {
+
+struct McEdge {
+    int axis, lo, hi;
+};
+
+McEdge mc_edge(int e) {
+    const int a = e / 4, r = e % 4;
+    int b = -1, c = -1;
+    for (int d = 0; d < 3; ++d)
+        if (d != a) {
+            if (b < 0) b = d;
+            else c = d;
+        }
+    const int lo = ((r & 1) << b) | (((r >> 1) & 1) << c);
+    return McEdge{a, lo, lo | (1 << a)};
+}
+
+int mc_edge_of(int c0, int c1) {
+    for (int e = 0; e < 12; ++e) {
+        const McEdge E = mc_edge(e);
+        if ((E.lo == c0 && E.hi == c1) || (E.lo == c1 && E.hi == c0)) return e;
+    }
+    return -1;
+}
+
+// Triangles (edge triples) of one cube given its inside-corner bit mask.
+std::vector<std::array<int, 3>> mc_cube_triangles(int inside) {
+    auto in = [&](int corner) { return (inside >> corner) & 1; };
+    // partner[e][0 / 1]: the crossed edges e is joined to on its two faces
+    int partner[12][2];
+    int np[12] = {0};
+    for (int f = 0; f < 6; ++f) {
+        const int a = f / 2, side = f % 2;
+        int b = -1, c = -1;
+        for (int d = 0; d < 3; ++d)
+            if (d != a) {
+                if (b < 0) b = d;
+                else c = d;
+            }
+        const int cyc[4] = {(side << a), (side << a) | (1 << b), (side << a) | (1 << b) | (1 << c),
+                            (side << a) | (1 << c)};
+        int cut[4];  // cut[k]: edge between cyc[k] and cyc[k+1] if crossed, else -1
+        int ncut = 0;
+        for (int k = 0; k < 4; ++k) {
+            const int c0 = cyc[k], c1 = cyc[(k + 1) % 4];
+            cut[k] = in(c0) != in(c1) ? mc_edge_of(c0, c1) : -1;
+            ncut += cut[k] >= 0;
+        }
+        auto join = [&](int e0, int e1) {
+            partner[e0][np[e0]++] = e1;
+            partner[e1][np[e1]++] = e0;
+        };
+        if (ncut == 2) {
+            int first = -1;
+            for (int k = 0; k < 4; ++k)
+                if (cut[k] >= 0) {
+                    if (first < 0) first = cut[k];
+                    else join(first, cut[k]);
+                }
+        } else if (ncut == 4) {
+            for (int k = 0; k < 4; ++k)
+                if (in(cyc[k])) join(cut[(k + 3) % 4], cut[k]);  // the two edges at inside corner k
+        }
+    }
+    // loops
+    std::vector<std::array<int, 3>> tris;
+    bool used[12] = {false};
+    for (int start = 0; start < 12; ++start) {
+        const McEdge S = mc_edge(start);
+        if (used[start] || in(S.lo) == in(S.hi)) continue;
+        std::vector<int> loop{start};
+        used[start] = true;
+        int prev = start, cur = partner[start][0];
+        while (cur != start) {
+            loop.push_back(cur);
+            used[cur] = true;
+            const int next = partner[cur][0] == prev ? partner[cur][1] : partner[cur][0];
+            prev = cur;
+            cur = next;
+        }
+        // orientation: Newell normal of the midpoints against the inside -> outside directions
+        double N[3] = {0, 0, 0}, g[3] = {0, 0, 0};
+        const size_t m = loop.size();
+        std::vector<std::array<double, 3>> q(m);
+        for (size_t i = 0; i < m; ++i) {
+            const McEdge E = mc_edge(loop[i]);
+            for (int d = 0; d < 3; ++d) q[i][d] = ((E.lo >> d) & 1) + (d == E.axis ? 0.5 : 0.0);
+            g[E.axis] += in(E.lo) ? 1.0 : -1.0;
+        }
+        for (size_t i = 0; i < m; ++i) {
+            const auto& p0 = q[i];
+            const auto& p1 = q[(i + 1) % m];
+            N[0] += (p0[1] - p1[1]) * (p0[2] + p1[2]);
+            N[1] += (p0[2] - p1[2]) * (p0[0] + p1[0]);
+            N[2] += (p0[0] - p1[0]) * (p0[1] + p1[1]);
+        }
+        if (N[0] * g[0] + N[1] * g[1] + N[2] * g[2] < 0.0) std::reverse(loop.begin(), loop.end());
+        // loop starts at its smallest edge number, which is `start` (loops are found in edge order)
+        const auto it = std::find(loop.begin(), loop.end(), start);
+        std::rotate(loop.begin(), it, loop.end());
+        for (size_t i = 1; i + 1 < m; ++i) tris.push_back({loop[0], loop[i], loop[i + 1]});
+    }
+    return tris;
+}
+
+}  // namespace
+
+// Marching Cubes over blocks given as arrays (coords [n][3] block coordinates,
+// D and W [n][512], voxel index x + 8 y + 64 z).  Writes up to cap triangles:
+// tri [cap][3][3] vertex positions in metres (voxel i at i * voxel_size) and cube
+// [cap][4] = (x, y, z of the cube's first corner voxel, triangle number within the
+// cube).  Returns the number of triangles (which may exceed cap).
+extern "C" long or_marching_cubes(const int32_t* coords, const float* D, const float* W, long n,
+                                  double voxel_size, double* tri, int32_t* cube, long cap) {
+    std::unordered_map<int64_t, long> index;
+    for (long b = 0; b < n; ++b) index[pack(coords[3 * b], coords[3 * b + 1], coords[3 * b + 2])] = b;
+    // the triangulation of every inside mask (the rule above, per cube)
+    static std::vector<std::array<int, 3>> cases[256];
+    static bool built = false;
+    if (!built) {
+        for (int m = 0; m < 256; ++m) cases[m] = mc_cube_triangles(m);
+        built = true;
+    }
+    long count = 0;
+    for (long b = 0; b < n; ++b) {
+        const long bx = coords[3 * b], by = coords[3 * b + 1], bz = coords[3 * b + 2];
+        for (int lz = 0; lz < BS; ++lz)
+            for (int ly = 0; ly < BS; ++ly)
+                for (int lx = 0; lx < BS; ++lx) {
+                    double cd[8];
+                    long cv[8][3];
+                    bool ok = true;
+                    for (int i = 0; i < 8 && ok; ++i) {
+                        const long vx = bx * BS + lx + (i & 1), vy = by * BS + ly + ((i >> 1) & 1),
+                                   vz = bz * BS + lz + ((i >> 2) & 1);
+                        const auto f = index.find(pack(floor_div(vx, BS), floor_div(vy, BS), floor_div(vz, BS)));
+                        if (f == index.end()) {
+                            ok = false;
+                            break;
+                        }
+                        const long vi = (vx - floor_div(vx, BS) * BS) + BS * (vy - floor_div(vy, BS) * BS) +
+                                        BS * BS * (vz - floor_div(vz, BS) * BS);
+                        if (!(W[f->second * NV + vi] > 0.0f)) ok = false;
+                        cd[i] = D[f->second * NV + vi];
+                        cv[i][0] = vx;
+                        cv[i][1] = vy;
+                        cv[i][2] = vz;
+                    }
+                    if (!ok) continue;
+                    int inside = 0;
+                    for (int i = 0; i < 8; ++i) inside |= (cd[i] < 0.0 ? 1 : 0) << i;
+                    const auto& tl = cases[inside];
+                    for (size_t k = 0; k < tl.size(); ++k) {
+                        if (count < cap) {
+                            for (int j = 0; j < 3; ++j) {
+                                const McEdge E = mc_edge(tl[k][j]);
+                                const double t = cd[E.lo] / (cd[E.lo] - cd[E.hi]);
+                                for (int d = 0; d < 3; ++d)
+                                    tri[count * 9 + 3 * j + d] =
+                                        voxel_size * ((double)cv[E.lo][d] + (d == E.axis ? t : 0.0));
+                            }
+                            cube[count * 4] = (int32_t)(bx * BS + lx);
+                            cube[count * 4 + 1] = (int32_t)(by * BS + ly);
+                            cube[count * 4 + 2] = (int32_t)(bz * BS + lz);
+                            cube[count * 4 + 3] = (int32_t)k;
+                        }
+                        ++count;
+                    }
+                }
+    }
+    return count;
+}
+
+// The triangulation rule alone: edge triples of inside mask m (for the pins).
+extern "C" int or_mc_case(int m, int32_t* edges) {
+    const auto t = mc_cube_triangles(m & 255);
+    for (size_t k = 0; k < t.size(); ++k)
+        for (int j = 0; j < 3; ++j) edges[3 * k + j] = t[k][j];
+    return (int)t.size();
 }
