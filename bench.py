@@ -17,8 +17,8 @@ value = 60 re-integrations / step time.  The JSON line also reports the update
 alone, batched (one graph) vs plain (120 per-keyframe calls), the roofline of the
 dominant kernel, the oracle on the host cores, clocks and the kernel count, and,
 under "rows", colour keyframe fusion of the 600 textured frames into the 60
-keyframes (its CUDA-event time, HBM roofline and the oracle beside it), measured
-outside the step.
+keyframes (its CUDA-event time, HBM roofline and the oracle beside it), and
+Marching Cubes of the corrected volume, both measured outside the step.
 
 --gpus N > 1 (under torchrun) runs N independent replicas (the path does not
 shard across GPUs in this build); value sums the replicas' throughput.
@@ -350,6 +350,36 @@ def colour_timing(P, reps, warmup):
     return statistics.median(ts)
 
 
+def oracle_mc(max_blocks=20000):
+    """The oracle's Marching Cubes on (a bounded sample of) the oracle's own re-integrated
+    volume from the CPU baseline: (blocks per second, blocks, triangles, seconds)."""
+    import oracle
+    O = getattr(oracle_reintegration, "last_volume", None)
+    if O is None:
+        return None
+    ex = O.export()
+    n = min(max_blocks, len(ex.coords))
+    D, W = ex.D[:n].astype(np.float32), ex.W[:n].astype(np.float32)
+    t0 = time.perf_counter()
+    tri, _ = oracle.marching_cubes(ex.coords[:n], D, W, O.voxel_size)
+    dt = time.perf_counter() - t0
+    return n / dt, n, len(tri), dt
+
+
+def mc_timing(V, out, reps, warmup):
+    """Median time of one sc_marching_cubes call (count read-back and status included)."""
+    import torch
+    for _ in range(warmup):
+        tri = V.marching_cubes(capacity=out.shape[0], out=out)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        tri = V.marching_cubes(capacity=out.shape[0], out=out)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return statistics.median(ts), int(tri.shape[0])
+
+
 def oracle_colour(w, kf_depth, n_kf=3):
     """The oracle's colour fusion of the first n_kf keyframes (10 frames each) on the host
     cores: (keyframes per second, threads)."""
@@ -398,6 +428,7 @@ def oracle_reintegration(n_kf, steps=1, warmup=0, w=None):
             O.integrate(k, depth[k], rgba[k], it, w.new_poses[k])
         if step >= warmup:
             times.append(time.perf_counter() - t0)
+    oracle_reintegration.last_volume = O
     return statistics.median(times), oracle.get_threads()
 
 
@@ -600,6 +631,23 @@ def main():
     roofline["hbm_view"] = {"peak_GBps": hbm_peak, "peak_kind": peak_kind, "kernels": hbm}
     prof = {"update": prof_upd, "integrate": prof_int, "plain_integrate": prof_plain, "fusion": fprof}
 
+    # ---- Marching Cubes of the corrected volume (after the step's pose update), measured
+    # on its own: one call = the slot-count read-back, one kernel launch, count + status
+    P.step()
+    torch.cuda.synchronize()
+    n_blocks = V.info()["allocated_blocks"]
+    mc_out = torch.empty((8 << 20, 3, 3), dtype=torch.float32, device=dev)
+    mc_ms, n_tri = mc_timing(V, mc_out, 10, 3)
+    mc_b = n_blocks * 512 * 8 + n_tri * 36
+    mc_gbs = mc_b / (mc_ms / 1e3) / 1e9
+    mc_row = {"ms_per_call": mc_ms, "blocks": n_blocks, "triangles": n_tri,
+              "blocks_per_s": ws * n_blocks / (mc_ms / 1e3),
+              "roofline": {"bound": "hbm", "achieved": mc_gbs, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": mc_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                           "algorithmic_bytes": mc_b,
+                           "note": "whole call time (host round trips included): a lower bound on the kernel's rate"}}
+    del mc_out
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample, w)
@@ -607,6 +655,11 @@ def main():
         colour_row["cpu_baseline"] = {"value": kps, "unit": "keyframes/s", "cores": threads, "kind": "oracle",
                                       "sample": f"colour fusion of 3 keyframes (10 frames each, 640x480), FP64, "
                                                 f"{dt:.1f} s"}
+        om = oracle_mc()
+        if om:
+            mc_row["cpu_baseline"] = {"value": om[0], "unit": "blocks/s", "cores": 1, "kind": "oracle",
+                                      "sample": f"Marching Cubes of {om[1]} blocks of the oracle's re-integrated "
+                                                f"volume ({om[2]} triangles), FP64, {om[3]:.1f} s"}
 
     if rank == 0:
         line = {
@@ -631,7 +684,7 @@ def main():
             "profile": prof,
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "rows": {"colour_fusion": colour_row},
+            "rows": {"colour_fusion": colour_row, "marching_cubes": mc_row},
             "clocks": clocks,
             "setup_s": setup_s,
         }

@@ -297,6 +297,45 @@ int sc_extract_block_list(sc_volume* vol, int32_t* coords, int32_t* slots, float
 int sc_get_keyframe_blocks(sc_volume* vol, int32_t kf_id, int32_t* slots, int32_t capacity, int32_t* count,
                            sc_stream stream);
 
+/* ------------------------------------------------- marching cubes, import ---- */
+
+/* Iso-surface extraction (Section 3 "SDF volume": the surface is extracted with
+ * Marching Cubes).  Cube (x, y, z) has the corner voxels (x + i0, y + i1, z + i2),
+ * i0..i2 the bits of the corner number 0..7; it is meshed when all 8 corner voxels
+ * are allocated and observed (W > 0).  A corner is inside when D < 0; each cube
+ * edge between an inside and an outside corner carries the vertex
+ * p = voxel_size * (v_lo + t e_axis), t = D_lo / (D_lo - D_hi).  Edge e (0..11)
+ * runs along axis e / 4 from the corner whose two other coordinate bits are e % 4
+ * (lower axis in bit 0).  Triangulation rule: on each cube face, every maximal run
+ * of inside corners around the face (not all four) is closed off by one segment
+ * joining the crossed edges at its ends (diagonal inside corners are cut off
+ * separately); the segments chain into loops oriented so that triangle normals
+ * (v1 - v0) x (v2 - v0) point to D > 0; each loop is fanned from its smallest edge,
+ * loops in order of their smallest edge.  At most 5 triangles per cube.
+ * triangles device [capacity][3][3] float (metres, world frame of the volume);
+ * cubes device [capacity][4] int32 (first corner voxel x, y, z and the triangle's
+ * number within its cube) or NULL.  *count (host) receives the number of
+ * triangles; output order is unspecified; SC_ERR_CAPACITY if it exceeds capacity
+ * (the first `capacity` found are written).  Synchronises the stream. */
+int sc_marching_cubes(sc_volume* vol, float* triangles, int32_t* cubes, int64_t capacity, int64_t* count,
+                      sc_stream stream);
+
+/* The triangulation rule alone: for the inside-corner mask (0..255), writes the
+ * edge triples of its triangles to edges (host, up to 15 ints) and returns their
+ * number (0..5), or a negative status.  Host only. */
+int sc_mc_case(int32_t mask, int32_t* edges);
+
+/* Load voxel blocks into a volume (restore, or a volume made elsewhere): for each of
+ * n blocks, coords device [n][3] int32 block coordinates (distinct, each in
+ * [-2^20, 2^20)), D and W device [n][512] float (voxel x + 8 y + 64 z), C device
+ * [n][512] uint32 RGBA8 or [n][3][512] float (the volume's colour format) or NULL
+ * (black).  An absent block is inserted and takes a pool slot; a present one is
+ * overwritten.  Keyframe block lists are not changed.  Device arrays 16-byte
+ * aligned.  Returns SC_ERR_INVALID_ARG for a coordinate out of range, SC_ERR_HASH_FULL
+ * / SC_ERR_POOL_FULL when the volume is full.  Synchronises the stream. */
+int sc_import_blocks(sc_volume* vol, const int32_t* coords, const float* D, const float* W, const void* C,
+                     int32_t n, sc_stream stream);
+
 /* --------------------------------------------- loss and adjoint (extension) ---- */
 
 /* Loss on the fused SDF (no counterpart in the paper):

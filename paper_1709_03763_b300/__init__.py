@@ -9,4 +9,4 @@ include/surfcorr.h); this package marshals torch tensors into it.
 """
 from ._lib import SurfcorrError, lib  # noqa: F401
 from .volume import (Volume, fuse_colour_keyframes, fuse_frames_into_keyframe, fuse_keyframes, prepare_colour, make_intrinsics, prepare_fuse, make_pose, pose_distance,  # noqa: F401
-                     pose_exp_left, select_consecutive, select_topm)
+                     mc_case, pose_exp_left, select_consecutive, select_topm)

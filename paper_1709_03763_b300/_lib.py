@@ -100,6 +100,9 @@ SIGNATURES = {
     "sc_get_batch_config": (c_i32, [c_p, P(BatchConfig)]),
     "sc_autotune_batch": (c_i32, [c_p, P(ReintItem), c_i32, P(Intrinsics), c_p, P(BatchConfig), P(c_f)]),
     "sc_extract_block_list": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_i32, P(c_i32), c_p]),
+    "sc_marching_cubes": (c_i32, [c_p, c_p, c_p, c_i64, P(c_i64), c_p]),
+    "sc_mc_case": (c_i32, [c_i32, P(c_i32)]),
+    "sc_import_blocks": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i32, c_p]),
     "sc_get_keyframe_blocks": (c_i32, [c_p, c_i32, c_p, c_i32, P(c_i32), c_p]),
     "sc_sdf_loss": (c_i32, [c_p, c_p, c_i64, c_f, c_p, c_p, c_p]),
     "sc_sdf_adjoint": (c_i32, [c_p, P(c_i32), P(c_p), P(Pose), c_i32, P(Intrinsics), c_p, c_p, c_p, c_p]),

@@ -398,7 +398,7 @@ extern "C" int sc_create_volume(const sc_volume_params* p, sc_volume** out) {
     if ((e = dalloc(V, &V->list_counts, (size_t)p->max_keyframes * 2 * sizeof(int32_t))) != cudaSuccess)
         return fail(e);
     if ((e = dalloc(V, &V->extract_slots, nb * sizeof(int32_t))) != cudaSuccess) return fail(e);
-    if ((e = dalloc(V, &V->extract_count, sizeof(uint32_t))) != cudaSuccess) return fail(e);
+    if ((e = dalloc(V, &V->extract_count, sizeof(unsigned long long))) != cudaSuccess) return fail(e);
     if ((e = dalloc(V, &V->prof_dev, 4 * sizeof(unsigned long long))) != cudaSuccess) return fail(e);
     if ((e = cudaMemset(V->prof_dev, 0, 4 * sizeof(unsigned long long))) != cudaSuccess) return fail(e);
     for (cudaEvent_t& ev : V->graph_ev)

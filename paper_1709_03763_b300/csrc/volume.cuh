@@ -26,7 +26,7 @@ struct sc_volume {
     int32_t* lists;        // [max_keyframes][2][max_blocks_per_keyframe]
     int32_t* list_counts;  // [max_keyframes][2]
     int32_t* extract_slots;  // [max_blocks] scratch for extraction
-    uint32_t* extract_count;
+    uint32_t* extract_count;  // 8 bytes: 32-bit extraction count, 64-bit triangle count
     // host mirrors
     std::vector<uint8_t> integrated;
     std::vector<uint8_t> cur;  // which of the two list buffers holds the current list

@@ -18,7 +18,7 @@ from ._lib import (BatchConfig, ColourParams, FusionParams, Intrinsics, Pose, Pr
 
 __all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
            "prepare_colour", "pose_distance", "select_topm", "select_consecutive",
-           "pose_exp_left", "SurfcorrError", "make_intrinsics", "make_pose"]
+           "pose_exp_left", "mc_case", "SurfcorrError", "make_intrinsics", "make_pose"]
 
 
 def make_intrinsics(intr) -> Intrinsics:
@@ -223,6 +223,44 @@ class Volume:
             out.update(D=D[:m], W=W[:m], C=C[:m])
         return out
 
+    def import_blocks(self, coords: torch.Tensor, D: torch.Tensor, W: torch.Tensor, C: torch.Tensor | None = None,
+                      stream=None):
+        """Insert / overwrite blocks: coords [n,3] int32, D / W [n,512] float32, C [n,512,4] uint8
+        (rgba8) or [n,3,512] float32 (f32) or None (device tensors)."""
+        n = int(coords.shape[0])
+        if n == 0:
+            return
+        if D.shape != (n, 512) or W.shape != (n, 512):
+            raise ValueError("D and W must be [n, 512]")
+        cptr = None
+        if C is not None:
+            cptr = (_dev(C, torch.float32, "C") if self.colour == "f32" else _dev(C, torch.uint8, "C"))
+            if C.numel() != n * 512 * (3 if self.colour == "f32" else 4):
+                raise ValueError("C has the wrong size for the volume's colour format")
+        check(lib().sc_import_blocks(self.h, _dev(coords, torch.int32, "coords"), _dev(D, torch.float32, "D"),
+                                     _dev(W, torch.float32, "W"), cptr, n, _stream(stream)), "sc_import_blocks")
+
+    def marching_cubes(self, capacity: int | None = None, cubes: bool = False, out: torch.Tensor | None = None,
+                       stream=None):
+        """Zero-level-set triangles [t,3,3] float32 (metres) and, with cubes=True, their cube
+        ids [t,4] int32 (first corner voxel, triangle number in the cube).  Unordered.
+        Without a capacity the call counts first, then extracts."""
+        dev = torch.device("cuda", self.device)
+        n = ctypes.c_int64(0)
+        if capacity is None and out is None:
+            rc = lib().sc_marching_cubes(self.h, None, None, 0, ctypes.byref(n), _stream(stream))
+            if rc not in (_lib.SC_OK, _lib.SC_ERR_CAPACITY):
+                check(rc, "sc_marching_cubes")
+            capacity = n.value
+        if out is None:
+            out = torch.empty((max(int(capacity), 1), 3, 3), dtype=torch.float32, device=dev)
+        cap = out.shape[0] if capacity is None else int(capacity)
+        cb = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=dev) if cubes else None
+        check(lib().sc_marching_cubes(self.h, _dev(out, torch.float32, "out"), cb.data_ptr() if cubes else None,
+                                      cap, ctypes.byref(n), _stream(stream)), "sc_marching_cubes")
+        t = n.value
+        return (out[:t], cb[:t]) if cubes else out[:t]
+
     def keyframe_blocks(self, kf_id: int, stream=None) -> torch.Tensor:
         """Pool slots of kf_id's stored block list (its allocation set A(k, T))."""
         n = ctypes.c_int32(0)
@@ -409,6 +447,15 @@ def select_consecutive(dist, m: int) -> int:
     if j < 0:
         raise SurfcorrError(j, "sc_select_consecutive")
     return j
+
+
+def mc_case(mask: int) -> np.ndarray:
+    """The library's Marching Cubes triangulation of an inside-corner mask: edge triples [t,3]."""
+    e = (ctypes.c_int32 * 15)()
+    t = lib().sc_mc_case(int(mask), e)
+    if t < 0:
+        raise SurfcorrError(t, "sc_mc_case")
+    return np.array(list(e)[:3 * t], dtype=np.int32).reshape(t, 3)
 
 
 def pose_exp_left(T, xi) -> np.ndarray:
