@@ -95,6 +95,9 @@ def _declare(L):
     L.or_marching_cubes.restype = _l
     L.or_mc_case.argtypes = [_i, _p]
     L.or_mc_case.restype = _i
+    L.or_overlap.argtypes = [_p, _p, _p, _d, _d, _d, _d, _i, _i, _p]
+    L.or_segment.argtypes = [_i, _d, _d, _p, _p, _i, _d, _d, _d, _d, _i, _i, _p, _p]
+    L.or_segment.restype = _i
 
 
 def _ptr(a):
@@ -225,6 +228,42 @@ def marching_cubes(coords, D, W, voxel_size):
     cube = np.zeros((max(cnt, 1), 4), np.int32)
     lib().or_marching_cubes(_ptr(c), _ptr(d), _ptr(w), n, vs, _ptr(tri), _ptr(cube), cnt)
     return tri[:cnt], cube[:cnt]
+
+
+KF_CONST, KF_DIST, KF_OVRLP = 0, 1, 2
+
+
+def overlap(depth, frame_pose, kf_pose, intr):
+    """Overlap counts of a frame against a keyframe: (valid, inside, marginal)."""
+    d = _f32(_np(depth))
+    H, W = d.shape
+    c = np.zeros(3, np.int64)
+    fx, fy, cx, cy = _intr(intr)
+    lib().or_overlap(_ptr(d), _ptr(_f32(frame_pose).reshape(12)), _ptr(_f32(kf_pose).reshape(12)), fx, fy, cx, cy,
+                     W, H, _ptr(c))
+    return int(c[0]), int(c[1]), int(c[2])
+
+
+def segment(strategy, params, poses, intr=None, depths=None):
+    """Keyframe groups of frames in order: (frame_kf [n] int32, flag [n] u8, number of keyframes).
+    KF_CONST: params = (kappa,); KF_DIST: (thr_t, thr_r); KF_OVRLP: (thr,) with depths [n,H,W]."""
+    p = _f32(_np(poses)).reshape(-1, 12)
+    n = len(p)
+    fk = np.zeros(n, np.int32)
+    fl = np.zeros(n, np.uint8)
+    p0 = float(params[0])
+    p1 = float(params[1]) if len(params) > 1 else 0.0
+    if strategy == KF_OVRLP:
+        d = _f32(_np(depths))
+        H, W = d.shape[1:]
+        fx, fy, cx, cy = _intr(intr)
+        p0 = f32(p0)
+    else:
+        d, H, W, fx, fy, cx, cy = None, 0, 0, 0.0, 0.0, 0.0, 0.0
+        if strategy == KF_DIST:
+            p0, p1 = f32(p0), f32(p1)
+    g = lib().or_segment(int(strategy), p0, p1, _ptr(d), _ptr(p), n, fx, fy, cx, cy, W, H, _ptr(fk), _ptr(fl))
+    return fk, fl, g
 
 
 def allocation_set(depth, pose, intr, voxel_size, trunc):

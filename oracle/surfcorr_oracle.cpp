@@ -36,6 +36,15 @@
 //                            translated views of a ramp (sign and size of the warp, exact
 //                            bilinear samples), w_z = cos(theta)/z^2 on a tilted plane,
 //                            dropped occluded / out-of-view samples.
+//   or_marching_cubes,       Marching Cubes (Section 3 "SDF volume") under a stated
+//   or_mc_case               triangulation rule.  Pinned: single-corner, checkerboard and
+//                            half-cube cases; a plane (vertices, area, orientation,
+//                            skipped cubes); a sphere (distance bound, closed orientable
+//                            genus-0 mesh, enclosed volume).
+//   or_overlap, or_segment   Keyframe strategies KF_CONST / KF_DIST / KF_OVRLP (Section
+//                            4.2).  Pinned: constant groups, translation and rotation
+//                            steps against the distance thresholds, the closed-form
+//                            overlap of sideways views of a plane.
 //   or_loss, or_grad,        Loss on the fused SDF and its analytic gradient with
 //   or_loss_perturbed        respect to keyframe se(3) poses and depth pixels (this
 //                            extension has no counterpart in the paper).  Pinned: a
@@ -1533,4 +1542,112 @@ extern "C" int or_mc_case(int m, int32_t* edges) {
     for (size_t k = 0; k < t.size(); ++k)
         for (int j = 0; j < 3; ++j) edges[3 * k + j] = t[k][j];
     return (int)t.size();
+}
+
+// ============================================================================
+// Keyframe strategies (Section 4.2): KF_CONST, KF_DIST, KF_OVRLP
+// ============================================================================
+//
+// Frames are taken in order; frame 0 starts the first group and the frame that
+// triggers a new keyframe starts the next group (its pose is the keyframe pose).
+//  * KF_CONST(kappa): a new keyframe every kappa frames.
+//  * KF_DIST(thr_t, thr_r): a new keyframe when the relative pose between the current
+//    frame and the current keyframe has translation norm > thr_t (metres) or rotation
+//    angle > thr_r (radians).  Reading: translation norm |t_f - t_k| (of T_k^-1 T_f),
+//    angle acos((trace(R_k^T R_f) - 1) / 2).
+//  * KF_OVRLP(thr): a new keyframe when the overlap ratio drops below thr.  Reading of
+//    "pixels visible in both": the share of the frame's valid pixels (Z > 0) whose
+//    point, warped into the keyframe, is in front of it (z > 0) and has its nearest
+//    pixel (halves up) inside the keyframe image.
+// For the overlap ratio the oracle also counts the marginal pixels (a rounding or the
+// camera plane within the margins), so that a float32 evaluation can be compared.
+
+namespace {
+
+void overlap_count(const float* depth, const Pose& Tf, const Pose& Tk, const Intr& K, long* valid, long* inside,
+                   long* marginal) {
+    long nv = 0, ni = 0, nm = 0;
+    for (long v = 0; v < K.H; ++v)
+        for (long u = 0; u < K.W; ++u) {
+            const double z = depth[v * K.W + u];
+            if (!(z > 0.0)) continue;
+            ++nv;
+            double P[3], pw[3], pk[3];
+            backproject(K, (double)u, (double)v, z, P);
+            apply(Tf, P, pw);
+            apply_inv(Tk, pw, pk);
+            bool marg = std::fabs(pk[2]) < g_tau_m;
+            if (!(pk[2] > 0.0)) {
+                nm += marg;
+                continue;
+            }
+            double mu_, mv_;
+            const double uf = K.fx * pk[0] / pk[2] + K.cx, vf = K.fy * pk[1] / pk[2] + K.cy;
+            const long xs = round_half_up(uf, &mu_), ys = round_half_up(vf, &mv_);
+            // a marginal rounding matters only where it can move the pixel across the border
+            if ((mu_ < g_tau_px && (xs == 0 || xs == K.W || xs == -1 || xs == K.W - 1)) ||
+                (mv_ < g_tau_px && (ys == 0 || ys == K.H || ys == -1 || ys == K.H - 1)))
+                marg = true;
+            nm += marg;
+            if (xs >= 0 && xs < K.W && ys >= 0 && ys < K.H) ++ni;
+        }
+    *valid = nv;
+    *inside = ni;
+    *marginal = nm;
+}
+
+double rotation_angle(const Pose& A, const Pose& B) {
+    double tr = 0.0;  // trace(R_A^T R_B)
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) tr += A.R[r][c] * B.R[r][c];
+    const double x = std::max(-1.0, std::min(1.0, (tr - 1.0) / 2.0));
+    return std::acos(x);
+}
+
+}  // namespace
+
+extern "C" void or_overlap(const float* depth, const float* frame_pose, const float* kf_pose, double fx, double fy,
+                           double cx, double cy, int W, int H, long* counts /*valid, inside, marginal*/) {
+    const Intr K{fx, fy, cx, cy, W, H};
+    overlap_count(depth, pose_from(frame_pose), pose_from(kf_pose), K, &counts[0], &counts[1], &counts[2]);
+}
+
+// strategy 0 KF_CONST (p0 = kappa), 1 KF_DIST (p0 = thr_t, p1 = thr_r), 2 KF_OVRLP (p0 = thr).
+// frame_kf[f] = group of frame f; flag[f] = 1 where frame f's decision is within the
+// margins (KF_OVRLP: the marginal pixels could move the ratio across thr; KF_DIST: a
+// distance within 1e-6 relative of its threshold).  Returns the number of keyframes.
+extern "C" int or_segment(int strategy, double p0, double p1, const float* depths, const float* poses, int n,
+                          double fx, double fy, double cx, double cy, int W, int H, int32_t* frame_kf, uint8_t* flag) {
+    const Intr K{fx, fy, cx, cy, W, H};
+    if (n <= 0) return 0;
+    int groups = 1, kf = 0;
+    frame_kf[0] = 0;
+    flag[0] = 0;
+    for (int f = 1; f < n; ++f) {
+        bool fresh = false;
+        flag[f] = 0;
+        const Pose Tf = pose_from(poses + 12 * f), Tk = pose_from(poses + 12 * kf);
+        if (strategy == 0) {
+            fresh = (f % (int)p0) == 0;
+        } else if (strategy == 1) {
+            double dt = 0.0;
+            for (int r = 0; r < 3; ++r) dt += (Tf.t[r] - Tk.t[r]) * (Tf.t[r] - Tk.t[r]);
+            dt = std::sqrt(dt);
+            const double dr = rotation_angle(Tk, Tf);
+            fresh = dt > p0 || dr > p1;
+            if (std::fabs(dt - p0) <= 1e-6 * p0 || std::fabs(dr - p1) <= 1e-6 * p1) flag[f] = 1;
+        } else {
+            long nv, ni, nm;
+            overlap_count(depths + (size_t)f * W * H, Tf, Tk, K, &nv, &ni, &nm);
+            const double ratio = nv > 0 ? (double)ni / (double)nv : 0.0;
+            fresh = ratio < p0;
+            if (nv > 0 && std::fabs(ratio - p0) * (double)nv <= (double)nm) flag[f] = 1;
+        }
+        if (fresh) {
+            kf = f;
+            ++groups;
+        }
+        frame_kf[f] = groups - 1;
+    }
+    return groups;
 }
