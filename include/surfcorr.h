@@ -218,6 +218,37 @@ int sc_fuse_colour_keyframes(const uint8_t* rgba, const float* depths, const sc_
                              const sc_colour_params* params, void* workspace, uint64_t workspace_bytes,
                              uint8_t* kf_rgba, float* kf_colour, float* frame_weight, sc_stream stream);
 
+/* ------------------------------------------------- keyframe strategies ---- */
+
+/* Keyframe strategies (Section 4.2). */
+typedef enum {
+    SC_KF_CONST = 0, /* params[0] = kappa: a new keyframe every kappa frames */
+    SC_KF_DIST = 1,  /* params[0] = thr_t (m), params[1] = thr_r (rad): a new keyframe when the
+                        current frame's pose is more than thr_t away from the current keyframe's
+                        (|t_f - t_k|) or rotated by more than thr_r (angle of R_k^T R_f) */
+    SC_KF_OVRLP = 2  /* params[0] = thr in [0, 1]: a new keyframe when the overlap ratio of the
+                        current frame with the current keyframe (sc_overlap_counts) < thr */
+} sc_kf_strategy;
+
+/* Overlap of frames with a keyframe (KF_OVRLP, Section 4.2): for each frame i, counts
+ * (device, out [n][2] uint64) = (valid pixels Z > 0, valid pixels whose point, warped
+ * with pi^-1, the frame pose and the keyframe pose, is in front of the keyframe and
+ * has its nearest pixel (halves up) inside the keyframe image).  The overlap ratio is
+ * counts[i][1] / counts[i][0].  depths device [n][H][W]; poses host.  Asynchronous. */
+int sc_overlap_counts(const float* depths, const sc_pose* frame_poses, int32_t n, const sc_pose* kf_pose,
+                      const sc_intrinsics* intr, uint64_t* counts, sc_stream stream);
+
+/* Group frames 0..n-1 (in order) into keyframes: frame 0 starts the first group, a frame
+ * that meets the strategy's condition against the current keyframe starts the next
+ * group and becomes its keyframe (its pose is the keyframe pose).  frame_kf (host, out
+ * [n]) receives each frame's group, *n_keyframes their number.  depths (device
+ * [n][H][W]) and intr are needed for SC_KF_OVRLP only (otherwise may be NULL).  KF_DIST
+ * distances are computed in double from the float poses; KF_OVRLP ratios from integer
+ * counts.  Synchronises the stream (KF_OVRLP: once per 32 frames evaluated). */
+int sc_segment_keyframes(int32_t strategy, const double* params, const float* depths, const sc_pose* poses,
+                         int32_t n, const sc_intrinsics* intr, int32_t* frame_kf, int32_t* n_keyframes,
+                         sc_stream stream);
+
 /* ------------------------------------------------ integration (plain path) ---- */
 
 /* Integrate keyframe kf_id at pose T (Section 3 "SDF volume": voxel blocks are

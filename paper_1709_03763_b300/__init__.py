@@ -9,4 +9,5 @@ include/surfcorr.h); this package marshals torch tensors into it.
 """
 from ._lib import SurfcorrError, lib  # noqa: F401
 from .volume import (Volume, fuse_colour_keyframes, fuse_frames_into_keyframe, fuse_keyframes, prepare_colour, make_intrinsics, prepare_fuse, make_pose, pose_distance,  # noqa: F401
-                     mc_case, pose_exp_left, select_consecutive, select_topm)
+                     KF_CONST, KF_DIST, KF_OVRLP, mc_case, overlap_counts, pose_exp_left, segment_keyframes,
+                     select_consecutive, select_topm)

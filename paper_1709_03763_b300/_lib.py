@@ -51,6 +51,9 @@ class FusionParams(ctypes.Structure):
     _fields_ = [("disc_rel", c_f)]
 
 
+SC_KF_CONST, SC_KF_DIST, SC_KF_OVRLP = 0, 1, 2
+
+
 class ColourParams(ctypes.Structure):
     _fields_ = [("disc_rel", c_f), ("occl_rel", c_f)]
 
@@ -92,6 +95,8 @@ SIGNATURES = {
     "sc_colour_workspace_bytes": (c_u64, [c_i32, c_i32]),
     "sc_fuse_colour_keyframes": (c_i32, [c_p, c_p, P(Pose), P(c_i32), c_i32, c_p, P(Pose), c_i32, P(Intrinsics),
                                          P(ColourParams), c_p, c_u64, c_p, c_p, c_p, c_p]),
+    "sc_overlap_counts": (c_i32, [c_p, P(Pose), c_i32, P(Pose), P(Intrinsics), c_p, c_p]),
+    "sc_segment_keyframes": (c_i32, [c_i32, P(c_d), c_p, P(Pose), c_i32, P(Intrinsics), P(c_i32), P(c_i32), c_p]),
     "sc_integrate_keyframe": (c_i32, [c_p, c_i32, c_p, c_p, P(Intrinsics), P(Pose), c_p]),
     "sc_deintegrate_keyframe": (c_i32, [c_p, c_i32, c_p, c_p, P(Intrinsics), P(Pose), c_p]),
     "sc_reintegrate_batch": (c_i32, [c_p, P(ReintItem), c_i32, P(Intrinsics), c_p]),

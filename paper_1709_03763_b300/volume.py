@@ -18,7 +18,8 @@ from ._lib import (BatchConfig, ColourParams, FusionParams, Intrinsics, Pose, Pr
 
 __all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
            "prepare_colour", "pose_distance", "select_topm", "select_consecutive",
-           "pose_exp_left", "mc_case", "SurfcorrError", "make_intrinsics", "make_pose"]
+           "pose_exp_left", "mc_case", "overlap_counts", "segment_keyframes", "KF_CONST", "KF_DIST",
+           "KF_OVRLP", "SurfcorrError", "make_intrinsics", "make_pose"]
 
 
 def make_intrinsics(intr) -> Intrinsics:
@@ -447,6 +448,41 @@ def select_consecutive(dist, m: int) -> int:
     if j < 0:
         raise SurfcorrError(j, "sc_select_consecutive")
     return j
+
+
+KF_CONST, KF_DIST, KF_OVRLP = _lib.SC_KF_CONST, _lib.SC_KF_DIST, _lib.SC_KF_OVRLP
+
+
+def overlap_counts(depths: torch.Tensor, frame_poses, kf_pose, intr, out: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+    """KF_OVRLP counts [n,2] int64 (valid pixels, overlapping pixels) of frames against a keyframe."""
+    n = depths.shape[0]
+    if out is None:
+        out = torch.empty((max(n, 1), 2), dtype=torch.int64, device=depths.device)
+    pz = (Pose * max(n, 1))(*[make_pose(p) for p in frame_poses])
+    check(lib().sc_overlap_counts(_dev(depths, torch.float32, "depths"), pz, n, ctypes.byref(make_pose(kf_pose)),
+                                  ctypes.byref(make_intrinsics(intr)), _dev(out, torch.int64, "out"),
+                                  _stream(stream)), "sc_overlap_counts")
+    return out[:n]
+
+
+def segment_keyframes(strategy: int, params, poses, intr=None, depths: torch.Tensor | None = None,
+                      stream=None) -> tuple[np.ndarray, int]:
+    """Keyframe groups of frames in order (KF_CONST: params=(kappa,), KF_DIST: (thr_t, thr_r),
+    KF_OVRLP: (thr,) with depths [n,H,W] on the device).  Returns (frame_kf [n] int32, keyframes)."""
+    n = len(poses)
+    pz = (Pose * max(n, 1))(*[make_pose(p) for p in poses])
+    pr = (ctypes.c_double * 2)(*[float(x) for x in (list(params) + [0.0, 0.0])[:2]])
+    fk = np.zeros(max(n, 1), np.int32)
+    g = ctypes.c_int32(0)
+    dptr = _dev(depths, torch.float32, "depths") if depths is not None else None
+    iptr = ctypes.byref(make_intrinsics(intr)) if intr is not None else None
+    # KF_CONST / KF_DIST run on the host only: no stream needed
+    st = _stream(stream) if (depths is not None or stream is not None) else None
+    check(lib().sc_segment_keyframes(int(strategy), pr, dptr, pz, n, iptr,
+                                     fk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(g), st),
+          "sc_segment_keyframes")
+    return fk[:n], g.value
 
 
 def mc_case(mask: int) -> np.ndarray:
