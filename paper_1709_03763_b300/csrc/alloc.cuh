@@ -3,7 +3,7 @@
 //
 // A(k, T): every 8^3 block whose closed box meets the band segment
 // {pi^-1(x, z) : z in [Z(x) - mu, Z(x) + mu]} of a valid pixel x, in world
-// coordinates.  Computed per 32x8 pixel tile by one CTA:
+// coordinates.  Computed per 32x16 pixel tile by one CTA:
 //   A  enumerate each pixel's candidate blocks (slab test) into a shared-memory
 //      set, which removes the many duplicates neighbouring pixels produce;
 //   B  claim every unique key in the global hash table (64-bit CAS); the tile's
@@ -19,7 +19,7 @@
 namespace sc {
 
 #ifndef SC_ALLOC_TY
-#define SC_ALLOC_TY 8
+#define SC_ALLOC_TY 16
 #endif
 #ifndef SC_ALLOC_WARP_DEDUPE
 #define SC_ALLOC_WARP_DEDUPE 0

@@ -102,7 +102,7 @@ void prof_pair(sc_volume* V, cudaEvent_t a, cudaEvent_t b, int kind) {
 
 namespace {
 
-// Plain path: one CTA per 32x8 pixel tile of one keyframe.
+// Plain path: one CTA per 32x16 pixel tile of one keyframe.
 __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) alloc_kernel(DevVolume V, KfCam k, PlainSink sk) {
     __shared__ AllocShared sh;
     alloc_tile(V, k, blockIdx.x, blockIdx.y, sk, sh);
