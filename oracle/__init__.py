@@ -98,6 +98,8 @@ def _declare(L):
     L.or_overlap.argtypes = [_p, _p, _p, _d, _d, _d, _d, _i, _i, _p]
     L.or_segment.argtypes = [_i, _d, _d, _p, _p, _i, _d, _d, _d, _d, _i, _i, _p, _p]
     L.or_segment.restype = _i
+    L.or_sphere_outside.argtypes = [_p, _l, _d, _p, _d, _p, _p]
+    L.or_sphere_outside.restype = _l
 
 
 def _ptr(a):
@@ -264,6 +266,16 @@ def segment(strategy, params, poses, intr=None, depths=None):
             p0, p1 = f32(p0), f32(p1)
     g = lib().or_segment(int(strategy), p0, p1, _ptr(d), _ptr(p), n, fx, fy, cx, cy, W, H, _ptr(fk), _ptr(fl))
     return fk, fl, g
+
+
+def sphere_outside(coords, voxel_size, centre, radius):
+    """Blocks outside the streaming sphere: (outside [n] bool, marginal [n] bool)."""
+    c = np.ascontiguousarray(coords, np.int32).reshape(-1, 3)
+    o = np.zeros(len(c), np.uint8)
+    m = np.zeros(len(c), np.uint8)
+    ce = np.ascontiguousarray(np.asarray(centre, np.float32).astype(np.float64))
+    lib().or_sphere_outside(_ptr(c), len(c), f32(voxel_size), _ptr(ce), f32(radius), _ptr(o), _ptr(m))
+    return o.astype(bool), m.astype(bool)
 
 
 def allocation_set(depth, pose, intr, voxel_size, trunc):

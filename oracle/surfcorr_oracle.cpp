@@ -1651,3 +1651,31 @@ extern "C" int or_segment(int strategy, double p0, double p1, const float* depth
     }
     return groups;
 }
+
+// ============================================================================
+// Streaming sphere (Section 3 "SDF volume"; Section 4.3 streaming order)
+// ============================================================================
+//
+// Only voxel blocks within a sphere of constant radius around the camera stay in
+// GPU memory.  Reading: a block is inside when its centre, the centre of its 8^3
+// voxels ((8 b + 3.5) * voxel_size per axis), lies within radius of the camera
+// position (distance <= radius).  out[b] = 1 for blocks outside; marg[b] = 1 where
+// the distance is within 1e-6 m of the radius (a float32 evaluation may decide
+// otherwise).  Streaming itself changes no voxel value; the tests check that
+// invariance against the unstreamed volume.
+extern "C" long or_sphere_outside(const int32_t* coords, long n, double voxel_size, const double* centre,
+                                  double radius, uint8_t* out, uint8_t* marg) {
+    long count = 0;
+    for (long b = 0; b < n; ++b) {
+        double d2 = 0.0;
+        for (int r = 0; r < 3; ++r) {
+            const double c = (8.0 * coords[3 * b + r] + 3.5) * voxel_size - centre[r];
+            d2 += c * c;
+        }
+        const double d = std::sqrt(d2);
+        out[b] = d > radius;
+        marg[b] = std::fabs(d - radius) <= 1e-6;
+        count += out[b];
+    }
+    return count;
+}
