@@ -59,7 +59,9 @@ typedef enum {
     SC_ERR_NOT_INTEGRATED = -6,     /* de-integrating a keyframe id that is not integrated */
     SC_ERR_CAPACITY = -7,           /* output buffer too small (count still reported) */
     SC_ERR_ALREADY_INTEGRATED = -8, /* integrating a keyframe id that is integrated */
-    SC_ERR_LIST_FULL = -9           /* a keyframe touched more blocks than its list holds */
+    SC_ERR_LIST_FULL = -9,          /* a keyframe touched more blocks than its list holds */
+    SC_ERR_NOT_RESIDENT = -10,      /* a keyframe's block is in the host block store, not on the GPU */
+    SC_ERR_CONFLICT = -11           /* a block streamed in is already resident on the GPU */
 } sc_status;
 
 typedef enum { SC_RGBA8 = 0, SC_RGB_F32 = 1 } sc_colour_format;
@@ -366,6 +368,44 @@ int sc_mc_case(int32_t mask, int32_t* edges);
  * / SC_ERR_POOL_FULL when the volume is full.  Synchronises the stream. */
 int sc_import_blocks(sc_volume* vol, const int32_t* coords, const float* D, const float* W, const void* C,
                      int32_t n, sc_stream stream);
+
+/* -------------------------------------------------- the streaming sphere ---- */
+
+/* Host block store of the streaming sphere (Section 3 "SDF volume": only blocks within
+ * a sphere of constant radius around the camera stay in GPU memory; the others are
+ * streamed to the host).  Pinned, device-mapped host memory for `capacity` blocks
+ * (12 KB each in RGBA8, 20 KB in RGB_F32) on the current device; colour_format must
+ * match the volumes it serves. */
+typedef struct sc_block_store sc_block_store;
+int sc_create_block_store(int64_t capacity, int32_t colour_format, sc_block_store** out);
+int sc_destroy_block_store(sc_block_store* store);
+/* Blocks held by the store (-1 for NULL). */
+int64_t sc_block_store_count(const sc_block_store* store);
+
+/* Stream out: every resident block whose centre ((8 b + 3.5) * voxel_size per axis) is
+ * farther than `radius` from `centre` (host float[3], metres; distance compared
+ * squared in float) moves into the store with its D, W, C and initialisation flag.
+ * The pool is compacted (the remaining blocks keep their data, some change slot), the
+ * hash table is rebuilt, and keyframe block lists keep naming every block of their
+ * A(k, T): resident blocks by slot, stored ones by an external id.  De-integrating,
+ * re-integrating (sc_reintegrate_batch) or differentiating (sc_sdf_adjoint) a
+ * keyframe whose list names a stored block returns SC_ERR_NOT_RESIDENT before any
+ * launch; stream those blocks in first.  Integrating a new keyframe over a region
+ * whose blocks are stored allocates fresh blocks there and makes their later
+ * stream-in fail with SC_ERR_CONFLICT, so stream a region in before integrating
+ * into it (the paper streams the sphere around the camera before each
+ * integration).  *n_moved (host) = blocks moved.  SC_ERR_CAPACITY if the store
+ * cannot take them (nothing moves).  Synchronises the stream. */
+int sc_stream_out(sc_volume* vol, sc_block_store* store, const float* centre, float radius, int64_t* n_moved,
+                  sc_stream stream);
+
+/* Stream in: every stored block whose centre is within `radius` of `centre` (the same
+ * test) returns to the GPU at a new pool slot, and list entries naming it become its
+ * slot.  A stored block whose coordinate has been allocated on the GPU meanwhile
+ * stays stored and the call returns SC_ERR_CONFLICT (stream in before integrating
+ * into a region).  radius = +inf streams in everything.  Synchronises the stream. */
+int sc_stream_in(sc_volume* vol, sc_block_store* store, const float* centre, float radius, int64_t* n_moved,
+                 sc_stream stream);
 
 /* --------------------------------------------- loss and adjoint (extension) ---- */
 

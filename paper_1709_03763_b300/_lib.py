@@ -29,6 +29,8 @@ SC_ERR_NOT_INTEGRATED = -6
 SC_ERR_CAPACITY = -7
 SC_ERR_ALREADY_INTEGRATED = -8
 SC_ERR_LIST_FULL = -9
+SC_ERR_NOT_RESIDENT = -10
+SC_ERR_CONFLICT = -11
 SC_RGBA8 = 0
 SC_RGB_F32 = 1
 
@@ -108,6 +110,11 @@ SIGNATURES = {
     "sc_marching_cubes": (c_i32, [c_p, c_p, c_p, c_i64, P(c_i64), c_p]),
     "sc_mc_case": (c_i32, [c_i32, P(c_i32)]),
     "sc_import_blocks": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i32, c_p]),
+    "sc_create_block_store": (c_i32, [c_i64, c_i32, P(c_p)]),
+    "sc_destroy_block_store": (c_i32, [c_p]),
+    "sc_block_store_count": (c_i64, [c_p]),
+    "sc_stream_out": (c_i32, [c_p, c_p, P(c_f), c_f, P(c_i64), c_p]),
+    "sc_stream_in": (c_i32, [c_p, c_p, P(c_f), c_f, P(c_i64), c_p]),
     "sc_get_keyframe_blocks": (c_i32, [c_p, c_i32, c_p, c_i32, P(c_i32), c_p]),
     "sc_sdf_loss": (c_i32, [c_p, c_p, c_i64, c_f, c_p, c_p, c_p]),
     "sc_sdf_adjoint": (c_i32, [c_p, P(c_i32), P(c_p), P(Pose), c_i32, P(Intrinsics), c_p, c_p, c_p, c_p]),

@@ -116,8 +116,12 @@ __global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const
             int32_t slot = -1;
             if (j < cnt) {
                 slot = list[j];
-                atomicOr(masks + (size_t)slot * mw + (i >> 5), bit);
-                first = atomicExch(&V.stamp[slot], call_id) != call_id;
+                if (slot >= 0) {
+                    atomicOr(masks + (size_t)slot * mw + (i >> 5), bit);
+                    first = atomicExch(&V.stamp[slot], call_id) != call_id;
+                } else {
+                    set_status(V.status, SC_ERR_NOT_RESIDENT);  // streamed out to the host
+                }
             }
             const unsigned m = __ballot_sync(0xffffffffu, first);
             if (!m) continue;
@@ -556,6 +560,7 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         if (!it.newp || !pose_finite(it.newp) || (it.oldp && !pose_finite(it.oldp))) return SC_ERR_INVALID_ARG;
         seen[it.kf_id] = 1;
         if (it.oldp && !V->integrated[it.kf_id]) return SC_ERR_NOT_INTEGRATED;
+        if (it.oldp && V->nonresident[it.kf_id]) return SC_ERR_NOT_RESIDENT;
         if (!it.oldp && V->integrated[it.kf_id]) return SC_ERR_ALREADY_INTEGRATED;
     }
     int rc = batch_init(V);

@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
     double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
     for (uint32_t b = blockIdx.x * (ADJ_THREADS / 32) + warp; b < cnt; b += nw) {
         const int32_t slot = it.list[b];
+        if (slot < 0) {  // streamed out to the host block store
+            if (lane == 0) set_status(V.status, SC_ERR_NOT_RESIDENT);
+            continue;
+        }
         const int4 c = V.coord[slot];
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll 1
@@ -333,6 +337,7 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
     for (int i = 0; i < n; ++i) {
         if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes || !depths[i]) return SC_ERR_INVALID_ARG;
         if (!V->integrated[kf_ids[i]]) return SC_ERR_NOT_INTEGRATED;
+        if (V->nonresident[kf_ids[i]]) return SC_ERR_NOT_RESIDENT;
     }
     cudaStream_t s = (cudaStream_t)stream;
     int rc = adj_reserve(V->device, n);
@@ -403,6 +408,7 @@ extern "C" int sc_sdf_adjoint_noalloc(sc_volume* V, const int32_t* kf_ids, const
     for (int i = 0; i < n; ++i) {
         if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes || !depths[i]) return SC_ERR_INVALID_ARG;
         if (!V->integrated[kf_ids[i]]) return SC_ERR_NOT_INTEGRATED;
+        if (V->nonresident[kf_ids[i]]) return SC_ERR_NOT_RESIDENT;
     }
     int dev = 0;
     SC_CUDA(cudaGetDevice(&dev));

@@ -125,6 +125,10 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam 
     const int lx0 = (4 * t) & 7, ly = ((4 * t) >> 3) & 7, lz = (4 * t) >> 6;
     for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
         const int32_t slot = list[i];
+        if (slot < 0) {  // streamed out to the host block store
+            if (t == 0) set_status(V.status, SC_ERR_NOT_RESIDENT);
+            continue;
+        }
         const int4 c = V.coord[slot];
         bool fresh = false;
         if (SIGN > 0) {
@@ -340,6 +344,8 @@ extern "C" const char* sc_status_string(int s) {
         case SC_ERR_CAPACITY: return "output capacity too small";
         case SC_ERR_ALREADY_INTEGRATED: return "keyframe already integrated";
         case SC_ERR_LIST_FULL: return "keyframe block list full";
+        case SC_ERR_NOT_RESIDENT: return "keyframe block not resident (stream it in first)";
+        case SC_ERR_CONFLICT: return "streamed-in block already resident";
         default: return "unknown status";
     }
 }
@@ -358,6 +364,7 @@ extern "C" int sc_create_volume(const sc_volume_params* p, sc_volume** out) {
     V->p = *p;
     V->integrated.assign(p->max_keyframes, 0);
     V->cur.assign(p->max_keyframes, 0);
+    V->nonresident.assign(p->max_keyframes, 0);
     V->call_id = 0;
     V->last_stream = nullptr;
     V->batch = nullptr;
@@ -463,6 +470,7 @@ extern "C" int sc_reset_volume(sc_volume* V, sc_stream stream) {
     SC_CUDA(cudaMemsetAsync(V->pool_count, 0, sizeof(uint32_t), s));
     SC_CUDA(cudaMemsetAsync(V->status, 0, sizeof(int32_t), s));
     SC_CUDA(cudaMemsetAsync(V->list_counts, 0, (size_t)V->p.max_keyframes * 2 * sizeof(int32_t), s));
+    std::fill(V->nonresident.begin(), V->nonresident.end(), 0);
     // pool slots are handed out again from 0: mark them fresh lazily via the allocator,
     // and forget the per-call stamps
     SC_CUDA(cudaMemsetAsync(V->stamp, 0, (size_t)V->p.max_blocks * sizeof(uint32_t), s));
@@ -547,6 +555,7 @@ extern "C" int sc_deintegrate_keyframe(sc_volume* V, int32_t kf_id, const float*
     int rc = check_kf_args(V, kf_id, depth, rgba, K, T);
     if (rc) return rc;
     if (!V->integrated[kf_id]) return SC_ERR_NOT_INTEGRATED;
+    if (V->nonresident[kf_id]) return SC_ERR_NOT_RESIDENT;
     cudaStream_t s = (cudaStream_t)stream;
     const KfCam cam = make_cam(V, K, T, depth, rgba);
     const int which = V->cur[kf_id];

@@ -30,6 +30,7 @@ struct sc_volume {
     // host mirrors
     std::vector<uint8_t> integrated;
     std::vector<uint8_t> cur;  // which of the two list buffers holds the current list
+    std::vector<uint8_t> nonresident;  // the current list names a block in a host block store
     uint32_t call_id;
     cudaStream_t last_stream;
     int32_t* h_status;  // pinned

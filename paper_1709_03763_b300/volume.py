@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (BatchConfig, ColourParams, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
                    VolumeParams, check, lib)
 
-__all__ = ["Volume", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
+__all__ = ["Volume", "BlockStore", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
            "prepare_colour", "pose_distance", "select_topm", "select_consecutive",
            "pose_exp_left", "mc_case", "overlap_counts", "segment_keyframes", "KF_CONST", "KF_DIST",
            "KF_OVRLP", "SurfcorrError", "make_intrinsics", "make_pose"]
@@ -262,6 +262,24 @@ class Volume:
         t = n.value
         return (out[:t], cb[:t]) if cubes else out[:t]
 
+    def stream_out(self, store: "BlockStore", centre, radius: float, stream=None) -> int:
+        """Move the blocks whose centre is farther than radius from centre into the host
+        store; returns the number moved."""
+        c = (ctypes.c_float * 3)(*[float(x) for x in np.asarray(centre).reshape(3)])
+        n = ctypes.c_int64(0)
+        check(lib().sc_stream_out(self.h, store.h, c, float(radius), ctypes.byref(n), _stream(stream)),
+              "sc_stream_out")
+        return n.value
+
+    def stream_in(self, store: "BlockStore", centre, radius: float = float("inf"), stream=None) -> int:
+        """Move the stored blocks whose centre is within radius of centre back to the GPU;
+        returns the number moved."""
+        c = (ctypes.c_float * 3)(*[float(x) for x in np.asarray(centre).reshape(3)])
+        n = ctypes.c_int64(0)
+        check(lib().sc_stream_in(self.h, store.h, c, float(radius), ctypes.byref(n), _stream(stream)),
+              "sc_stream_in")
+        return n.value
+
     def keyframe_blocks(self, kf_id: int, stream=None) -> torch.Tensor:
         """Pool slots of kf_id's stored block list (its allocation set A(k, T))."""
         n = ctypes.c_int32(0)
@@ -483,6 +501,29 @@ def segment_keyframes(strategy: int, params, poses, intr=None, depths: torch.Ten
                                      fk.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(g), st),
           "sc_segment_keyframes")
     return fk[:n], g.value
+
+
+class BlockStore:
+    """Host block store of the streaming sphere (pinned, device-mapped memory)."""
+
+    def __init__(self, capacity: int, colour: str = "rgba8"):
+        self.h = ctypes.c_void_p()
+        check(lib().sc_create_block_store(int(capacity), _lib.SC_RGB_F32 if colour == "f32" else _lib.SC_RGBA8,
+                                          ctypes.byref(self.h)), "sc_create_block_store")
+
+    def __len__(self) -> int:
+        return int(lib().sc_block_store_count(self.h))
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sc_destroy_block_store(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mc_case(mask: int) -> np.ndarray:
