@@ -407,6 +407,14 @@ int sc_stream_out(sc_volume* vol, sc_block_store* store, const float* centre, fl
 int sc_stream_in(sc_volume* vol, sc_block_store* store, const float* centre, float radius, int64_t* n_moved,
                  sc_stream stream);
 
+/* Stream in exactly the stored blocks that the current block lists of keyframes
+ * kf_ids (host [n]) name, so that those keyframes can be de-/re-integrated (the
+ * paper streams in the sphere around T_j* "to safely access them"; this streams the
+ * blocks the keyframes need, each once).  Same rules and errors as sc_stream_in.
+ * Synchronises the stream. */
+int sc_stream_in_keyframes(sc_volume* vol, sc_block_store* store, const int32_t* kf_ids, int32_t n,
+                           int64_t* n_moved, sc_stream stream);
+
 /* --------------------------------------------- loss and adjoint (extension) ---- */
 
 /* Loss on the fused SDF (no counterpart in the paper):

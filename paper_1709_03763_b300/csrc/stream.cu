@@ -39,6 +39,9 @@ struct sc_block_store {
     int32_t* slot_out;  // [cap] staging: the pool slot each streamed-in entry got, or -1
     // device
     int32_t* ext2slot;  // [cap] store entry -> new pool slot during a stream-in, else -1
+    uint32_t* mark;     // [cap] store entries named by the keyframes of one stream-in (0 between calls)
+    int32_t* dlist;     // [cap] device list of those entries
+    int32_t* dcount;    // [1]
     // host bookkeeping
     std::vector<int32_t> free_ids;
     std::vector<uint8_t> used;
@@ -249,6 +252,26 @@ __global__ void list_flags_kernel(const int32_t* lists, const int32_t* counts, i
     }
 }
 
+// the store entries named (as -(e + 2)) by the given lists, each once
+struct KfLists {
+    const int32_t* list[64];
+    const int32_t* count[64];
+};
+__global__ void collect_ext_kernel(KfLists L, int n_lists, uint32_t cap, uint32_t* mark, int32_t* out,
+                                   int32_t* count) {
+    for (int l = blockIdx.y; l < n_lists; l += gridDim.y) {
+        const uint32_t m = min((uint32_t)*L.count[l], cap);
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+            const int32_t e = L.list[l][i];
+            if (e <= -2 && atomicExch(&mark[-e - 2], 1u) == 0u) out[atomicAdd(count, 1)] = -e - 2;
+        }
+    }
+}
+
+__global__ void unmark_kernel(const int32_t* ext, int32_t k, uint32_t* mark) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) mark[ext[i]] = 0u;
+}
+
 __global__ void reset_ext2slot_kernel(const int32_t* ext, int32_t k, int32_t* ext2slot) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) ext2slot[ext[i]] = -1;
 }
@@ -309,6 +332,10 @@ extern "C" int sc_create_block_store(int64_t capacity, int32_t colour_format, sc
     if (e == cudaSuccess) e = halloc((void**)&S->slot_out, cap * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&S->ext2slot, cap * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(S->ext2slot, 0xff, cap * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S->mark, cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(S->mark, 0, cap * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S->dlist, cap * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S->dcount, sizeof(int32_t));
     if (e != cudaSuccess) {
         sc_destroy_block_store(S);
         return cuda_status(e);
@@ -332,6 +359,9 @@ extern "C" int sc_destroy_block_store(sc_block_store* S) {
     if (S->ext) cudaFreeHost(S->ext);
     if (S->slot_out) cudaFreeHost(S->slot_out);
     if (S->ext2slot) cudaFree(S->ext2slot);
+    if (S->mark) cudaFree(S->mark);
+    if (S->dlist) cudaFree(S->dlist);
+    if (S->dcount) cudaFree(S->dcount);
     delete S;
     return SC_OK;
 }
@@ -411,24 +441,11 @@ extern "C" int sc_stream_out(sc_volume* V, sc_block_store* S, const float* centr
     return rc ? rc : st;
 }
 
-extern "C" int sc_stream_in(sc_volume* V, sc_block_store* S, const float* centre, float radius, int64_t* n_moved,
-                            sc_stream stream) {
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!V || !S || !centre || !(radius >= 0.f) || !n_moved) return SC_ERR_INVALID_ARG;
-    if (!std::isfinite(centre[0]) || !std::isfinite(centre[1]) || !std::isfinite(centre[2])) return SC_ERR_INVALID_ARG;
-    if (S->colour_f32 != (V->p.colour_format == SC_RGB_F32) || S->device != V->device) return SC_ERR_INVALID_ARG;
-    SC_CUDA(cudaSetDevice(V->device));
-    *n_moved = 0;
-    SC_CUDA(cudaStreamSynchronize(s));  // the store's entries are final on the host
-    const float r2 = std::isinf(radius) ? INFINITY : radius * radius;
-    int32_t k = 0;
-    for (int64_t e = 0; e < S->capacity; ++e) {
-        if (!S->used[e]) continue;
-        const int4 c = S->coord[e];
-        if (!outside_sphere(c.x, c.y, c.z, V->p.voxel_size, centre[0], centre[1], centre[2], r2))
-            S->ext[k++] = (int32_t)e;
-    }
-    if (k == 0) return read_status(V, s);
+namespace {
+
+// Stream in the store entries S->ext[0..k) (k > 0), then update lists, residency
+// flags and the store's bookkeeping.
+int stream_in_entries(sc_volume* V, sc_block_store* S, int32_t k, int64_t* n_moved, cudaStream_t s) {
     const int wgrid = std::min((k + 7) / 8, V->num_sms * 16);
     si_copy_in_kernel<<<wgrid, 256, 0, s>>>(V->dv, S->ext, k, S->coord, S->flags, S->D, S->W, S->C, S->ext2slot,
                                             S->slot_out);
@@ -453,4 +470,67 @@ extern "C" int sc_stream_in(sc_volume* V, sc_block_store* S, const float* centre
     S->count -= moved;
     *n_moved = moved;
     return st;
+}
+
+bool stream_args_ok(sc_volume* V, sc_block_store* S) {
+    return V && S && S->colour_f32 == (V->p.colour_format == SC_RGB_F32) && S->device == V->device;
+}
+
+}  // namespace
+
+extern "C" int sc_stream_in(sc_volume* V, sc_block_store* S, const float* centre, float radius, int64_t* n_moved,
+                            sc_stream stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!stream_args_ok(V, S) || !centre || !(radius >= 0.f) || !n_moved) return SC_ERR_INVALID_ARG;
+    if (!std::isfinite(centre[0]) || !std::isfinite(centre[1]) || !std::isfinite(centre[2])) return SC_ERR_INVALID_ARG;
+    SC_CUDA(cudaSetDevice(V->device));
+    *n_moved = 0;
+    SC_CUDA(cudaStreamSynchronize(s));  // the store's entries are final on the host
+    const float r2 = std::isinf(radius) ? INFINITY : radius * radius;
+    int32_t k = 0;
+    for (int64_t e = 0; e < S->capacity; ++e) {
+        if (!S->used[e]) continue;
+        const int4 c = S->coord[e];
+        if (!outside_sphere(c.x, c.y, c.z, V->p.voxel_size, centre[0], centre[1], centre[2], r2))
+            S->ext[k++] = (int32_t)e;
+    }
+    if (k == 0) return read_status(V, s);
+    return stream_in_entries(V, S, k, n_moved, s);
+}
+
+extern "C" int sc_stream_in_keyframes(sc_volume* V, sc_block_store* S, const int32_t* kf_ids, int32_t n,
+                                      int64_t* n_moved, sc_stream stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!stream_args_ok(V, S) || !kf_ids || n < 0 || !n_moved) return SC_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes) return SC_ERR_INVALID_ARG;
+    SC_CUDA(cudaSetDevice(V->device));
+    *n_moved = 0;
+    SC_CUDA(cudaMemsetAsync(S->dcount, 0, sizeof(int32_t), s));
+    for (int i0 = 0; i0 < n; i0 += 64) {
+        KfLists L;
+        int m = 0;
+        for (int i = i0; i < n && i < i0 + 64; ++i) {
+            const int kf = kf_ids[i];
+            if (!V->integrated[kf] || !V->nonresident[kf]) continue;
+            L.list[m] = list_ptr(V, kf, V->cur[kf]);
+            L.count[m] = count_ptr(V, kf, V->cur[kf]);
+            ++m;
+        }
+        if (m == 0) continue;
+        const dim3 grid(std::max(1, std::min(64, (int)((V->p.max_blocks_per_keyframe + 255) / 256))), m);
+        collect_ext_kernel<<<grid, 256, 0, s>>>(L, m, V->p.max_blocks_per_keyframe, S->mark, S->dlist, S->dcount);
+        count_launches(1);
+        SC_CUDA(cudaGetLastError());
+    }
+    int32_t k = 0;
+    SC_CUDA(cudaMemcpyAsync(&k, S->dcount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    if (k == 0) return read_status(V, s);
+    SC_CUDA(cudaMemcpyAsync(S->ext, S->dlist, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    unmark_kernel<<<std::min((k + 255) / 256, 1024), 256, 0, s>>>(S->dlist, k, S->mark);
+    count_launches(1);
+    SC_CUDA(cudaGetLastError());
+    SC_CUDA(cudaStreamSynchronize(s));
+    return stream_in_entries(V, S, k, n_moved, s);
 }

@@ -280,6 +280,14 @@ class Volume:
               "sc_stream_in")
         return n.value
 
+    def stream_in_keyframes(self, store: "BlockStore", kf_ids, stream=None) -> int:
+        """Move the stored blocks that the keyframes' block lists name back to the GPU."""
+        ids = (ctypes.c_int32 * max(len(kf_ids), 1))(*[int(k) for k in kf_ids])
+        n = ctypes.c_int64(0)
+        check(lib().sc_stream_in_keyframes(self.h, store.h, ids, len(kf_ids), ctypes.byref(n), _stream(stream)),
+              "sc_stream_in_keyframes")
+        return n.value
+
     def keyframe_blocks(self, kf_id: int, stream=None) -> torch.Tensor:
         """Pool slots of kf_id's stored block list (its allocation set A(k, T))."""
         n = ctypes.c_int32(0)

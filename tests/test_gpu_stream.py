@@ -79,11 +79,14 @@ def test_deintegration_across_streaming_equals_unstreamed_and_oracle():
         V.deintegrate(2, w.kf_depth[2].cuda(), w.kf_rgba[2].cuda(), w.intr, w.kf_poses[2])
     assert e.value.code == _lib.SC_ERR_NOT_RESIDENT
     _same(_by_key(V.extract()), snap)
-    # stream it in (the sphere around its own camera, then the rest), de-integrate
-    V.stream_in(S, _camera(w.kf_poses[2]), 1.0)
-    V.stream_in(S, _camera(w.kf_poses[2]))
+    # stream in exactly the blocks keyframe 2 needs, de-integrate it, then the rest
+    stored = len(S)
+    n2 = V.stream_in_keyframes(S, [2])
+    assert 0 < n2 <= stored and len(S) == stored - n2
+    assert V.stream_in_keyframes(S, [2]) == 0  # nothing left to bring in for it
     for vol in (V, R):
         vol.deintegrate(2, w.kf_depth[2].cuda(), w.kf_rgba[2].cuda(), w.intr, w.kf_poses[2])
+    V.stream_in(S, _camera(w.kf_poses[2]))
     O.deintegrate(2, w.kf_depth[2], w.kf_rgba[2], it, w.kf_poses[2])
     _same(_by_key(V.extract()), _by_key(R.extract()))
     compare_volumes(V.extract(), O.export())
