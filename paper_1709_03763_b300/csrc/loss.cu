@@ -3,9 +3,10 @@
 //
 //   L = (1/P) sum_p Dt(p)^2 + lambda * sum_v W D^2 / sum_v W
 //
-// Forward: two passes over the points (count + sum of Dt^2, then the scatter of
-// dL/dD once P is known) and one pass over the pool for the weighted
-// regulariser.  Adjoint: D(v) = sum_k w_k d_k(v) / W(v), so for each keyframe the
+// Forward: one pass over the pool for the weighted regulariser's sums (which also
+// zeroes the gradient), one pass over the points (count, sum of Dt^2 and the scatter
+// of the unscaled point gradient 2 Dt beta), and one pass over the pool that scales
+// the point gradient by 1/P once P is known and adds the regulariser's gradient.  Adjoint: D(v) = sum_k w_k d_k(v) / W(v), so for each keyframe the
 // kernel walks its block list, recomputes each voxel's projective sample exactly
 // as the integration did (same sample function, same camera constants) and
 // accumulates g = dL/dD(v) / W(v) for unclamped samples into the depth-pixel
@@ -75,8 +76,8 @@ __device__ inline bool point_corners(const DevVolume& V, float s, const float* p
     return true;
 }
 
-// out[1] += P, out[2] += sum Dt^2
-__global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64_t n, double* out) {
+// out[1] += P, out[2] += sum Dt^2, grad += 2 Dt beta (scaled by 1/P later)
+__global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64_t n, double* out, float* grad) {
     __shared__ double sh[2][LOSS_THREADS / 32];
     double a = 0.0, cnt = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -85,6 +86,9 @@ __global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64
         if (point_corners(V, s, pts + 3 * i, c, Dt)) {
             a += (double)Dt * Dt;
             cnt += 1.0;
+            const float g = 2.f * Dt;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) atomicAdd(grad + c.vox[k], g * c.beta[k]);
         }
     }
     a = warp_sum(a);
@@ -106,14 +110,15 @@ __global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64
     }
 }
 
-// out[3] += sum W D^2, out[4] += sum W over pool slots [0, used)
-__global__ void loss_reg_kernel(DevVolume V, double* out) {
+// out[3] += sum W D^2, out[4] += sum W over pool slots [0, used); grad = 0 there
+__global__ void loss_reg_kernel(DevVolume V, double* out, float* grad) {
     __shared__ double sh[2][LOSS_THREADS / 32];
     const size_t nv = (size_t)min(*V.pool_count, V.max_blocks) * NVOX;
     double a = 0.0, b = 0.0;
     for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < nv; i += (size_t)gridDim.x * blockDim.x * 4) {
         const float4 W = *reinterpret_cast<const float4*>(V.W + i);
         const float4 D = *reinterpret_cast<const float4*>(V.D + i);
+        *reinterpret_cast<float4*>(grad + i) = make_float4(0.f, 0.f, 0.f, 0.f);
         float pa = 0.f, pb = 0.f;
         if (W.x > 0.f) { pa = fmaf(W.x * D.x, D.x, pa); pb += W.x; }
         if (W.y > 0.f) { pa = fmaf(W.y * D.y, D.y, pa); pb += W.y; }
@@ -141,30 +146,22 @@ __global__ void loss_reg_kernel(DevVolume V, double* out) {
     }
 }
 
-// grad_D = 2 lambda W D / sum W (0 where W = 0), pool slots [0, used)
-__global__ void loss_grad_init_kernel(DevVolume V, float lambda, const double* out, float* grad) {
+// grad_D = grad_D / P + 2 lambda W D / sum W (the regulariser's part 0 where W = 0),
+// pool slots [0, used); the point part is zero wherever W = 0
+__global__ void loss_grad_combine_kernel(DevVolume V, float lambda, const double* out, float* grad) {
     const size_t nv = (size_t)min(*V.pool_count, V.max_blocks) * NVOX;
-    const double sw = out[4];
+    const double P = out[1], sw = out[4];
+    const float inv_p = P > 0.0 ? (float)(1.0 / P) : 0.f;
     const float scale = sw > 0.0 ? (float)(2.0 * lambda / sw) : 0.f;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nv; i += (size_t)gridDim.x * blockDim.x) {
-        const float W = V.W[i];
-        grad[i] = W > 0.f ? scale * W * V.D[i] : 0.f;
-    }
-}
-
-// grad_D += (2/P) Dt beta
-__global__ void loss_points_grad_kernel(DevVolume V, float s, const float* pts, int64_t n, const double* out,
-                                        float* grad) {
-    const double P = out[1];
-    if (!(P > 0.0)) return;
-    const float sc2 = (float)(2.0 / P);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        Corners c;
-        float Dt;
-        if (!point_corners(V, s, pts + 3 * i, c, Dt)) continue;
-        const float g = sc2 * Dt;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) atomicAdd(grad + c.vox[k], g * c.beta[k]);
+    for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < nv; i += (size_t)gridDim.x * blockDim.x * 4) {
+        const float4 W = *reinterpret_cast<const float4*>(V.W + i);
+        const float4 D = *reinterpret_cast<const float4*>(V.D + i);
+        float4 g = *reinterpret_cast<const float4*>(grad + i);
+        g.x = g.x * inv_p + (W.x > 0.f ? scale * W.x * D.x : 0.f);
+        g.y = g.y * inv_p + (W.y > 0.f ? scale * W.y * D.y : 0.f);
+        g.z = g.z * inv_p + (W.z > 0.f ? scale * W.z * D.z : 0.f);
+        g.w = g.w * inv_p + (W.w > 0.f ? scale * W.w * D.w : 0.f);
+        *reinterpret_cast<float4*>(grad + i) = g;
     }
 }
 
@@ -190,7 +187,10 @@ struct AdjItem {
 // the warp and CTA reductions double, one set of 4 atomics per CTA.
 constexpr int ADJ_THREADS = 256;
 
-__global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const AdjItem* items, uint32_t cap,
+#ifndef SC_ADJ_MIN_BLOCKS
+#define SC_ADJ_MIN_BLOCKS 1  // resident CTAs per SM the register budget must allow
+#endif
+__global__ void __launch_bounds__(ADJ_THREADS, SC_ADJ_MIN_BLOCKS) adjoint_kernel(DevVolume V, const AdjItem* items, uint32_t cap,
                                                               const float* grad, double* acc) {
     __shared__ double sh[ADJ_THREADS / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -216,6 +216,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
             lane_voxels(lane, g, lx0, ly, lz);
             const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
             const int iy = 8 * c.y + ly, iz = 8 * c.z + lz;
+            // the lane's 4 voxels are contiguous: one 16-byte load each of dL/dD and W,
+            // issued before the projection so that their latency overlaps it
+            const float4 g4 = __ldg(reinterpret_cast<const float4*>(grad + off));
+            const float4 w4 = __ldg(reinterpret_cast<const float4*>(V.W + off));
+            const float gj[4] = {g4.x, g4.y, g4.z, g4.w}, wj[4] = {w4.x, w4.y, w4.z, w4.w};
             Proj4 P;
             project4(cam, (float)(8 * c.x + lx0), (float)iy, (float)iz, P);
             float Z[4];
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) adjoint_kernel(DevVolume V, const
                 const int ix = 8 * c.x + lx0 + j;
                 if (!decide(cam, P.ok[j], Z[j], P.pz[j], d, eta)) continue;
                 if (!(eta < cam.mu)) continue;  // clamped: no derivative
-                const float gv = __fdiv_rn(grad[off + j], V.W[off + j]);
+                const float gv = __fdiv_rn(gj[j], wj[j]);
                 if (gv == 0.f) continue;
                 if (it.grad_depth) atomicAdd(it.grad_depth + pix, gv);
                 a0 += gv;
@@ -318,12 +323,11 @@ extern "C" int sc_sdf_loss(sc_volume* V, const float* points, int64_t n, float l
     const float vs = V->p.voxel_size;
     SC_CUDA(cudaMemsetAsync(out, 0, 5 * sizeof(double), s));
     const int grid = V->num_sms * 8;
-    if (n > 0) loss_points_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, points, n, out);
-    loss_reg_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, out);
-    loss_grad_init_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, lambda, out, grad_D);
-    if (n > 0) loss_points_grad_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, points, n, out, grad_D);
+    loss_reg_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, out, grad_D);
+    if (n > 0) loss_points_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, points, n, out, grad_D);
+    loss_grad_combine_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, lambda, out, grad_D);
     loss_finalize_kernel<<<1, 1, 0, s>>>(lambda, out);
-    count_launches(n > 0 ? 5 : 3);
+    count_launches(n > 0 ? 4 : 3);
     SC_CUDA(cudaGetLastError());
     V->last_stream = s;
     return SC_OK;
@@ -332,7 +336,8 @@ extern "C" int sc_sdf_loss(sc_volume* V, const float* points, int64_t n, float l
 extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
                               int32_t n, const sc_intrinsics* K, const float* grad_D, double* grad_xi,
                               float* grad_depth, sc_stream stream) {
-    if (!V || !kf_ids || !depths || !poses || n < 1 || n > 65535 || !intrinsics_ok(K) || !grad_D || !grad_xi)
+    if (!V || !kf_ids || !depths || !poses || n < 1 || n > 65535 || !intrinsics_ok(K) || !grad_D || !grad_xi ||
+        ((uintptr_t)grad_D & 15))
         return SC_ERR_INVALID_ARG;
     for (int i = 0; i < n; ++i) {
         if (kf_ids[i] < 0 || kf_ids[i] >= V->p.max_keyframes || !depths[i]) return SC_ERR_INVALID_ARG;
@@ -402,7 +407,8 @@ static __device__ __align__(256) unsigned char g_adj_static[sizeof(AdjStatic)];
 extern "C" int sc_sdf_adjoint_noalloc(sc_volume* V, const int32_t* kf_ids, const float* const* depths,
                                       const sc_pose* poses, int32_t n, const sc_intrinsics* K, const float* grad_D,
                                       double* grad_xi, float* grad_depth, sc_stream stream) {
-    if (!V || !kf_ids || !depths || !poses || n < 1 || !intrinsics_ok(K) || !grad_D || !grad_xi)
+    if (!V || !kf_ids || !depths || !poses || n < 1 || !intrinsics_ok(K) || !grad_D || !grad_xi ||
+        ((uintptr_t)grad_D & 15))
         return SC_ERR_INVALID_ARG;
     if (n > ADJ_STATIC_MAX) return SC_ERR_CAPACITY;
     for (int i = 0; i < n; ++i) {
