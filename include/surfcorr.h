@@ -177,6 +177,12 @@ int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int
                       const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* intr,
                       const sc_fusion_params* fusion, float* kf_depth, float* kf_weight, sc_stream stream);
 
+/* Raw sensor depth to metres: depth[i] = raw[i] * scale (one float multiply, round
+ * to nearest; raw 0 gives 0, the invalid depth), for 16-bit depth images such as
+ * those of Kinect-class sensors (scale 1/1000 for millimetres, 1/5000 for the TUM
+ * RGB-D format).  raw and depth device [n], 16-byte aligned.  Asynchronous. */
+int sc_depth_from_u16(const uint16_t* raw, int64_t n, float scale, float* depth, sc_stream stream);
+
 /* ------------------------------------------------- colour keyframe fusion ---- */
 
 /* Device workspace sc_fuse_colour_keyframes needs for width x height images:

@@ -259,3 +259,38 @@ extern "C" int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses
     return fuse_impl(depths, frame_poses, frame_kf, n_frames, kf_poses, n_kf, K, fusion, kf_depth, kf_weight,
                      (cudaStream_t)stream);
 }
+
+// ------------------------------------------------------------ raw sensor depth ----
+
+namespace {
+
+// z = raw * scale (one float multiply, round to nearest), 0 stays 0 (invalid)
+__global__ void depth_from_u16_kernel(const uint16_t* __restrict__ raw, size_t n, float scale, float* __restrict__ out) {
+    const size_t n8 = n / 8;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n8; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 r = __ldg(reinterpret_cast<const uint4*>(raw) + i);
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+        float4* o = reinterpret_cast<float4*>(out) + 2 * i;
+        o[0] = make_float4(__fmul_rn((float)(w[0] & 0xffffu), scale), __fmul_rn((float)(w[0] >> 16), scale),
+                           __fmul_rn((float)(w[1] & 0xffffu), scale), __fmul_rn((float)(w[1] >> 16), scale));
+        o[1] = make_float4(__fmul_rn((float)(w[2] & 0xffffu), scale), __fmul_rn((float)(w[2] >> 16), scale),
+                           __fmul_rn((float)(w[3] & 0xffffu), scale), __fmul_rn((float)(w[3] >> 16), scale));
+    }
+    for (size_t i = n8 * 8 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = __fmul_rn((float)raw[i], scale);
+}
+
+}  // namespace
+
+extern "C" int sc_depth_from_u16(const uint16_t* raw, int64_t n, float scale, float* depth, sc_stream stream) {
+    if (n < 0 || (n > 0 && (!raw || !depth)) || !(scale > 0.f) || !std::isfinite(scale)) return SC_ERR_INVALID_ARG;
+    if (((uintptr_t)raw & 15) || ((uintptr_t)depth & 15)) return SC_ERR_INVALID_ARG;
+    if (n == 0) return SC_OK;
+    int dev = 0, sms = 0;
+    SC_CUDA(cudaGetDevice(&dev));
+    SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    depth_from_u16_kernel<<<sms * 8, 256, 0, (cudaStream_t)stream>>>(raw, (size_t)n, scale, depth);
+    sc::count_launches(1);
+    SC_CUDA(cudaGetLastError());
+    return SC_OK;
+}

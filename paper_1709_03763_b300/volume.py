@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (BatchConfig, ColourParams, FusionParams, Intrinsics, Pose, Profile, ReintItem, SurfcorrError, VolumeInfo,
                    VolumeParams, check, lib)
 
-__all__ = ["Volume", "BlockStore", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
+__all__ = ["Volume", "BlockStore", "depth_from_u16", "fuse_frames_into_keyframe", "fuse_keyframes", "prepare_fuse", "fuse_colour_keyframes",
            "prepare_colour", "pose_distance", "select_topm", "select_consecutive",
            "pose_exp_left", "mc_case", "overlap_counts", "segment_keyframes", "KF_CONST", "KF_DIST",
            "KF_OVRLP", "SurfcorrError", "make_intrinsics", "make_pose"]
@@ -394,6 +394,19 @@ def fuse_keyframes(depths: torch.Tensor, frame_poses=None, frame_kf=None, kf_pos
                                   _dev(out_weight, torch.float32, "out_weight"), _stream(stream)),
           "sc_fuse_keyframes")
     return out_depth, out_weight
+
+
+def depth_from_u16(raw: torch.Tensor, scale: float, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Raw 16-bit sensor depth (any shape, int16 / uint16 storage) to metres: raw * scale."""
+    if raw.dtype not in (torch.int16, torch.uint16):
+        raise TypeError("raw depth must be 16-bit")
+    if not raw.is_cuda or not raw.is_contiguous():
+        raise ValueError("raw depth must be a contiguous CUDA tensor")
+    if out is None:
+        out = torch.empty(raw.shape, dtype=torch.float32, device=raw.device)
+    check(lib().sc_depth_from_u16(raw.data_ptr(), raw.numel(), float(scale), _dev(out, torch.float32, "out"),
+                                  _stream(stream)), "sc_depth_from_u16")
+    return out
 
 
 def prepare_colour(frame_poses, frame_kf, kf_poses, width: int, height: int, device=None):

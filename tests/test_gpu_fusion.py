@@ -61,3 +61,15 @@ def test_batched_fusion_equals_per_keyframe_fusion():
         Zk, Wk = fuse_frames_into_keyframe(dg[s:s + 5].contiguous(), poses[s:s + 5], poses[s], synthetic.KINECT)
         assert torch.allclose(Wb[k], Wk, rtol=1e-5, atol=1e-9)
         assert torch.allclose(Zb[k], Zk, rtol=1e-6, atol=1e-7)
+
+
+def test_depth_from_u16_is_one_float_multiply():
+    from paper_1709_03763_b300 import depth_from_u16
+    g = np.random.default_rng(5)
+    raw = g.integers(0, 65536, 100003).astype(np.uint16)   # ragged tail after the 8-wide body
+    raw[:5] = [0, 1, 65535, 5000, 20000]
+    scale = np.float32(1.0 / 5000.0)
+    t = torch.from_numpy(raw.view(np.int16)).cuda()
+    out = depth_from_u16(t, float(scale)).cpu().numpy()
+    assert np.array_equal(out, raw.astype(np.float32) * scale)
+    assert out[0] == 0.0 and abs(out[3] - 1.0) < 1e-6
