@@ -99,13 +99,14 @@ __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) batch_all
     }
 }
 
+// grid (chunks, max_batch): blockIdx.y is the item, its chunk CTAs stride over its list
 __global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const BatchHeader* hdr, uint32_t* masks,
                                       int mw, int32_t* ulist, int32_t* counters, uint32_t list_cap) {
     const int n = hdr->n;
     const uint32_t call_id = hdr->call_id;
     const int lane = threadIdx.x & 31;
     const uint32_t stride = gridDim.x * blockDim.x;
-    for (int i = 0; i < n; ++i) {
+    for (int i = blockIdx.y; i < n; i += gridDim.y) {
         const uint32_t cnt = min((uint32_t)*items[i].old_count, list_cap);
         const int32_t* list = items[i].old_list;
         const uint32_t bit = 1u << (i & 31);
@@ -485,8 +486,9 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
     batch_alloc_kernel<<<V->num_sms * ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
         V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
     if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[1], s, cudaEventRecordExternal);
-    batch_mark_old_kernel<<<V->num_sms * 8, 256, 0, s>>>(V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist,
-                                                         B->counters, V->p.max_blocks_per_keyframe);
+    const int mark_y = std::min(V->p.max_batch, 1024);
+    batch_mark_old_kernel<<<dim3(std::max(1, V->num_sms * 8 / mark_y), mark_y), 256, 0, s>>>(
+        V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
     if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[2], s, cudaEventRecordExternal);
     const sc_batch_config& c = V->bcfg;
     const int grid = V->num_sms * ctas_per_sm_clamped(V, c);

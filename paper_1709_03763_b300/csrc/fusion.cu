@@ -139,7 +139,17 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel_any(const float*
 }
 
 __global__ void fuse_normalise_kernel(float* Z, const float* Wsum, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t n4 = n / 4;  // both arrays 16-byte aligned
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 w = reinterpret_cast<const float4*>(Wsum)[i];
+        float4 z = reinterpret_cast<float4*>(Z)[i];
+        z.x = w.x > 0.f ? z.x / w.x : 0.f;
+        z.y = w.y > 0.f ? z.y / w.y : 0.f;
+        z.z = w.z > 0.f ? z.z / w.z : 0.f;
+        z.w = w.w > 0.f ? z.w / w.w : 0.f;
+        reinterpret_cast<float4*>(Z)[i] = z;
+    }
+    for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float w = Wsum[i];
         Z[i] = w > 0.f ? Z[i] / w : 0.f;
     }
@@ -208,7 +218,10 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
         sc::count_launches(1);
         SC_CUDA(cudaGetLastError());
     }
-    fuse_normalise_kernel<<<1024, 256, 0, s>>>(kf_depth, kf_weight, n_kf * npx);
+    int dev = 0, sms = 148;
+    SC_CUDA(cudaGetDevice(&dev));
+    SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    fuse_normalise_kernel<<<sms * 8, 256, 0, s>>>(kf_depth, kf_weight, n_kf * npx);
     sc::count_launches(1);
     SC_CUDA(cudaGetLastError());
     return SC_OK;
