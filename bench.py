@@ -81,6 +81,9 @@ def parse():
                          "--profile-from-start off); prints only the timing")
     ap.add_argument("--profile-colour", action="store_true",
                     help="run colour fusion steps between cudaProfilerStart/Stop (for ncu) and exit")
+    ap.add_argument("--profile-extra", choices=["mc", "kf", "stream"], default=None,
+                    help="run Marching Cubes / KF_OVRLP grouping / a stream-out + stream-in of the "
+                         "step's volume between cudaProfilerStart/Stop (for ncu) and exit")
     ap.add_argument("--keyframes", type=int, default=60, help="keyframes of the workload (small ncu cases)")
     ap.add_argument("--max-blocks", type=int, default=1 << 21)
     return ap.parse_args()
@@ -545,6 +548,34 @@ def main():
     cfg, tune_ms = V.autotune_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true, P.intr)
     P.prep_upd = V.prepare_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true)
     setup_s = time.perf_counter() - t_setup
+
+    if args.profile_extra:
+        from paper_1709_03763_b300 import KF_OVRLP, BlockStore, segment_keyframes
+        P.step()
+        torch.cuda.synchronize()
+        nfr = P.K * KAPPA
+        cam = np.asarray(w.frame_poses[nfr - 1], np.float32)[:, 3]
+        store = BlockStore(V.info()["allocated_blocks"] + 1024, "rgba8") if args.profile_extra == "stream" else None
+        mc_out = torch.empty((4 << 20, 3, 3), dtype=torch.float32, device=dev) if args.profile_extra == "mc" else None
+
+        def extra():
+            if args.profile_extra == "mc":
+                V.marching_cubes(capacity=mc_out.shape[0], out=mc_out)
+            elif args.profile_extra == "kf":
+                segment_keyframes(KF_OVRLP, (KF_OVRLP_THR,), w.frame_poses[:nfr], w.intr, w.frames_depth[:nfr])
+            else:
+                V.stream_out(store, cam, STREAM_RADIUS)
+                V.stream_in(store, cam)
+        for _ in range(args.warmup):
+            extra()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            extra()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_extra": args.profile_extra, "steps": args.steps}), flush=True)
+        return
 
     if args.profile_colour:
         for _ in range(args.warmup):
