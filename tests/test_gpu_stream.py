@@ -144,3 +144,22 @@ def test_block_allocated_while_stored_conflicts():
     assert len(S) == n  # the conflicting blocks stay stored
     V.close()
     S.close()
+
+
+def test_store_capacity_and_empty_cases():
+    w = synthetic.workload_tiny()
+    V = _volume(w, colour="rgba8")
+    V.integrate(0, w.kf_depth[0].cuda(), w.kf_rgba[0].cuda(), w.intr, w.kf_poses[0])
+    n = V.info()["allocated_blocks"]
+    small = BlockStore(max(1, n // 4))
+    with pytest.raises(SurfcorrError) as e:  # more blocks than the store holds: nothing moves
+        V.stream_out(small, _camera(w.kf_poses[0]), 0.0)
+    assert e.value.code == _lib.SC_ERR_CAPACITY
+    assert len(small) == 0 and V.info()["allocated_blocks"] == n
+    big = BlockStore(n + 16)
+    assert V.stream_out(big, _camera(w.kf_poses[0]), 1e6) == 0      # everything inside: nothing moves
+    assert V.stream_in(big, _camera(w.kf_poses[0])) == 0             # empty store
+    with pytest.raises(SurfcorrError):                               # colour formats must match
+        V.stream_out(BlockStore(16, "f32"), _camera(w.kf_poses[0]), 0.0)
+    for x in (V, small, big):
+        x.close()
