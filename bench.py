@@ -467,10 +467,10 @@ def oracle_reintegration(n_kf, steps=1, warmup=0, w=None):
     import oracle
     from paper_1709_03763_b300 import synthetic
     oracle.build()
-    if w is None:
+    if w is None:  # the same workload as the GPU arm (sensor-format depth, textured colour)
         import torch
         dev = "cuda" if torch.cuda.is_available() else "cpu"
-        w = synthetic.workload_kinect(device=dev, n_frames=N_FRAMES, kappa=KAPPA, render_frames=n_kf * KAPPA)
+        w = make_workload(torch.device(dev), n_kf)
     it = w.intr.as_tuple()
     frames = w.frames_depth[:n_kf * KAPPA].cpu()
     depth = []
