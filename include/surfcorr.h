@@ -375,6 +375,15 @@ int sc_mc_case(int32_t mask, int32_t* edges);
 int sc_import_blocks(sc_volume* vol, const int32_t* coords, const float* D, const float* W, const void* C,
                      int32_t n, sc_stream stream);
 
+/* Restore a keyframe's block list A(k, T) (checkpoint / resume): coords device [n][3]
+ * int32, the block coordinates of its list (e.g. sc_get_keyframe_blocks mapped to
+ * coordinates before the checkpoint), all resident in the volume.  Marks kf_id
+ * integrated, so that it can be de-integrated and re-integrated with the depth,
+ * colour and pose it was integrated with.  SC_ERR_ALREADY_INTEGRATED if kf_id is
+ * integrated, SC_ERR_LIST_FULL if n > max_blocks_per_keyframe, SC_ERR_INVALID_ARG
+ * (kf_id left not integrated) if a coordinate has no resident block.  Synchronises. */
+int sc_set_keyframe_blocks(sc_volume* vol, int32_t kf_id, const int32_t* coords, int32_t n, sc_stream stream);
+
 /* -------------------------------------------------- the streaming sphere ---- */
 
 /* Host block store of the streaming sphere (Section 3 "SDF volume": only blocks within

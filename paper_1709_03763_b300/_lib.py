@@ -111,6 +111,7 @@ SIGNATURES = {
     "sc_marching_cubes": (c_i32, [c_p, c_p, c_p, c_i64, P(c_i64), c_p]),
     "sc_mc_case": (c_i32, [c_i32, P(c_i32)]),
     "sc_import_blocks": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_i32, c_p]),
+    "sc_set_keyframe_blocks": (c_i32, [c_p, c_i32, c_p, c_i32, c_p]),
     "sc_create_block_store": (c_i32, [c_i64, c_i32, P(c_p)]),
     "sc_destroy_block_store": (c_i32, [c_p]),
     "sc_block_store_count": (c_i64, [c_p]),

@@ -1,5 +1,5 @@
 // Marching Cubes extraction of the SDF's zero level set (Section 3 "SDF volume"),
-// and block import.
+// block import and keyframe block lists set from coordinates (restoring a volume).
 //
 // Cube (x, y, z) has the 8 corner voxels (x + i0, y + i1, z + i2), i0..i2 the bits
 // of the corner number; it is meshed when all 8 exist and are observed (W > 0).  A
@@ -324,7 +324,47 @@ __global__ void import_kernel(DevVolume V, const int32_t* coords, const float* D
     }
 }
 
+// list[i] = slot of block coords[i]; a coordinate without a resident block sets the
+// status (SC_ERR_INVALID_ARG), and the caller then leaves the list empty
+__global__ void set_list_kernel(DevVolume V, const int32_t* coords, int32_t n, int32_t* list) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int x = coords[3 * i], y = coords[3 * i + 1], z = coords[3 * i + 2];
+        const int32_t s = coord_ok(x, y, z) ? find_slot(V, pack_key(x, y, z)) : -1;
+        if (s < 0) set_status(V.status, SC_ERR_INVALID_ARG);
+        list[i] = s < 0 ? 0 : s;
+    }
+}
+
 }  // namespace
+
+extern "C" int sc_set_keyframe_blocks(sc_volume* V, int32_t kf_id, const int32_t* coords, int32_t n,
+                                      sc_stream stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!V || kf_id < 0 || kf_id >= V->p.max_keyframes || n < 0 || (n > 0 && !coords) || ((uintptr_t)coords & 3))
+        return SC_ERR_INVALID_ARG;
+    if ((uint32_t)n > V->p.max_blocks_per_keyframe) return SC_ERR_LIST_FULL;
+    if (V->integrated[kf_id]) return SC_ERR_ALREADY_INTEGRATED;
+    SC_CUDA(cudaSetDevice(V->device));
+    const int which = V->cur[kf_id];
+    int32_t* list = list_ptr(V, kf_id, which);
+    if (n > 0) {
+        set_list_kernel<<<std::min((n + 255) / 256, V->num_sms * 8), 256, 0, s>>>(V->dv, coords, n, list);
+        count_launches(1);
+        SC_CUDA(cudaGetLastError());
+    }
+    V->h_word[3] = (uint32_t)n;
+    SC_CUDA(cudaMemcpyAsync(count_ptr(V, kf_id, which), V->h_word + 3, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const int st = read_status(V, s);
+    if (st) {  // a block is missing: the keyframe stays not integrated
+        V->h_word[3] = 0;
+        SC_CUDA(cudaMemcpyAsync(count_ptr(V, kf_id, which), V->h_word + 3, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        SC_CUDA(cudaStreamSynchronize(s));
+        return st;
+    }
+    V->integrated[kf_id] = 1;
+    V->nonresident[kf_id] = 0;
+    return SC_OK;
+}
 
 extern "C" int sc_mc_case(int32_t mask, int32_t* edges) {
     if (mask < 0 || mask > 255 || !edges) return SC_ERR_INVALID_ARG;

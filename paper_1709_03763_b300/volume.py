@@ -241,6 +241,47 @@ class Volume:
         check(lib().sc_import_blocks(self.h, _dev(coords, torch.int32, "coords"), _dev(D, torch.float32, "D"),
                                      _dev(W, torch.float32, "W"), cptr, n, _stream(stream)), "sc_import_blocks")
 
+    def set_keyframe_blocks(self, kf_id: int, coords: torch.Tensor, stream=None):
+        """Restore keyframe kf_id's block list from block coordinates [n,3] int32 (device)."""
+        n = int(coords.shape[0])
+        ptr = _dev(coords.contiguous(), torch.int32, "coords") if n else None
+        check(lib().sc_set_keyframe_blocks(self.h, int(kf_id), ptr, n, _stream(stream)), "sc_set_keyframe_blocks")
+
+    def save(self, path: str, keyframes=()):
+        """Checkpoint: every block (coords, D, W, C) and the block lists (as coordinates)
+        of the given integrated keyframes, to an .npz file."""
+        ex = self.extract()
+        out = {k: v.cpu().numpy() for k, v in ex.items()}
+        slot_coord = {}
+        slots = ex["slots"].cpu().numpy()
+        coords = out["coords"]
+        idx = np.full(int(slots.max()) + 1 if len(slots) else 1, -1, np.int64)
+        idx[slots] = np.arange(len(slots))
+        for k in keyframes:
+            ks = self.keyframe_blocks(int(k)).cpu().numpy()
+            out[f"kf_{int(k)}"] = coords[idx[ks]]
+        out["colour"] = np.array(self.colour)
+        np.savez(path, **out)
+
+    def load(self, path: str, stream=None) -> list:
+        """Resume from save(): import the blocks into this (empty) volume and restore the
+        saved keyframes' block lists.  Returns the restored keyframe ids."""
+        z = np.load(path)
+        if str(z["colour"]) != self.colour:
+            raise ValueError("checkpoint colour format differs from the volume's")
+        dev = torch.device("cuda", self.device)
+        C = torch.from_numpy(z["C"]).to(dev)
+        if self.colour == "f32":
+            C = C.permute(0, 2, 1).contiguous()  # extract gives [n,512,3]; import takes [n,3,512]
+        else:
+            C = C.contiguous()
+        self.import_blocks(torch.from_numpy(z["coords"]).to(dev), torch.from_numpy(z["D"]).to(dev),
+                           torch.from_numpy(z["W"]).to(dev), C, stream=stream)
+        kfs = sorted(int(k[3:]) for k in z.files if k.startswith("kf_"))
+        for k in kfs:
+            self.set_keyframe_blocks(k, torch.from_numpy(z[f"kf_{k}"]).to(dev), stream=stream)
+        return kfs
+
     def marching_cubes(self, capacity: int | None = None, cubes: bool = False, out: torch.Tensor | None = None,
                        stream=None):
         """Zero-level-set triangles [t,3,3] float32 (metres) and, with cubes=True, their cube
