@@ -69,7 +69,10 @@ __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, floa
         tmax[r] = __int_as_float(0x7f800000);  // +inf: no crossing on this axis
         tdel[r] = tmax[r];
         if (rem[r] > 0) {
-            const float inv = __frcp_rn(d);
+            // approximate reciprocal (1 ulp): the crossing times only order the axes of
+            // the walk; a different order within float error of a tie is a marginal
+            // decision (a segment passing within float error of a block edge)
+            const float inv = rcp_approx(d);
             const float bound = (float)(8 * (b[r] + (step[r] > 0 ? 1 : 0)) - k.ti[r]);
             tmax[r] = __fmul_rn(__fsub_rn(bound, q0[r]), inv);
             tdel[r] = __fmul_rn(8.f, fabsf(inv));
