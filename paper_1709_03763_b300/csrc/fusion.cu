@@ -16,20 +16,12 @@ namespace {
 
 constexpr int FUSE_MAX_FRAMES = 64;  // frames per launch (kernel parameter space)
 
-// a*b - c*d with one rounding error (fma-compensated, W. Kahan): the normal's
-// components cancel strongly for surfaces seen at grazing angles
-__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
-    const float w = c * d;
-    const float e = fmaf(-c, d, w);
-    const float f = fmaf(a, b, -w);
-    return f + e;
-}
 constexpr int FUSE_TX = 32, FUSE_TY = 8;
 
 struct FuseFrame {
-    float R[9];  // keyframe_from_frame rotation  R*^T R_i
-    float t[3];  // keyframe_from_frame translation R*^T (t_i - t*)
-    int kf;      // output keyframe image
+    float Pr[9];  // keyframe_from_frame rotation R*^T R_i, rows 0 and 1 scaled by fx and fy
+    float t[3];   // keyframe_from_frame translation R*^T (t_i - t*), scaled likewise
+    int kf;       // output keyframe image
 };
 
 struct FuseArgs {
@@ -54,50 +46,55 @@ cudaEvent_t fprof_event(cudaStream_t s) {
 }
 
 struct FuseCam {
-    float fx, fy, cx, cy, ifx, ify;  // ifx = 1/fx, ify = 1/fy
+    float cx, cy, ifx, ify;  // ifx = 1/fx, ify = 1/fy
+    float cxh, cyh;          // cx + 1/2, cy + 1/2: nearest pixel by one floor
+    float Wf, Hf;
     int W, H;
     float disc_rel;
     float* S;     // sum w_z Z*_p (in the Z* output until normalised)
     float* Wsum;  // sum w_z (the W* output)
 };
 
-// Eq. 1 contribution of one frame pixel (u, v) with depth z and 4-neighbours.
-__device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c, int u, int v, float z, float zl,
-                                           float zr, float zu, float zd, float* S, float* Wsum) {
-    if (!(z > 0.f)) return;
-    if (!(zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f)) return;
+// floor(x) for 0 <= x < 2^23 without a conversion instruction: adding 2^23 rounded
+// down leaves floor(x) in the low mantissa bits
+__device__ __forceinline__ int fuse_floor(float x) { return __float_as_int(__fadd_rd(x, 8388608.f)) - 0x4b000000; }
+
+// Eq. 1 contribution of one frame pixel with depth z and 4-neighbours at normalised
+// image coordinates xn = (u - cx) / fx, yn = (v - cy) / fy.  Sk, Wk: the keyframe's images.
+// All tests fold into one predicate, so a warp takes no divergent early exits.
+__device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c, float xn, float yn, float z,
+                                           float zl, float zr, float zu, float zd, float* Sk, float* Wk) {
+    // a valid depth whose four neighbours are valid and within disc_rel * z of it
     const float lim = c.disc_rel * z;
-    if (fabsf(zl - z) > lim || fabsf(zr - z) > lim || fabsf(zu - z) > lim || fabsf(zd - z) > lim) return;
-    // warp into the keyframe
-    const float xn = (u - c.cx) * c.ifx, yn = (v - c.cy) * c.ify;
-    const float P[3] = {xn * z, yn * z, z};
-    float ps[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) ps[r] = fmaf(F.R[3 * r], P[0], fmaf(F.R[3 * r + 1], P[1], fmaf(F.R[3 * r + 2], P[2], F.t[r])));
-    if (!(ps[2] > 0.f)) return;
+    bool ok = z > 0.f && zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f;
+    ok = ok && fabsf(zl - z) <= lim && fabsf(zr - z) <= lim && fabsf(zu - z) <= lim && fabsf(zd - z) <= lim;
+    // warp into the keyframe: (fx X*, fy Y*, Z*) = Pr P + t
+    const float P0 = xn * z, P1 = yn * z;
+    const float X = fmaf(F.Pr[0], P0, fmaf(F.Pr[1], P1, fmaf(F.Pr[2], z, F.t[0])));
+    const float Y = fmaf(F.Pr[3], P0, fmaf(F.Pr[4], P1, fmaf(F.Pr[5], z, F.t[1])));
+    const float Zs = fmaf(F.Pr[6], P0, fmaf(F.Pr[7], P1, fmaf(F.Pr[8], z, F.t[2])));
     // approximate reciprocal (2 ulp): a few 1e-5 px at the nearest-pixel rounding
-    const float rz = __fdividef(1.f, ps[2]);
-    const float uu = fmaf(c.fx * ps[0], rz, c.cx) + 0.5f;
-    const float vv = fmaf(c.fy * ps[1], rz, c.cy) + 0.5f;
-    if (!(uu >= 0.f && uu < (float)c.W && vv >= 0.f && vv < (float)c.H)) return;
-    const size_t q = (size_t)F.kf * c.W * c.H + (size_t)(int)vv * c.W + (int)uu;
-    // w_z = cos(theta) / Z^2, theta from the central-difference normal
-    // a = P(u+1,v) - P(u-1,v), b = P(u,v+1) - P(u,v-1), written as
-    // x (z_r - z_l) + (z_r + z_l) / fx etc. so that no large terms cancel
-    const float dzx = zr - zl, dzy = zd - zu;
-    const float ax = fmaf(xn, dzx, (zr + zl) * c.ifx);
-    const float ay = yn * dzx;
-    const float az = dzx;
-    const float bx = xn * dzy;
-    const float by = fmaf(yn, dzy, (zd + zu) * c.ify);
-    const float bz = dzy;
-    const float nx = diff_of_products(ay, bz, az, by), ny = diff_of_products(az, bx, ax, bz),
-                nz = diff_of_products(ax, by, ay, bx);
-    const float n2 = fmaf(nx, nx, fmaf(ny, ny, nz * nz));
-    if (!(n2 > 0.f)) return;
-    const float w = __fdividef(fabsf(nz) * rsqrtf(n2), z * z);
-    atomicAdd(S + q, w * ps[2]);
-    atomicAdd(Wsum + q, w);
+    const float rz = __fdividef(1.f, Zs);
+    const float uu = fmaf(X, rz, c.cxh);
+    const float vv = fmaf(Y, rz, c.cyh);
+    // NaN and inf fail these comparisons
+    ok = ok && Zs > 0.f && uu >= 0.f && uu < c.Wf && vv >= 0.f && vv < c.Hf;
+    // w_z = cos(theta) / Z^2, theta from the normal n = a x b of the central differences
+    // a = P(u+1,v) - P(u-1,v) = dzx (xn, yn, 1) + (A, 0, 0),  A = (z_r + z_l) / fx
+    // b = P(u,v+1) - P(u,v-1) = dzy (xn, yn, 1) + (0, B, 0),  B = (z_d + z_u) / fy
+    // whose cross product expands to n = (-dzx B, -dzy A, A B + dzx B xn + dzy A yn):
+    // the dzx dzy xn yn terms of a_x b_y and a_y b_x cancel algebraically, not in float
+    const float A = (zr + zl) * c.ifx, B = (zd + zu) * c.ify;
+    const float m1 = (zr - zl) * B, m2 = (zd - zu) * A;
+    const float nz = fmaf(m1, xn, fmaf(m2, yn, A * B));
+    const float n2 = fmaf(m1, m1, fmaf(m2, m2, nz * nz));
+    ok = ok && n2 > 0.f;
+    if (ok) {
+        const float w = __fdividef(fabsf(nz) * rsqrtf(n2), z * z);
+        const int q = fuse_floor(vv) * c.W + fuse_floor(uu);
+        atomicAdd(Sk + q, w * Zs);
+        atomicAdd(Wk + q, w);
+    }
 }
 
 // One thread per 4 consecutive pixels of a row (u0 = 4 * thread): the row and its two
@@ -109,19 +106,23 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     const int u0 = 4 * (blockIdx.x * FUSE_TX + threadIdx.x);
     const int v = blockIdx.y * FUSE_TY + threadIdx.y;
     if (u0 >= W || v < 1 || v >= H - 1) return;
-    const FuseFrame F = a.f[blockIdx.z];
-    const float* Z = depths + (size_t)blockIdx.z * W * H + (size_t)v * W + u0;
+    const FuseFrame& F = a.f[blockIdx.z];
+    const size_t npx = (size_t)W * H;
+    const float* Z = depths + (size_t)blockIdx.z * npx + (size_t)v * W + u0;
     const float4 row = __ldg(reinterpret_cast<const float4*>(Z));
     const float4 up = __ldg(reinterpret_cast<const float4*>(Z - W));
     const float4 dn = __ldg(reinterpret_cast<const float4*>(Z + W));
-    const float left = u0 > 0 ? __ldg(Z - 1) : 0.f;
-    const float right = u0 + 4 < W ? __ldg(Z + 4) : 0.f;
-    float* S = c.S;
-    float* Ws = c.Wsum;
-    if (u0 > 0) fuse_pixel(F, c, u0, v, row.x, left, row.y, up.x, dn.x, S, Ws);
-    fuse_pixel(F, c, u0 + 1, v, row.y, row.x, row.z, up.y, dn.y, S, Ws);
-    fuse_pixel(F, c, u0 + 2, v, row.z, row.y, row.w, up.z, dn.z, S, Ws);
-    if (u0 + 4 < W) fuse_pixel(F, c, u0 + 3, v, row.w, row.z, right, up.w, dn.w, S, Ws);
+    const float left = u0 > 0 ? __ldg(Z - 1) : 0.f;     // 0: the first pixel has no left neighbour
+    const float right = u0 + 4 < W ? __ldg(Z + 4) : 0.f;  // 0: the last pixel has no right neighbour
+    float* Sk = c.S + (size_t)F.kf * npx;
+    float* Wk = c.Wsum + (size_t)F.kf * npx;
+    // pixel coordinates stepped in float (exact integers): one conversion per thread
+    const float uf = (float)u0;
+    const float yn = ((float)v - c.cy) * c.ify;
+    fuse_pixel(F, c, (uf - c.cx) * c.ifx, yn, row.x, left, row.y, up.x, dn.x, Sk, Wk);
+    fuse_pixel(F, c, ((uf + 1.f) - c.cx) * c.ifx, yn, row.y, row.x, row.z, up.y, dn.y, Sk, Wk);
+    fuse_pixel(F, c, ((uf + 2.f) - c.cx) * c.ifx, yn, row.z, row.y, row.w, up.z, dn.z, Sk, Wk);
+    fuse_pixel(F, c, ((uf + 3.f) - c.cx) * c.ifx, yn, row.w, row.z, right, up.w, dn.w, Sk, Wk);
 }
 
 // Any width: one thread per pixel.
@@ -132,10 +133,12 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel_any(const float*
     const int W = c.W, H = c.H;
     if (u < 1 || v < 1 || u >= W - 1 || v >= H - 1) return;
     const FuseFrame& F = a.f[blockIdx.z];
-    const float* Z = depths + (size_t)blockIdx.z * W * H;
+    const size_t npx = (size_t)W * H;
+    const float* Z = depths + (size_t)blockIdx.z * npx;
     const size_t p = (size_t)v * W + u;
-    fuse_pixel(F, c, u, v, __ldg(Z + p), __ldg(Z + p - 1), __ldg(Z + p + 1), __ldg(Z + p - W), __ldg(Z + p + W), c.S,
-               c.Wsum);
+    fuse_pixel(F, c, ((float)u - c.cx) * c.ifx, ((float)v - c.cy) * c.ify, __ldg(Z + p), __ldg(Z + p - 1),
+               __ldg(Z + p + 1), __ldg(Z + p - W), __ldg(Z + p + W), c.S + (size_t)F.kf * npx,
+               c.Wsum + (size_t)F.kf * npx);
 }
 
 __global__ void fuse_normalise_kernel(float* Z, const float* Wsum, size_t n) {
@@ -174,8 +177,8 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
     const size_t npx = (size_t)W * H;
     SC_CUDA(cudaMemsetAsync(kf_depth, 0, n_kf * npx * sizeof(float), s));
     SC_CUDA(cudaMemsetAsync(kf_weight, 0, n_kf * npx * sizeof(float), s));
-    FuseCam c{K->fx, K->fy, K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), W, H, fusion->disc_rel,
-              kf_depth, kf_weight};
+    FuseCam c{K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), (float)((double)K->cx + 0.5),
+              (float)((double)K->cy + 0.5), (float)W, (float)H, W, H, fusion->disc_rel, kf_depth, kf_weight};
     for (int f0 = 0; f0 < n; f0 += FUSE_MAX_FRAMES) {
         const int nf = (n - f0) < FUSE_MAX_FRAMES ? (n - f0) : FUSE_MAX_FRAMES;
         FuseArgs a;
@@ -183,16 +186,18 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
             const sc_pose& T = frame_poses[f0 + f];
             const int kf = frame_kf ? frame_kf[f0 + f] : 0;
             const sc_pose& Tk = kf_poses[kf];
-            // keyframe_from_frame, composed in double and rounded once
+            // keyframe_from_frame with the focal lengths folded into rows 0 and 1,
+            // composed in double and rounded once
+            const double scale[3] = {(double)K->fx, (double)K->fy, 1.0};
             for (int r = 0; r < 3; ++r) {
                 for (int q = 0; q < 3; ++q) {
                     double acc = 0;
                     for (int k = 0; k < 3; ++k) acc += (double)Tk.m[k][r] * (double)T.m[k][q];
-                    a.f[f].R[3 * r + q] = (float)acc;
+                    a.f[f].Pr[3 * r + q] = (float)(scale[r] * acc);
                 }
                 double acc = 0;
                 for (int k = 0; k < 3; ++k) acc += (double)Tk.m[k][r] * ((double)T.m[k][3] - (double)Tk.m[k][3]);
-                a.f[f].t[r] = (float)acc;
+                a.f[f].t[r] = (float)(scale[r] * acc);
             }
             a.f[f].kf = kf;
         }
