@@ -36,21 +36,33 @@ struct Corners {
     float beta[8];
 };
 
-__device__ inline bool point_corners(const DevVolume& V, float s, const float* p, Corners& c, float& Dt) {
-    // grid coordinate in double: at ~10^3 voxels from the origin a float fraction
-    // would carry 1e-4-voxel errors into the interpolation weights
+__device__ inline bool point_corners(const DevVolume& V, float s, float inv_s, const float* p, Corners& c, float& Dt) {
+    // grid coordinate g = p / s without a double division: q = p (1/s) is within two
+    // float ulps of g, r = p - q s is its residual (one fused rounding), and the
+    // fraction (q - floor(q)) + r / s carries about 1e-7 voxel of error where a
+    // float g would carry 1e-4 at 10^3 voxels from the origin
     int i0[3];
     float f[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const double g = (double)p[a] / (double)s;
-        const double fl = floor(g);
+        const float x = __ldg(p + a);
+        const float q = __fmul_rn(x, inv_s);
+        const float r = __fmaf_rn(-q, s, x);
+        float fl = floorf(q);
+        float fr = __fadd_rn(__fsub_rn(q, fl), __fmul_rn(r, inv_s));
+        if (fr < 0.f) {  // g lies just below the integer q rounded up to
+            fl = __fsub_rn(fl, 1.f);
+            fr = __fadd_rn(fr, 1.f);
+        } else if (fr >= 1.f) {
+            fl = __fadd_rn(fl, 1.f);
+            fr = __fsub_rn(fr, 1.f);
+        }
         i0[a] = (int)fl;
-        f[a] = (float)(g - fl);
+        f[a] = fr;
     }
+    // the corners' blocks first (one, two, four or eight distinct ones) ...
     int32_t last_slot = -1;
     int lbx = 0x7fffffff, lby = 0, lbz = 0;
-    float acc = 0.f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
@@ -64,39 +76,60 @@ __device__ inline bool point_corners(const DevVolume& V, float s, const float* p
         }
         if (last_slot < 0) return false;
         const int vi = (ix & 7) + 8 * (iy & 7) + 64 * (iz & 7);
-        const uint32_t gv = (uint32_t)last_slot * NVOX + vi;
-        const float w = V.W[gv];
-        if (!(w > 0.f)) return false;
+        c.vox[k] = (uint32_t)last_slot * NVOX + vi;
+    }
+    // ... then all sixteen voxel loads in flight together
+    float w[8], d[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        w[k] = V.W[c.vox[k]];
+        d[k] = V.D[c.vox[k]];
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (!(w[k] > 0.f)) return false;
+        const int ox = k & 1, oy = (k >> 1) & 1, oz = (k >> 2) & 1;
         const float b = (ox ? f[0] : 1.f - f[0]) * (oy ? f[1] : 1.f - f[1]) * (oz ? f[2] : 1.f - f[2]);
-        c.vox[k] = gv;
         c.beta[k] = b;
-        acc = fmaf(b, V.D[gv], acc);
+        acc = fmaf(b, d[k], acc);
     }
     Dt = acc;
     return true;
 }
 
-// out[1] += P, out[2] += sum Dt^2, grad += 2 Dt beta (scaled by 1/P later)
-__global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64_t n, double* out, float* grad) {
+// out[1] += P, out[2] += sum Dt^2, grad += 2 Dt beta (scaled by 1/P later).  Dt^2 is
+// summed in float over at most 8 points of a thread, then in double.
+__global__ void loss_points_kernel(DevVolume V, float s, float inv_s, const float* pts, int64_t n, double* out,
+                                   float* grad) {
     __shared__ double sh[2][LOSS_THREADS / 32];
-    double a = 0.0, cnt = 0.0;
+    double a = 0.0;
+    float af = 0.f;
+    int m = 0;
+    unsigned cnt = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         Corners c;
         float Dt;
-        if (point_corners(V, s, pts + 3 * i, c, Dt)) {
-            a += (double)Dt * Dt;
-            cnt += 1.0;
+        if (point_corners(V, s, inv_s, pts + 3 * i, c, Dt)) {
+            af = fmaf(Dt, Dt, af);
+            ++cnt;
+            if (++m == 8) {
+                a += (double)af;
+                af = 0.f;
+                m = 0;
+            }
             const float g = 2.f * Dt;
 #pragma unroll
             for (int k = 0; k < 8; ++k) atomicAdd(grad + c.vox[k], g * c.beta[k]);
         }
     }
+    a += (double)af;
     a = warp_sum(a);
-    cnt = warp_sum(cnt);
+    const double cn = warp_sum((double)cnt);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         sh[0][w] = a;
-        sh[1][w] = cnt;
+        sh[1][w] = cn;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -114,19 +147,27 @@ __global__ void loss_points_kernel(DevVolume V, float s, const float* pts, int64
 __global__ void loss_reg_kernel(DevVolume V, double* out, float* grad) {
     __shared__ double sh[2][LOSS_THREADS / 32];
     const size_t nv = (size_t)min(*V.pool_count, V.max_blocks) * NVOX;
+    // float sums over at most 8 groups of 4 voxels, then double
     double a = 0.0, b = 0.0;
+    float pa = 0.f, pb = 0.f;
+    int m = 0;
     for (size_t i = (blockIdx.x * (size_t)blockDim.x + threadIdx.x) * 4; i < nv; i += (size_t)gridDim.x * blockDim.x * 4) {
         const float4 W = *reinterpret_cast<const float4*>(V.W + i);
         const float4 D = *reinterpret_cast<const float4*>(V.D + i);
         *reinterpret_cast<float4*>(grad + i) = make_float4(0.f, 0.f, 0.f, 0.f);
-        float pa = 0.f, pb = 0.f;
         if (W.x > 0.f) { pa = fmaf(W.x * D.x, D.x, pa); pb += W.x; }
         if (W.y > 0.f) { pa = fmaf(W.y * D.y, D.y, pa); pb += W.y; }
         if (W.z > 0.f) { pa = fmaf(W.z * D.z, D.z, pa); pb += W.z; }
         if (W.w > 0.f) { pa = fmaf(W.w * D.w, D.w, pa); pb += W.w; }
-        a += pa;
-        b += pb;
+        if (++m == 8) {
+            a += pa;
+            b += pb;
+            pa = pb = 0.f;
+            m = 0;
+        }
     }
+    a += pa;
+    b += pb;
     a = warp_sum(a);
     b = warp_sum(b);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -324,7 +365,8 @@ extern "C" int sc_sdf_loss(sc_volume* V, const float* points, int64_t n, float l
     SC_CUDA(cudaMemsetAsync(out, 0, 5 * sizeof(double), s));
     const int grid = V->num_sms * 8;
     loss_reg_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, out, grad_D);
-    if (n > 0) loss_points_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, points, n, out, grad_D);
+    if (n > 0) loss_points_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, vs, (float)(1.0 / (double)vs), points, n, out,
+                                                              grad_D);
     loss_grad_combine_kernel<<<grid, LOSS_THREADS, 0, s>>>(V->dv, lambda, out, grad_D);
     loss_finalize_kernel<<<1, 1, 0, s>>>(lambda, out);
     count_launches(n > 0 ? 4 : 3);
