@@ -1,7 +1,8 @@
 // Keyframe strategies (Section 4.2): the overlap ratio of KF_OVRLP on the GPU and
 // the host driver that groups frames into keyframes (KF_CONST, KF_DIST, KF_OVRLP).
 //
-// overlap_kernel: one thread per pixel of up to 64 frames per launch (grid z = frame):
+// overlap_kernel: one thread per 4 pixels of a row (one thread per pixel for widths
+// not a multiple of 4) of up to 64 frames per launch (grid z = frame):
 // a valid pixel (Z > 0) is warped into the keyframe (keyframe_from_frame composed in
 // double on the host) and counts as overlapping when it lands in front of the
 // keyframe with its nearest pixel (halves up) inside the image.  Per-CTA counts are
@@ -9,9 +10,12 @@
 //
 // KF_OVRLP is sequential by definition (the keyframe a frame is compared with depends
 // on the earlier decisions), so the driver evaluates the next 32 frames against the
-// current keyframe in one launch, reads the counts back, starts a keyframe at the
-// first frame below the threshold and continues after it.
+// current keyframe in one launch, reads the counts back (through a pinned buffer held
+// per device for the life of the process, so concurrent calls on one device take
+// turns), starts a keyframe at the first frame below the threshold and continues
+// after it.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "volume.cuh"
@@ -38,36 +42,36 @@ struct OvCam {
     int W, H;
 };
 
+
+
+// Overlap decision of one pixel (u, v) with depth z: valid (z > 0) and, if valid,
+// whether its point lands in front of the keyframe with its nearest pixel inside.
+__device__ __forceinline__ void overlap_pixel(const OvFrame& F, const OvCam& c, float uf, float yn, float z,
+                                              unsigned& valid, unsigned& inside) {
+    if (!(z > 0.f)) return;
+    ++valid;
+    const float P[3] = {(uf - c.cx) * c.ifx * z, yn * z, z};
+    float p[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        p[r] = fmaf(F.R[3 * r], P[0], fmaf(F.R[3 * r + 1], P[1], fmaf(F.R[3 * r + 2], P[2], F.t[r])));
+    if (p[2] > 0.f) {
+        const float rz = 1.f / p[2];
+        const float uu = floorf(fmaf(c.fx * p[0], rz, c.cx) + 0.5f);
+        const float vv = floorf(fmaf(c.fy * p[1], rz, c.cy) + 0.5f);
+        inside += (uu >= 0.f && uu < (float)c.W && vv >= 0.f && vv < (float)c.H) ? 1u : 0u;
+    }
+}
+
 __device__ __forceinline__ unsigned warp_add(unsigned v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__global__ void __launch_bounds__(OV_TX* OV_TY) overlap_kernel(const float* __restrict__ depths, const OvArgs a,
-                                                               const OvCam c, unsigned long long* counts) {
+// Per-CTA counts: warp shuffles, then two 64-bit atomics per CTA.
+__device__ __forceinline__ void overlap_reduce(unsigned valid, unsigned inside, unsigned long long* counts) {
     __shared__ unsigned red[2][OV_TX * OV_TY / 32];
-    const int j = blockIdx.z;
-    const OvFrame& F = a.f[j];
-    const int u = blockIdx.x * OV_TX + threadIdx.x, v = blockIdx.y * OV_TY + threadIdx.y;
-    unsigned valid = 0, inside = 0;
-    if (u < c.W && v < c.H) {
-        const float z = __ldg(depths + (size_t)F.frame * c.W * c.H + (size_t)v * c.W + u);
-        if (z > 0.f) {
-            valid = 1;
-            const float P[3] = {(u - c.cx) * c.ifx * z, (v - c.cy) * c.ify * z, z};
-            float p[3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-                p[r] = fmaf(F.R[3 * r], P[0], fmaf(F.R[3 * r + 1], P[1], fmaf(F.R[3 * r + 2], P[2], F.t[r])));
-            if (p[2] > 0.f) {
-                const float rz = 1.f / p[2];
-                const float uu = floorf(fmaf(c.fx * p[0], rz, c.cx) + 0.5f);
-                const float vv = floorf(fmaf(c.fy * p[1], rz, c.cy) + 0.5f);
-                inside = (uu >= 0.f && uu < (float)c.W && vv >= 0.f && vv < (float)c.H) ? 1u : 0u;
-            }
-        }
-    }
     const int tid = threadIdx.y * OV_TX + threadIdx.x, lane = tid & 31, w = tid >> 5;
     valid = warp_add(valid);
     inside = warp_add(inside);
@@ -80,9 +84,47 @@ __global__ void __launch_bounds__(OV_TX* OV_TY) overlap_kernel(const float* __re
         unsigned long long s = 0;
 #pragma unroll
         for (int k = 0; k < OV_TX * OV_TY / 32; ++k) s += red[tid][k];
-        if (s) atomicAdd(counts + 2 * j + tid, s);
+        if (s) atomicAdd(counts + 2 * blockIdx.z + tid, s);
     }
 }
+
+// Width a multiple of 4: pixels u0 .. u0 + 3 from one 16-byte load.
+__global__ void __launch_bounds__(OV_TX* OV_TY) overlap_kernel(const float* __restrict__ depths, const OvArgs a,
+                                                               const OvCam c, unsigned long long* counts) {
+    const OvFrame& F = a.f[blockIdx.z];
+    const int u0 = 4 * (blockIdx.x * OV_TX + threadIdx.x), v = blockIdx.y * OV_TY + threadIdx.y;
+    unsigned valid = 0, inside = 0;
+    if (u0 < c.W && v < c.H) {
+        const float4 z = __ldg(reinterpret_cast<const float4*>(depths + (size_t)F.frame * c.W * c.H +
+                                                                (size_t)v * c.W + u0));
+        const float uf = (float)u0, yn = ((float)v - c.cy) * c.ify;
+        overlap_pixel(F, c, uf, yn, z.x, valid, inside);
+        overlap_pixel(F, c, uf + 1.f, yn, z.y, valid, inside);
+        overlap_pixel(F, c, uf + 2.f, yn, z.z, valid, inside);
+        overlap_pixel(F, c, uf + 3.f, yn, z.w, valid, inside);
+    }
+    overlap_reduce(valid, inside, counts);
+}
+
+// Any width: one pixel per thread.
+__global__ void __launch_bounds__(OV_TX* OV_TY) overlap_kernel_any(const float* __restrict__ depths,
+                                                                   const OvArgs a, const OvCam c,
+                                                                   unsigned long long* counts) {
+    const OvFrame& F = a.f[blockIdx.z];
+    const int u = blockIdx.x * OV_TX + threadIdx.x, v = blockIdx.y * OV_TY + threadIdx.y;
+    unsigned valid = 0, inside = 0;
+    if (u < c.W && v < c.H)
+        overlap_pixel(F, c, (float)u, ((float)v - c.cy) * c.ify,
+                      __ldg(depths + (size_t)F.frame * c.W * c.H + (size_t)v * c.W + u), valid, inside);
+    overlap_reduce(valid, inside, counts);
+}
+
+// Pinned host copy of one driver step's counts, per device (allocated on first use,
+// held until exit); the mutex serialises KF_OVRLP calls that share it.
+struct OvHost {
+    std::mutex mu;
+    unsigned long long* counts = nullptr;
+} g_ov_host[64];
 
 bool pose_ok(const sc_pose& T) {
     for (int r = 0; r < 3; ++r)
@@ -115,8 +157,13 @@ int launch_overlap(const float* depths, const sc_pose* poses, const int* frames,
             F.frame = frames[i0 + i];
             F.pad = 0;
         }
-        const dim3 grid((K->width + OV_TX - 1) / OV_TX, (K->height + OV_TY - 1) / OV_TY, m);
-        overlap_kernel<<<grid, dim3(OV_TX, OV_TY), 0, s>>>(depths, a, c, counts + 2 * i0);
+        if (K->width % 4 == 0 && ((uintptr_t)depths & 15) == 0) {
+            const dim3 grid((K->width / 4 + OV_TX - 1) / OV_TX, (K->height + OV_TY - 1) / OV_TY, m);
+            overlap_kernel<<<grid, dim3(OV_TX, OV_TY), 0, s>>>(depths, a, c, counts + 2 * i0);
+        } else {
+            const dim3 grid((K->width + OV_TX - 1) / OV_TX, (K->height + OV_TY - 1) / OV_TY, m);
+            overlap_kernel_any<<<grid, dim3(OV_TX, OV_TY), 0, s>>>(depths, a, c, counts + 2 * i0);
+        }
         sc::count_launches(1);
         SC_CUDA(cudaGetLastError());
     }
@@ -183,9 +230,14 @@ extern "C" int sc_segment_keyframes(int32_t strategy, const double* params, cons
         }
     } else {
         const float thr = (float)params[0];
+        int dev = 0;
+        SC_CUDA(cudaGetDevice(&dev));
+        OvHost& oh = g_ov_host[dev & 63];
+        std::lock_guard<std::mutex> lock(oh.mu);
+        if (!oh.counts) SC_CUDA(cudaMallocHost((void**)&oh.counts, OV_SPEC * 2 * sizeof(unsigned long long)));
+        unsigned long long* hcounts = oh.counts;
         unsigned long long* dcounts = nullptr;
         SC_CUDA(cudaMallocAsync((void**)&dcounts, OV_SPEC * 2 * sizeof(unsigned long long), s));
-        unsigned long long hcounts[OV_SPEC * 2];
         int f = 1, rc = SC_OK;
         int frames[OV_SPEC];
         while (f < n && rc == SC_OK) {

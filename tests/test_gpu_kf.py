@@ -74,3 +74,26 @@ def test_kf_ovrlp_edge_cases():
         segment_keyframes(KF_OVRLP, (1.5,), [T] * 4, INTR, d)
     with pytest.raises(SurfcorrError):      # KF_OVRLP needs the depth frames
         segment_keyframes(KF_OVRLP, (0.5,), [T] * 4, INTR, None)
+
+
+def test_overlap_counts_ragged_width_matches_oracle():
+    # width 53: the one-pixel-per-thread kernel; a tilted plane with holes, frames
+    # translated and yawed against the keyframe
+    intr = (45.0, 45.0, 26.3, 18.1, 53, 37)
+    W, H = 53, 37
+    g = np.random.default_rng(11)
+    d = np.full((5, H, W), 1.6, np.float32) + np.linspace(0.0, 0.4, W, dtype=np.float32)[None, None, :]
+    d[g.random(d.shape) < 0.1] = 0.0
+    poses = []
+    for i in range(5):
+        a = math.radians(2.0 * i)
+        T = np.zeros((3, 4), np.float32)
+        T[:, :3] = [[math.cos(a), 0, math.sin(a)], [0, 1, 0], [-math.sin(a), 0, math.cos(a)]]
+        T[0, 3] = 0.05 * i
+        poses.append(T)
+    c = overlap_counts(torch.from_numpy(d).cuda(), poses, poses[1], intr).cpu().numpy()
+    for f in range(5):
+        valid, inside, marg = oracle.overlap(torch.from_numpy(d[f]), poses[f], poses[1], intr)
+        assert c[f, 0] == valid
+        assert abs(int(c[f, 1]) - inside) <= marg
+    assert c[1, 1] == c[1, 0]
