@@ -191,6 +191,40 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
     }
 }
 
+// One item's contribution to the 4 voxels, given their projection and texels.
+template <int SIGN>
+__device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], float aD[4],
+                                               int aW[4], int aC[4][3], bool& touched) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float d, eta;
+        if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
+            touched = true;
+            const uint32_t cw = t[j].y;
+            if (SIGN > 0) {
+                aD[j] = __fadd_rn(aD[j], d);
+                aW[j] += 1;
+                aC[j][0] += (int)(cw & 255u);
+                aC[j][1] += (int)((cw >> 8) & 255u);
+                aC[j][2] += (int)((cw >> 16) & 255u);
+            } else {
+                aD[j] = __fsub_rn(aD[j], d);
+                aW[j] -= 1;
+                aC[j][0] -= (int)(cw & 255u);
+                aC[j][1] -= (int)((cw >> 8) & 255u);
+                aC[j][2] -= (int)((cw >> 16) & 255u);
+            }
+        }
+    }
+}
+
+// Projection of the 4 voxels into item k and the texels (depth bits, RGBA8) they sample.
+__device__ __forceinline__ void net_delta_fetch(const NdCam& k, float vx, float vy, float vz, Proj4& P, uint2 t[4]) {
+    project4(k, vx, vy, vz, P);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
+}
+
 // Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over the items whose
 // bits are set in mask word `word` (items ibase .. ibase + 31 of the camera table
 // `cams`), with sign SIGN (-1: old bits, de-integration; +1: new bits).  Weights and
@@ -200,35 +234,12 @@ template <int SIGN>
 __device__ __forceinline__ void net_delta_word(const NdCam* cams, uint32_t word, float vx, float vy, float vz,
                                                float aD[4], int aW[4], int aC[4][3], bool& touched) {
     while (word) {
-        const int b = __ffs(word) - 1;
+        const int b0 = __ffs(word) - 1;
         word &= word - 1;
-        const NdCam& k = cams[b];
-        Proj4 P;
-        project4(k, vx, vy, vz, P);
-        uint2 t[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            float d, eta;
-            if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
-                touched = true;
-                const uint32_t cw = t[j].y;
-                if (SIGN > 0) {
-                    aD[j] = __fadd_rn(aD[j], d);
-                    aW[j] += 1;
-                    aC[j][0] += (int)(cw & 255u);
-                    aC[j][1] += (int)((cw >> 8) & 255u);
-                    aC[j][2] += (int)((cw >> 16) & 255u);
-                } else {
-                    aD[j] = __fsub_rn(aD[j], d);
-                    aW[j] -= 1;
-                    aC[j][0] -= (int)(cw & 255u);
-                    aC[j][1] -= (int)((cw >> 8) & 255u);
-                    aC[j][2] -= (int)((cw >> 16) & 255u);
-                }
-            }
-        }
+        Proj4 P0;
+        uint2 t0[4];
+        net_delta_fetch(cams[b0], vx, vy, vz, P0, t0);
+        net_delta_item<SIGN>(cams[b0], P0, t0, aD, aW, aC, touched);
     }
 }
 
