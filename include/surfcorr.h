@@ -183,6 +183,13 @@ int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int
  * RGB-D format).  raw and depth device [n], 16-byte aligned.  Asynchronous. */
 int sc_depth_from_u16(const uint16_t* raw, int64_t n, float scale, float* depth, sc_stream stream);
 
+/* Packed 8-bit RGB (3 bytes a pixel, the usual colour-sensor format) to the RGBA8
+ * layout the volume reads: rgba[4i .. 4i+2] = rgb[3i .. 3i+2], rgba[4i+3] = 255.
+ * Sending colour as RGB moves a quarter fewer bytes over the host link.  rgb device
+ * [n_pixels][3], 4-byte aligned; rgba device [n_pixels][4], 16-byte aligned; the two
+ * must not overlap.  n_pixels >= 0.  Asynchronous. */
+int sc_rgba_from_rgb(const uint8_t* rgb, int64_t n_pixels, uint8_t* rgba, sc_stream stream);
+
 /* ------------------------------------------------- colour keyframe fusion ---- */
 
 /* Device workspace sc_fuse_colour_keyframes needs for width x height images:

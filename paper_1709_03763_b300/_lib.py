@@ -95,6 +95,7 @@ SIGNATURES = {
     "sc_fuse_keyframes": (c_i32, [c_p, P(Pose), P(c_i32), c_i32, P(Pose), c_i32, P(Intrinsics), P(FusionParams),
                                   c_p, c_p, c_p]),
     "sc_depth_from_u16": (c_i32, [c_p, c_i64, c_f, c_p, c_p]),
+    "sc_rgba_from_rgb": (c_i32, [c_p, c_i64, c_p, c_p]),
     "sc_colour_workspace_bytes": (c_u64, [c_i32, c_i32]),
     "sc_fuse_colour_keyframes": (c_i32, [c_p, c_p, P(Pose), P(c_i32), c_i32, c_p, P(Pose), c_i32, P(Intrinsics),
                                          P(ColourParams), c_p, c_u64, c_p, c_p, c_p, c_p]),

@@ -312,3 +312,44 @@ extern "C" int sc_depth_from_u16(const uint16_t* raw, int64_t n, float scale, fl
     SC_CUDA(cudaGetLastError());
     return SC_OK;
 }
+
+// ------------------------------------------------------------ sensor colour ----
+
+namespace {
+
+// 4 pixels per thread: three 32-bit words of packed RGB in, one 16-byte RGBA store out
+// (little-endian: word 0 = r0 g0 b0 r1, word 1 = g1 b1 r2 g2, word 2 = b2 r3 g3 b3)
+__global__ void rgba_from_rgb_kernel(const uint8_t* __restrict__ rgb, size_t n, uint8_t* __restrict__ rgba) {
+    const size_t n4 = n / 4;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(rgb) + 3 * i;
+        const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2);
+        const uint32_t a = 0xff000000u;
+        reinterpret_cast<uint4*>(rgba)[i] = make_uint4((w0 & 0x00ffffffu) | a, (w0 >> 24) | ((w1 & 0xffffu) << 8) | a,
+                                                       (w1 >> 16) | ((w2 & 0xffu) << 16) | a, (w2 >> 8) | a);
+    }
+    for (size_t i = n4 * 4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        rgba[4 * i] = rgb[3 * i];
+        rgba[4 * i + 1] = rgb[3 * i + 1];
+        rgba[4 * i + 2] = rgb[3 * i + 2];
+        rgba[4 * i + 3] = 255u;
+    }
+}
+
+}  // namespace
+
+extern "C" int sc_rgba_from_rgb(const uint8_t* rgb, int64_t n_pixels, uint8_t* rgba, sc_stream stream) {
+    if (n_pixels < 0 || (n_pixels > 0 && (!rgb || !rgba))) return SC_ERR_INVALID_ARG;
+    if (((uintptr_t)rgb & 3) || ((uintptr_t)rgba & 15)) return SC_ERR_INVALID_ARG;
+    if (n_pixels == 0) return SC_OK;
+    const uintptr_t a0 = (uintptr_t)rgb, a1 = a0 + 3 * (uintptr_t)n_pixels;
+    const uintptr_t b0 = (uintptr_t)rgba, b1 = b0 + 4 * (uintptr_t)n_pixels;
+    if (a0 < b1 && b0 < a1) return SC_ERR_INVALID_ARG;  // overlapping buffers
+    int dev = 0, sms = 0;
+    SC_CUDA(cudaGetDevice(&dev));
+    SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    rgba_from_rgb_kernel<<<sms * 8, 256, 0, (cudaStream_t)stream>>>(rgb, (size_t)n_pixels, rgba);
+    sc::count_launches(1);
+    SC_CUDA(cudaGetLastError());
+    return SC_OK;
+}

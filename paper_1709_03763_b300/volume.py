@@ -450,6 +450,21 @@ def depth_from_u16(raw: torch.Tensor, scale: float, out: torch.Tensor | None = N
     return out
 
 
+def rgba_from_rgb(rgb: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Packed RGB8 images [..., 3] (uint8, CUDA) to RGBA8 [..., 4] with alpha 255."""
+    if rgb.dtype != torch.uint8 or rgb.shape[-1] != 3:
+        raise TypeError("rgb must be uint8 with a last dimension of 3")
+    if not rgb.is_cuda or not rgb.is_contiguous():
+        raise ValueError("rgb must be a contiguous CUDA tensor")
+    if out is None:
+        out = torch.empty((*rgb.shape[:-1], 4), dtype=torch.uint8, device=rgb.device)
+    if out.dtype != torch.uint8 or out.numel() != 4 * (rgb.numel() // 3) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous uint8 tensor of 4 bytes a pixel")
+    check(lib().sc_rgba_from_rgb(rgb.data_ptr(), rgb.numel() // 3, out.data_ptr(), _stream(stream)),
+          "sc_rgba_from_rgb")
+    return out
+
+
 def prepare_colour(frame_poses, frame_kf, kf_poses, width: int, height: int, device=None):
     """Argument arrays and the device workspace for fuse_colour_keyframes, built once
     and reusable (the workspace must not be shared by calls that overlap on the GPU)."""

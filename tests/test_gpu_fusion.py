@@ -73,3 +73,18 @@ def test_depth_from_u16_is_one_float_multiply():
     out = depth_from_u16(t, float(scale)).cpu().numpy()
     assert np.array_equal(out, raw.astype(np.float32) * scale)
     assert out[0] == 0.0 and abs(out[3] - 1.0) < 1e-6
+
+
+def test_rgba_from_rgb_expands_with_opaque_alpha():
+    from paper_1709_03763_b300 import SurfcorrError, rgba_from_rgb
+    g = np.random.default_rng(6)
+    for n in (0, 1, 3, 4, 7, 100003):   # empty, below one vector, ragged tail after the 4-wide body
+        rgb = torch.from_numpy(g.integers(0, 256, (n, 3), dtype=np.uint8)).cuda()
+        out = rgba_from_rgb(rgb).cpu().numpy()
+        ref = np.concatenate([rgb.cpu().numpy(), np.full((n, 1), 255, np.uint8)], axis=1)
+        assert np.array_equal(out, ref)
+    img = torch.from_numpy(g.integers(0, 256, (2, 48, 64, 3), dtype=np.uint8)).cuda()
+    assert np.array_equal(rgba_from_rgb(img)[..., :3].cpu().numpy(), img.cpu().numpy())
+    base = torch.zeros(4 * 11, dtype=torch.uint8, device="cuda")
+    with pytest.raises(SurfcorrError):   # input not 4-byte aligned: refused before any launch
+        rgba_from_rgb(base[1:1 + 30].view(10, 3), out=torch.empty((10, 4), dtype=torch.uint8, device="cuda"))
