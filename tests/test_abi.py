@@ -43,8 +43,25 @@ def test_library_exports_every_declared_symbol():
 def test_abi_version_and_status_strings():
     L = _lib.lib()
     assert L.sc_abi_version() == 1
-    for code in range(0, -10, -1):
+    for code in range(0, -12, -1):
         assert L.sc_status_string(code).decode() != "unknown status"
+
+
+def test_sensor_conversions_reject_bad_arguments_before_any_launch():
+    # the pointers below are never dereferenced: each call is refused by the host-side
+    # checks (or, for an empty input, returns before touching the device)
+    L = _lib.lib()
+    bad = _lib.SC_ERR_INVALID_ARG
+    assert L.sc_rgba_from_rgb(None, 5, None, None) == bad
+    assert L.sc_rgba_from_rgb(0x1000, -1, 0x2000, None) == bad
+    assert L.sc_rgba_from_rgb(0x1001, 5, 0x2000, None) == bad      # rgb not 4-byte aligned
+    assert L.sc_rgba_from_rgb(0x1000, 5, 0x2008, None) == bad      # rgba not 16-byte aligned
+    assert L.sc_rgba_from_rgb(0x1000, 16, 0x1010, None) == bad     # overlapping buffers
+    assert L.sc_rgba_from_rgb(None, 0, None, None) == 0              # empty: nothing to do
+    assert L.sc_depth_from_u16(0x1000, 8, 0.0, 0x2000, None) == bad  # scale must be positive
+    assert L.sc_depth_from_u16(0x1000, 8, float("nan"), 0x2000, None) == bad
+    assert L.sc_depth_from_u16(0x1002, 8, 0.001, 0x2000, None) == bad  # raw not 16-byte aligned
+    assert L.sc_depth_from_u16(None, 0, 0.001, None, None) == 0
 
 
 def test_struct_layouts():
