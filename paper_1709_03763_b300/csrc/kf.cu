@@ -1,5 +1,5 @@
 // Keyframe strategies (Section 4.2): the overlap ratio of KF_OVRLP on the GPU and
-// the host driver that groups frames into keyframes (KF_CONST, KF_DIST, KF_OVRLP).
+// the host loop that groups frames into keyframes (KF_CONST, KF_DIST, KF_OVRLP).
 //
 // overlap_kernel: one thread per 4 pixels of a row (one thread per pixel for widths
 // not a multiple of 4) of up to 64 frames per launch (grid z = frame):
@@ -9,7 +9,7 @@
 // reduced with warp shuffles and added with two 64-bit atomics per frame.
 //
 // KF_OVRLP is sequential by definition (the keyframe a frame is compared with depends
-// on the earlier decisions), so the driver evaluates the next 32 frames against the
+// on the earlier decisions), so the grouping loop evaluates the next 32 frames against the
 // current keyframe in one launch, reads the counts back (through a pinned buffer held
 // per device for the life of the process, so concurrent calls on one device take
 // turns), starts a keyframe at the first frame below the threshold and continues
@@ -23,7 +23,7 @@
 namespace {
 
 constexpr int OV_MAX_FRAMES = 64;
-constexpr int OV_SPEC = 32;  // frames evaluated per driver step
+constexpr int OV_SPEC = 32;  // frames evaluated per step of the grouping loop
 constexpr int OV_TX = 32, OV_TY = 8;
 
 struct OvFrame {
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(OV_TX* OV_TY) overlap_kernel_any(const float* 
     overlap_reduce(valid, inside, counts);
 }
 
-// Pinned host copy of one driver step's counts, per device (allocated on first use,
+// Pinned host copy of one grouping step's counts, per device (allocated on first use,
 // held until exit); the mutex serialises KF_OVRLP calls that share it.
 struct OvHost {
     std::mutex mu;
