@@ -9,11 +9,11 @@
 // reduced with warp shuffles and added with two 64-bit atomics per frame.
 //
 // KF_OVRLP is sequential by definition (the keyframe a frame is compared with depends
-// on the earlier decisions), so the grouping loop evaluates the next 32 frames against the
-// current keyframe in one launch, reads the counts back (through a pinned buffer held
-// per device for the life of the process, so concurrent calls on one device take
-// turns), starts a keyframe at the first frame below the threshold and continues
-// after it.
+// on the earlier decisions), so the grouping loop evaluates up to the next 32 frames
+// against the current keyframe in one launch (about 1.5x the last group's length),
+// reads the counts back (through a pinned buffer held per device for the life of the
+// process, so concurrent calls on one device take turns), starts a keyframe at the
+// first frame below the threshold and continues after it.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -240,8 +240,12 @@ extern "C" int sc_segment_keyframes(int32_t strategy, const double* params, cons
         SC_CUDA(cudaMallocAsync((void**)&dcounts, OV_SPEC * 2 * sizeof(unsigned long long), s));
         int f = 1, rc = SC_OK;
         int frames[OV_SPEC];
+        // frames evaluated in the next step: half again the last group's length (groups
+        // of a trajectory have similar lengths), at least 8, at most OV_SPEC; the
+        // decisions do not depend on it, only how much work is speculative
+        int spec = OV_SPEC;
         while (f < n && rc == SC_OK) {
-            const int m = std::min(OV_SPEC, n - f);
+            const int m = std::min(spec, n - f);
             for (int i = 0; i < m; ++i) frames[i] = f + i;
             rc = launch_overlap(depths, poses, frames, m, poses[kf], K, dcounts, s);
             if (rc != SC_OK) break;
@@ -259,12 +263,15 @@ extern "C" int sc_segment_keyframes(int32_t strategy, const double* params, cons
                 frame_kf[f + i] = groups - 1;
             }
             if (i < m) {  // frame f + i starts a keyframe; evaluate the frames after it
+                const int len = f + i - kf;
+                spec = std::max(8, std::min(OV_SPEC, len + len / 2));
                 kf = f + i;
                 ++groups;
                 frame_kf[kf] = groups - 1;
                 f = kf + 1;
             } else {
                 f += m;
+                spec = OV_SPEC;
             }
         }
         cudaFreeAsync(dcounts, s);
