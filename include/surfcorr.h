@@ -259,7 +259,9 @@ int sc_overlap_counts(const float* depths, const sc_pose* frame_poses, int32_t n
  * [n]) receives each frame's group, *n_keyframes their number.  depths (device
  * [n][H][W]) and intr are needed for SC_KF_OVRLP only (otherwise may be NULL).  KF_DIST
  * distances are computed in double from the float poses; KF_OVRLP ratios from integer
- * counts.  Synchronises the stream (KF_OVRLP: once per 32 frames evaluated). */
+ * counts.  Synchronises the stream (KF_OVRLP: once per group of 8 to 32 frames
+ * evaluated against the current keyframe).  Concurrent KF_OVRLP calls on one device
+ * share a pinned read-back buffer and take turns. */
 int sc_segment_keyframes(int32_t strategy, const double* params, const float* depths, const sc_pose* poses,
                          int32_t n, const sc_intrinsics* intr, int32_t* frame_kf, int32_t* n_keyframes,
                          sc_stream stream);
