@@ -108,3 +108,19 @@ def test_pose_exp_left_closed_forms():
     out = pose_exp_left(T, [0, 0, 0, *w])
     assert np.allclose(out[:, :3], Rw @ T[:, :3], atol=1e-6)
     assert np.allclose(out[:, 3], Rw @ T[:, 3], atol=1e-6)
+
+
+def test_sensor_conversion_wrappers_check_their_tensors():
+    # the binding refuses wrong dtypes, shapes and host tensors before calling the library
+    import torch
+    from paper_1709_03763_b300 import depth_from_u16, rgba_from_rgb
+    with pytest.raises(TypeError):
+        rgba_from_rgb(torch.zeros((4, 3), dtype=torch.int16))
+    with pytest.raises(TypeError):
+        rgba_from_rgb(torch.zeros((4, 4), dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        rgba_from_rgb(torch.zeros((4, 3), dtype=torch.uint8))          # host tensor
+    with pytest.raises(TypeError):
+        depth_from_u16(torch.zeros(8, dtype=torch.float32), 0.001)
+    with pytest.raises(ValueError):
+        depth_from_u16(torch.zeros(8, dtype=torch.int16), 0.001)        # host tensor
