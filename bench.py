@@ -65,7 +65,7 @@ VOXEL_BYTES_RW = 24             # D, W, RGBA8: 12 B read + 12 B written per voxe
 # (fusion) and keyframe images (batched allocation).
 SMS, SCHEDULERS, LANES = 148, 4, 32
 WINST_PER_UNIT = {"fuse_kernel": 1051372.0, "batch_alloc_kernel": 4839404.0}
-DRAM_PER_UNIT = {"fuse_kernel": 1.451e6, "batch_alloc_kernel": 1.285e6}
+DRAM_PER_UNIT = {"fuse_kernel": 1.497e6, "batch_alloc_kernel": 1.285e6}
 
 
 def parse():
