@@ -127,9 +127,22 @@ typedef struct {
 /* ---------------------------------------------------------------- volume ---- */
 
 /* Create an empty volume (Section 3 "SDF volume") on the current device.
- * All device memory is allocated here.  Returns SC_ERR_INVALID_ARG for a zero or
- * non-power-of-two bucket count, a non-positive voxel size or truncation, or
- * sizes out of range; SC_ERR_CUDA if allocation fails. */
+ * The hash table, voxel pool, block lists and counters are allocated here.  Other
+ * calls allocate too (and can return SC_ERR_CUDA when that fails):
+ *   - the first sc_reintegrate_batch / sc_integrate_keyframes / sc_autotune_batch
+ *     on a volume: the batch masks, union list and item tables; the packed
+ *     keyframe images again whenever the image size changes;
+ *   - sc_autotune_batch: a snapshot of the volume's used blocks, freed on return;
+ *   - the first sc_sdf_adjoint on a volume (and one with more keyframes than
+ *     before, at least 256): its item tables and accumulators;
+ *   - sc_overlap_counts / sc_segment_keyframes (a stream-ordered count buffer
+ *     per call), sc_stream_in_keyframes (a stream-ordered flag array per call),
+ *     sc_create_block_store, and the first sc_marching_cubes on a device (its
+ *     case table).
+ * sc_sdf_adjoint_noalloc allocates nothing.  Colour fusion uses a caller-owned
+ * workspace.  Returns SC_ERR_INVALID_ARG for a zero or non-power-of-two bucket
+ * count, a non-positive voxel size or truncation, or sizes out of range;
+ * SC_ERR_CUDA if allocation fails. */
 int sc_create_volume(const sc_volume_params* params, sc_volume** out);
 
 /* Free a volume and all its device memory (synchronises the device). */
@@ -464,7 +477,10 @@ int sc_sdf_loss(sc_volume* vol, const float* points, int64_t n, float lambda, fl
  * band, clamp) contribute nothing.
  *   kf_ids, poses  host [n]; depths host [n] array of device [H][W] pointers
  *   grad_xi        device [n][6] double, overwritten
- *   grad_depth     device [n][H][W] float or NULL, overwritten */
+ *   grad_depth     device [n][H][W] float or NULL, overwritten
+ * Its keyframe tables and accumulators belong to the volume (allocated by the
+ * first call, grown when n exceeds them), so calls on different volumes share no
+ * scratch; the call synchronises the stream before it rewrites the tables. */
 int sc_sdf_adjoint(sc_volume* vol, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
                    int32_t n, const sc_intrinsics* intr, const float* grad_D, double* grad_xi, float* grad_depth,
                    sc_stream stream);
@@ -472,17 +488,19 @@ int sc_sdf_adjoint(sc_volume* vol, const int32_t* kf_ids, const float* const* de
 /* sc_sdf_adjoint without any device-memory allocation by the library (the paper has
  * no counterpart; this is a deployment variant).  For callers that cannot call
  * cudaMalloc once running -- a real-time thread with a memory budget fixed at
- * start-up, code running while a CUDA graph is captured, an application whose
- * device memory belongs to another allocator.  Same arguments and results as
- * sc_sdf_adjoint (the caller still passes grad_D, grad_xi and grad_depth); its
- * keyframe table and accumulators live in a file-scope device array of about 60 KB
- * that every GPU loading the library holds until the process exits.
+ * start-up, an application whose device memory belongs to another allocator.  Same
+ * arguments and results as sc_sdf_adjoint (the caller still passes grad_D, grad_xi
+ * and grad_depth); its keyframe table and accumulators live in a file-scope device
+ * array of about 60 KB that every GPU loading the library holds until the process
+ * exits.
  *   - n <= 256 keyframes; more returns SC_ERR_CAPACITY and launches nothing.
+ *   - The volume's device must be the current device (else SC_ERR_INVALID_ARG).
  *   - The first call on a device looks up the array's device address (with that
- *     device current); make that first call before any stream capture.
+ *     device current; concurrent first calls are serialised by a lock); make that
+ *     first call before any stream capture.
  *   - All calls share the array: calls whose work overlaps on the GPU (other
- *     streams, other host threads, same device) race and give wrong results;
- *     serialise them.  Each call clears the accumulators it uses. */
+ *     streams, other host threads, other volumes on the same device) race and give
+ *     wrong results; serialise them.  Each call clears the accumulators it uses. */
 int sc_sdf_adjoint_noalloc(sc_volume* vol, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
                            int32_t n, const sc_intrinsics* intr, const float* grad_D, double* grad_xi,
                            float* grad_depth, sc_stream stream);

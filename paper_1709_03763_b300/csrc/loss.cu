@@ -13,7 +13,10 @@
 // gradient and into four pose moments (sum g, sum g q) from which the se(3)
 // gradient follows.  Lane values are float, warp and CTA partials double.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
+#include <new>
 
 #include "volume.cuh"
 
@@ -323,6 +326,11 @@ __global__ void adjoint_finalize_kernel(const AdjPose* poses, const double* acc,
     for (int j = 0; j < 3; ++j) g[3 + j] = bx[j] + tx[j] * A;
 }
 
+}  // namespace
+
+// Item and pose tables (pinned staging + device copies) and the double
+// accumulators of sc_sdf_adjoint, owned by one volume: calls on different volumes
+// share nothing.
 struct AdjScratch {
     int cap = 0;
     AdjItem* items_d = nullptr;
@@ -332,18 +340,27 @@ struct AdjScratch {
     AdjPose* poses_h = nullptr;
 };
 
-// one scratch per process and device is enough for the serialised calls on a volume
-AdjScratch g_adj[64];
+namespace {
 
-int adj_reserve(int device, int n) {
-    AdjScratch& A = g_adj[device & 63];
-    if (A.cap >= n) return SC_OK;
+void adj_free(AdjScratch& A) {
     if (A.items_d) cudaFree(A.items_d);
     if (A.poses_d) cudaFree(A.poses_d);
     if (A.acc_d) cudaFree(A.acc_d);
     if (A.items_h) cudaFreeHost(A.items_h);
     if (A.poses_h) cudaFreeHost(A.poses_h);
     A = AdjScratch();
+}
+
+// Room for n keyframes in the volume's adjoint tables (allocates on first use and
+// when n grows past the capacity, at least 256).
+int adj_reserve(sc_volume* V, int n) {
+    if (!V->adj) {
+        V->adj = new (std::nothrow) AdjScratch();
+        if (!V->adj) return SC_ERR_CUDA;
+    }
+    AdjScratch& A = *V->adj;
+    if (A.cap >= n) return SC_OK;
+    adj_free(A);
     const int cap = n < 256 ? 256 : n;
     SC_CUDA(cudaMalloc((void**)&A.items_d, cap * sizeof(AdjItem)));
     SC_CUDA(cudaMalloc((void**)&A.poses_d, cap * sizeof(AdjPose)));
@@ -355,6 +372,13 @@ int adj_reserve(int device, int n) {
 }
 
 }  // namespace
+
+void adj_destroy(sc_volume* V) {
+    if (!V->adj) return;
+    adj_free(*V->adj);
+    delete V->adj;
+    V->adj = nullptr;
+}
 
 extern "C" int sc_sdf_loss(sc_volume* V, const float* points, int64_t n, float lambda, float* grad_D, double* out,
                            sc_stream stream) {
@@ -387,9 +411,9 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
         if (V->nonresident[kf_ids[i]]) return SC_ERR_NOT_RESIDENT;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = adj_reserve(V->device, n);
+    int rc = adj_reserve(V, n);
     if (rc) return rc;
-    AdjScratch& A = g_adj[V->device & 63];
+    AdjScratch& A = *V->adj;
     // the pinned staging tables may still be read by a previous call's copies
     SC_CUDA(cudaStreamSynchronize(s));
     const size_t img = (size_t)K->width * K->height;
@@ -423,9 +447,9 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
 // The same adjoint kernels, with their keyframe table, pose table and double
 // accumulators in a file-scope device array instead of memory this library
 // allocates.  For callers that must not allocate device memory once running: a
-// real-time tracking thread whose memory budget is fixed at start-up, code that
-// runs while a CUDA graph is being captured (cudaMalloc is not allowed there), or
-// a host application whose device memory is owned by another allocator.
+// real-time tracking thread whose memory budget is fixed at start-up, or a host
+// application whose device memory is owned by another allocator (a pool that must
+// see every byte in use).
 
 namespace {
 
@@ -438,8 +462,10 @@ struct AdjStatic {
 };
 
 // host-side device addresses of the scratch array below, one per device (the
-// array's name in host code is a stand-in, not a device address)
-void* g_adj_static_ptr[64] = {nullptr};
+// array's name in host code is a stand-in, not a device address); looked up once
+// per device under the mutex, read without it afterwards
+std::atomic<void*> g_adj_static_ptr[64];
+std::mutex g_adj_static_mu;
 
 }  // namespace
 
@@ -458,16 +484,21 @@ extern "C" int sc_sdf_adjoint_noalloc(sc_volume* V, const int32_t* kf_ids, const
         if (!V->integrated[kf_ids[i]]) return SC_ERR_NOT_INTEGRATED;
         if (V->nonresident[kf_ids[i]]) return SC_ERR_NOT_RESIDENT;
     }
+    // the scratch array is per device: the volume's device must be the current one
     int dev = 0;
     SC_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return SC_ERR_INVALID_ARG;
-    if (!g_adj_static_ptr[dev]) {
+    if (dev != V->device || dev < 0 || dev >= 64) return SC_ERR_INVALID_ARG;
+    void* addr = g_adj_static_ptr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         // once per device, with that device current
-        void* p = nullptr;
-        SC_CUDA(cudaGetSymbolAddress(&p, g_adj_static));
-        g_adj_static_ptr[dev] = p;
+        std::lock_guard<std::mutex> lock(g_adj_static_mu);
+        addr = g_adj_static_ptr[dev].load(std::memory_order_relaxed);
+        if (!addr) {
+            SC_CUDA(cudaGetSymbolAddress(&addr, g_adj_static));
+            g_adj_static_ptr[dev].store(addr, std::memory_order_release);
+        }
     }
-    AdjStatic* S = static_cast<AdjStatic*>(g_adj_static_ptr[dev]);
+    AdjStatic* S = static_cast<AdjStatic*>(addr);
     cudaStream_t s = (cudaStream_t)stream;
     // host tables in pageable memory: cudaMemcpyAsync from pageable memory returns
     // once the data has been staged, so the buffers can be reused at once

@@ -329,6 +329,7 @@ bool pow2(uint32_t x) { return x && !(x & (x - 1)); }
 }  // namespace
 
 void batch_destroy(sc_volume* V);  // batch.cu
+void adj_destroy(sc_volume* V);    // loss.cu
 
 extern "C" int sc_abi_version(void) { return SC_ABI_VERSION; }
 
@@ -368,6 +369,7 @@ extern "C" int sc_create_volume(const sc_volume_params* p, sc_volume** out) {
     V->call_id = 0;
     V->last_stream = nullptr;
     V->batch = nullptr;
+    V->adj = nullptr;
     V->bcfg = sc_batch_config{4, 8, 1};
     V->prof_on = false;
     V->prof_dev = nullptr;
@@ -455,6 +457,7 @@ extern "C" int sc_destroy_volume(sc_volume* V) {
     if (!V) return SC_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
     batch_destroy(V);
+    adj_destroy(V);
     free_all(V);
     delete V;
     return SC_OK;

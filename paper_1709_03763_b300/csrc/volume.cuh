@@ -6,6 +6,7 @@
 #include "common.cuh"
 
 struct BatchState;  // batched re-integration state (batch.cu)
+struct AdjScratch;  // adjoint item tables and accumulators (loss.cu)
 
 struct sc_volume {
     sc_volume_params p;
@@ -37,6 +38,7 @@ struct sc_volume {
     uint32_t* h_word;   // pinned scratch
     uint64_t device_bytes;
     BatchState* batch;
+    AdjScratch* adj;  // allocated by the first sc_sdf_adjoint call, grown on demand
     sc_batch_config bcfg;
     // profiling
     bool prof_on;
