@@ -83,6 +83,11 @@ def _declare(L):
     L.or_grad.restype = _i
     L.or_loss_perturbed.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _l, _d]
     L.or_loss_perturbed.restype = _d
+    L.or_vol_stats.argtypes = [_p, _p]
+    L.or_adjoint.argtypes = [_p, _i, _p, _p, _p, _d, _d, _d, _d, _i, _i, _l, _p, _p, _p, _p, _p, _p]
+    L.or_adjoint.restype = _i
+    L.or_adjoint_functional.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _l, _p, _p]
+    L.or_adjoint_functional.restype = _d
     L.or_colour_unsharp.argtypes = [_p, _i, _i, _p]
     L.or_colour_blurriness.argtypes = [_p, _i, _i]
     L.or_colour_blurriness.restype = _d
@@ -418,6 +423,47 @@ class Volume:
         fx, fy, cx, cy = _intr(intr)
         return lib().or_loss_perturbed(self.h, kf_id, _ptr(d), _ptr(p), fx, fy, cx, cy, W, H, _ptr(x),
                                        int(pix), float(dz), _ptr(pts), len(pts), lam)
+
+
+    def stats(self):
+        """(voxel samples in front of the camera, samples with a value-changing marginal
+        decision) over every integration and de-integration of this volume."""
+        out = np.zeros(2, np.int64)
+        lib().or_vol_stats(self.h, _ptr(out))
+        return int(out[0]), int(out[1])
+
+    def adjoint(self, kf_ids, depths, poses, intr, g_coords, g_vals, with_depth=True):
+        """Vector-Jacobian product for the cotangent G = dL/dD given per block (g_coords
+        [n,3] int32, g_vals [n,512]): (grad_xi [K,6], grad_depth [K,H,W], err_xi, err_depth),
+        the errors bounding what a float32 evaluation of the marginal decisions may change."""
+        ids = np.ascontiguousarray(kf_ids, np.int32)
+        d = _f32(_np(depths))
+        K, H, W = d.shape
+        p = _f32(_np(poses)).reshape(K, 12)
+        gc = np.ascontiguousarray(g_coords, np.int32)
+        gv = np.ascontiguousarray(g_vals, np.float64)
+        gx, ex = np.zeros((K, 6)), np.zeros((K, 6))
+        gd = np.zeros((K, H, W)) if with_depth else None
+        ed = np.zeros((K, H, W)) if with_depth else None
+        fx, fy, cx, cy = _intr(intr)
+        rc = lib().or_adjoint(self.h, K, _ptr(ids), _ptr(d), _ptr(p), fx, fy, cx, cy, W, H, len(gc), _ptr(gc),
+                              _ptr(gv), _ptr(gx), _ptr(gd), _ptr(ex), _ptr(ed))
+        if rc:
+            raise ValueError("keyframe not integrated")
+        return gx, gd, ex, ed
+
+    def adjoint_functional(self, kf_id, depth, pose, intr, xi, g_coords, g_vals, pix=-1, dz=0.0):
+        """sum_v G(v) D(v) with kf_id's contribution at exp(xi^) T and depth + dz at pix, minus
+        its unperturbed value, decisions frozen (for central differences of adjoint())."""
+        d = _f32(_np(depth))
+        H, W = d.shape
+        p = _f32(_np(pose)).reshape(12)
+        x = np.ascontiguousarray(xi, np.float64).reshape(6)
+        gc = np.ascontiguousarray(g_coords, np.int32)
+        gv = np.ascontiguousarray(g_vals, np.float64)
+        fx, fy, cx, cy = _intr(intr)
+        return lib().or_adjoint_functional(self.h, kf_id, _ptr(d), _ptr(p), fx, fy, cx, cy, W, H, _ptr(x), int(pix),
+                                           float(dz), len(gc), _ptr(gc), _ptr(gv))
 
 
 def pose_distance(T0, T1) -> float:

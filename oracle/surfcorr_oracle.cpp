@@ -290,6 +290,9 @@ struct Vol {
     // blocks some integration reached only marginally (a float32 implementation
     // may allocate or update them where this reference does not)
     std::unordered_map<int64_t, uint8_t> ghosts;
+    // voxel samples taken by integrations and de-integrations: projected (in front of
+    // the camera) and with a value-changing marginal decision
+    long n_proj = 0, n_vmarg = 0;
 };
 
 // Closed segment [q0, q1] against the closed box [lo, hi]^3 (slab test).
@@ -370,7 +373,11 @@ void allocation_set(const Vol& V, const float* depth, const Intr& K, const Pose&
 // Returns true when the voxel is updated; fills d, c and the decision margins.
 struct Sample {
     bool upd;
-    bool marginal;
+    bool marginal;  // any decision within its margin (value-changing ones or the clamp kink)
+    bool vmarg;     // a decision within its margin that can change W, D or C: the pixel
+                    // rounding, the camera plane or the band edge (not the clamp kink,
+                    // where d = min(eta, mu) is continuous)
+    bool proj;      // in front of the camera: the nearest-pixel decision was taken
     bool clamped;
     long pix;
     double d;
@@ -384,6 +391,8 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     Sample S{};
     S.upd = false;
     S.marginal = false;
+    S.vmarg = false;
+    S.proj = false;
     S.pix = -1;
     S.pv[0] = ix * V.s;
     S.pv[1] = iy * V.s;
@@ -391,12 +400,13 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     double pc[3];
     apply_inv(T, S.pv, pc);
     S.zc = pc[2];
-    if (std::fabs(pc[2]) < g_tau_m) S.marginal = true;
+    if (std::fabs(pc[2]) < g_tau_m) S.marginal = S.vmarg = true;
     if (!(pc[2] > 0.0)) return S;
+    S.proj = true;
     double mu_, mv_;
     long px = round_half_up(K.fx * pc[0] / pc[2] + K.cx, &mu_);
     long py = round_half_up(K.fy * pc[1] / pc[2] + K.cy, &mv_);
-    if (mu_ < g_tau_px || mv_ < g_tau_px) S.marginal = true;
+    if (mu_ < g_tau_px || mv_ < g_tau_px) S.marginal = S.vmarg = true;
     S.pix = std::min(std::max(py, 0L), (long)K.H - 1) * K.W + std::min(std::max(px, 0L), (long)K.W - 1);
     if (px < 0 || px >= K.W || py < 0 || py >= K.H) return S;
     long q = py * K.W + px;
@@ -404,7 +414,7 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     if (!(Z > 0.0)) return S;
     // projective distance along the camera z axis (Section 4.3): eta = Z(x) - z_c
     double eta = Z - pc[2];
-    if (std::fabs(eta + V.mu) < g_tau_m) S.marginal = true;
+    if (std::fabs(eta + V.mu) < g_tau_m) S.marginal = S.vmarg = true;
     if (eta < -V.mu) return S;  // far behind the observed surface: not updated
     S.upd = true;
     S.pix = q;
@@ -437,7 +447,8 @@ void update_blocks(Vol& V, const std::vector<int64_t>& blocks, const std::vector
         auto it = V.blocks.find(blocks[b]);
         if (it != V.blocks.end()) ptrs[b] = &it->second;
     }
-#pragma omp parallel for schedule(dynamic, 16)
+    long n_proj = 0, n_vmarg = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : n_proj, n_vmarg)
     for (long b = 0; b < (long)blocks.size(); ++b) {
         Block* blk = ptrs[b];
         if (!blk) continue;
@@ -450,7 +461,10 @@ void update_blocks(Vol& V, const std::vector<int64_t>& blocks, const std::vector
                 for (int lx = 0; lx < BS; ++lx) {
                     int vi = lx + BS * ly + BS * BS * lz;
                     Sample S = sample_voxel(V, depth, rgba, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
-                    if (S.marginal) blk->vflag[vi] = 1;
+                    // vflag counts the value-changing marginal decisions (saturating)
+                    if (S.vmarg && blk->vflag[vi] < 255) ++blk->vflag[vi];
+                    n_proj += S.proj;
+                    n_vmarg += S.vmarg;
                     if (!S.upd) continue;
                     const double w = 1.0;
                     double Wv = blk->W[vi];
@@ -477,6 +491,8 @@ void update_blocks(Vol& V, const std::vector<int64_t>& blocks, const std::vector
                     }
                 }
     }
+    V.n_proj += n_proj;
+    V.n_vmarg += n_vmarg;
 }
 
 }  // namespace
@@ -1056,6 +1072,192 @@ extern "C" double or_loss_perturbed(void* vol, int kf_id, const float* depth, co
     DOverlay ov;
     ov.over = &over;
     return loss_impl(V, ov, pts, n, lambda, nullptr, nullptr);
+}
+
+// Sample counts of all integrations and de-integrations so far: out[0] voxel
+// samples in front of the camera, out[1] samples with a value-changing marginal
+// decision (pixel rounding, camera plane, band edge).
+extern "C" void or_vol_stats(void* vol, long* out) {
+    const Vol& V = *(const Vol*)vol;
+    out[0] = V.n_proj;
+    out[1] = V.n_vmarg;
+}
+
+namespace {
+
+// Cotangent dL/dD given per block: coords [n][3], values [n][512].
+std::unordered_map<int64_t, const double*> cotangent_map(long n, const int32_t* coords, const double* vals) {
+    std::unordered_map<int64_t, const double*> G;
+    for (long i = 0; i < n; ++i) G[pack(coords[3 * i], coords[3 * i + 1], coords[3 * i + 2])] = vals + i * NV;
+    return G;
+}
+
+// The contribution status of voxel (ix, iy, iz) sampled at pixel q of keyframe depth:
+// 1 if updated without clamping (eta in [-mu, mu)), else 0.  Used for the other
+// outcomes of a marginal rounding.
+int status_at(const Vol& V, const float* depth, const Intr& K, double zc, long qx, long qy) {
+    if (!(zc > 0.0) || qx < 0 || qx >= K.W || qy < 0 || qy >= K.H) return 0;
+    const double Z = depth[qy * K.W + qx];
+    if (!(Z > 0.0)) return 0;
+    const double eta = Z - zc;
+    return (eta >= -V.mu && eta < V.mu) ? 1 : 0;
+}
+
+}  // namespace
+
+// Vector-Jacobian product of the keyframe integrations (the adjoint) for a given
+// cotangent G = dL/dD (per voxel) on this volume:
+//   D(v) = sum_k w_k d_k(v) / W(v)  =>  dL/dd_k(v) = G(v) w / W(v)  (w = 1)
+//   d_k = Z_k(x) - z_c when unclamped, else mu;  dd/dZ_k(x) = 1,
+//   dd/drho = r3, dd/domega = p_v x r3  (left perturbation, r3 = R e3),
+// summed over the voxels of each keyframe's stored block list (marginal
+// non-members excluded).  Voxels with W = 0 or G = 0 contribute nothing.
+// err_xi [K][6] / err_depth [K][H][W] (may be null) bound what a float32
+// evaluation may do differently: a marginal decision whose other outcome changes
+// whether the sample contributes adds |G/W| times the derivative magnitudes to
+// the pose budget; a contributing sample with a marginal rounding adds |G/W| to
+// the depth budget at its pixel and at each pixel across the tie (the pose
+// derivative does not depend on the pixel, the depth gradient does).
+extern "C" int or_adjoint(void* vol, int K_, const int* kf_ids, const float* depths, const float* poses, double fx,
+                          double fy, double cx, double cy, int W, int H, long n_g, const int32_t* g_coords,
+                          const double* g_vals, double* grad_xi, double* grad_depth, double* err_xi,
+                          double* err_depth) {
+    Vol& V = *(Vol*)vol;
+    const Intr K{fx, fy, cx, cy, W, H};
+    const auto G = cotangent_map(n_g, g_coords, g_vals);
+    const long img = (long)W * H;
+    for (int k = 0; k < K_; ++k) {
+        auto it = V.touched.find(kf_ids[k]);
+        if (it == V.touched.end()) return -1;
+        double* gx = grad_xi + 6 * k;
+        double* ex = err_xi ? err_xi + 6 * k : nullptr;
+        double* gd = grad_depth ? grad_depth + k * img : nullptr;
+        double* ed = err_depth ? err_depth + k * img : nullptr;
+        for (int j = 0; j < 6; ++j) {
+            gx[j] = 0.0;
+            if (ex) ex[j] = 0.0;
+        }
+        for (long q = 0; gd && q < img; ++q) gd[q] = 0.0;
+        for (long q = 0; ed && q < img; ++q) ed[q] = 0.0;
+        const Pose T = pose_from(poses + 12 * k);
+        const float* depth = depths + k * img;
+        const double r3[3] = {T.R[0][2], T.R[1][2], T.R[2][2]};
+        const Touched& tl = it->second;
+        for (size_t b = 0; b < tl.blocks.size(); ++b) {
+            if (tl.marginal[b] == 2) continue;
+            auto gi = G.find(tl.blocks[b]);
+            if (gi == G.end()) continue;
+            const Block& blk = V.blocks.at(tl.blocks[b]);
+            long bx, by, bz;
+            unpack(tl.blocks[b], &bx, &by, &bz);
+            for (int vi = 0; vi < NV; ++vi) {
+                const double g = gi->second[vi];
+                if (g == 0.0 || !(blk.W[vi] > 0.0)) continue;
+                const long ix = bx * BS + vi % BS, iy = by * BS + (vi / BS) % BS, iz = bz * BS + vi / (BS * BS);
+                const Sample S = sample_voxel(V, depth, nullptr, K, T, ix, iy, iz);
+                const double gv = g / blk.W[vi];
+                const double* p = S.pv;
+                const double px_[3] = {p[1] * r3[2] - p[2] * r3[1], p[2] * r3[0] - p[0] * r3[2],
+                                       p[0] * r3[1] - p[1] * r3[0]};
+                const int base = (S.upd && !S.clamped) ? 1 : 0;
+                if (base) {
+                    for (int j = 0; j < 3; ++j) {
+                        gx[j] += gv * r3[j];
+                        gx[3 + j] += gv * px_[j];
+                    }
+                    if (gd) gd[S.pix] += gv;
+                }
+                if (!S.marginal) continue;
+                // the other outcomes a float32 evaluation may take
+                bool flips = false;
+                double pc[3];
+                apply_inv(T, S.pv, pc);
+                if (std::fabs(pc[2]) < g_tau_m) flips = true;  // camera plane
+                if (S.proj) {
+                    // S.pix is the nearest pixel clamped into the image; it is the
+                    // sampled pixel whenever the rounding put the voxel inside
+                    const double Z = depth[S.pix];
+                    const double eta = Z - pc[2];
+                    if (S.upd || Z > 0.0) {
+                        if (std::fabs(eta + V.mu) < g_tau_m) flips = true;  // band edge
+                        if (std::fabs(eta - V.mu) < g_tau_m) flips = true;  // clamp kink
+                    }
+                }
+                std::vector<long> alts;  // pixels across a marginal rounding tie
+                if (pc[2] > 0.0) {
+                    const double uf = K.fx * pc[0] / pc[2] + K.cx, vf = K.fy * pc[1] / pc[2] + K.cy;
+                    double mu_, mv_;
+                    const long qx = round_half_up(uf, &mu_), qy = round_half_up(vf, &mv_);
+                    const long ax = (uf + 0.5 - std::floor(uf + 0.5) < 0.5) ? qx - 1 : qx + 1;
+                    const long ay = (vf + 0.5 - std::floor(vf + 0.5) < 0.5) ? qy - 1 : qy + 1;
+                    const bool mu_m = mu_ < g_tau_px, mv_m = mv_ < g_tau_px;
+                    const long cand[3][2] = {{ax, qy}, {qx, ay}, {ax, ay}};
+                    const bool use[3] = {mu_m, mv_m, mu_m && mv_m};
+                    for (int c = 0; c < 3; ++c) {
+                        if (!use[c]) continue;
+                        const int st = status_at(V, depth, K, pc[2], cand[c][0], cand[c][1]);
+                        if (st != base) flips = true;
+                        if (st) alts.push_back(cand[c][1] * W + cand[c][0]);
+                    }
+                }
+                const double ag = std::fabs(gv);
+                if (flips && ex)
+                    for (int j = 0; j < 3; ++j) {
+                        ex[j] += ag * std::fabs(r3[j]);
+                        ex[3 + j] += ag * std::fabs(px_[j]);
+                    }
+                if (ed) {
+                    if (flips && base) ed[S.pix] += ag;
+                    if (!alts.empty()) {
+                        if (base) ed[S.pix] += ag;
+                        for (long q : alts) ed[q] += ag;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+// The functional L_G(xi, dz) = sum_v G(v) D(v) with keyframe kf_id's contribution
+// re-evaluated at exp(xi^) T and depth Z + dz at pixel pix (pix < 0: none), every
+// discrete decision frozen at the unperturbed state; its central differences
+// check or_adjoint.
+extern "C" double or_adjoint_functional(void* vol, int kf_id, const float* depth, const float* pose, double fx,
+                                        double fy, double cx, double cy, int W, int H, const double* xi, long pix,
+                                        double dz, long n_g, const int32_t* g_coords, const double* g_vals) {
+    Vol& V = *(Vol*)vol;
+    const Intr K{fx, fy, cx, cy, W, H};
+    auto it = V.touched.find(kf_id);
+    if (it == V.touched.end()) return NAN;
+    const auto G = cotangent_map(n_g, g_coords, g_vals);
+    const Pose T = pose_from(pose);
+    const Pose Tp = perturb(T, xi);
+    // sum over the keyframe's voxels of G (d(xi) - d(0)) w / W; the other keyframes'
+    // terms and this keyframe's unperturbed terms are constant and cancel in a
+    // central difference, so only the change is summed
+    double acc = 0.0;
+    const Touched& tl = it->second;
+    for (size_t b = 0; b < tl.blocks.size(); ++b) {
+        if (tl.marginal[b] == 2) continue;
+        auto gi = G.find(tl.blocks[b]);
+        if (gi == G.end()) continue;
+        const Block& blk = V.blocks.at(tl.blocks[b]);
+        long bx, by, bz;
+        unpack(tl.blocks[b], &bx, &by, &bz);
+        for (int vi = 0; vi < NV; ++vi) {
+            const double g = gi->second[vi];
+            if (g == 0.0 || !(blk.W[vi] > 0.0)) continue;
+            const Sample S = sample_voxel(V, depth, nullptr, K, T, bx * BS + vi % BS, by * BS + (vi / BS) % BS,
+                                          bz * BS + vi / (BS * BS));
+            if (!S.upd || S.clamped) continue;
+            double pc[3];
+            apply_inv(Tp, S.pv, pc);
+            const double Z = (double)depth[S.pix] + (S.pix == pix ? dz : 0.0);
+            acc += g * ((Z - pc[2]) - S.d) / blk.W[vi];
+        }
+    }
+    return acc;
 }
 
 // ============================================================================
