@@ -84,6 +84,7 @@ def _declare(L):
     L.or_loss_perturbed.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _p, _l, _d]
     L.or_loss_perturbed.restype = _d
     L.or_vol_stats.argtypes = [_p, _p]
+    L.or_vol_export_kink.argtypes = [_p, _p]
     L.or_adjoint.argtypes = [_p, _i, _p, _p, _p, _d, _d, _d, _d, _i, _i, _l, _p, _p, _p, _p, _p, _p]
     L.or_adjoint.restype = _i
     L.or_adjoint_functional.argtypes = [_p, _i, _p, _p, _d, _d, _d, _d, _i, _i, _p, _l, _d, _l, _p, _p]
@@ -424,6 +425,12 @@ class Volume:
         return lib().or_loss_perturbed(self.h, kf_id, _ptr(d), _ptr(p), fx, fy, cx, cy, W, H, _ptr(x),
                                        int(pix), float(dz), _ptr(pts), len(pts), lam)
 
+
+    def kink_flags(self) -> np.ndarray:
+        """[n,512] u8 clamp-kink marginal decisions per voxel, in export() block order."""
+        k = np.zeros((self.num_blocks(), 512), np.uint8)
+        lib().or_vol_export_kink(self.h, _ptr(k))
+        return k
 
     def stats(self):
         """(voxel samples in front of the camera, samples with a value-changing marginal

@@ -254,12 +254,14 @@ struct Block {
     double W[NV];
     double C[NV][3];
     uint8_t vflag[NV];
+    uint8_t kflag[NV];  // clamp-kink marginal decisions among the integrated samples
     uint8_t bflag;
     Block() {
         std::memset(D, 0, sizeof(D));
         std::memset(W, 0, sizeof(W));
         std::memset(C, 0, sizeof(C));
         std::memset(vflag, 0, sizeof(vflag));
+        std::memset(kflag, 0, sizeof(kflag));
         bflag = 0;
     }
 };
@@ -378,6 +380,7 @@ struct Sample {
                     // rounding, the camera plane or the band edge (not the clamp kink,
                     // where d = min(eta, mu) is continuous)
     bool proj;      // in front of the camera: the nearest-pixel decision was taken
+    bool kink;      // updated with eta within its margin of mu (the clamp decision)
     bool clamped;
     long pix;
     double d;
@@ -393,6 +396,7 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     S.marginal = false;
     S.vmarg = false;
     S.proj = false;
+    S.kink = false;
     S.pix = -1;
     S.pv[0] = ix * V.s;
     S.pv[1] = iy * V.s;
@@ -419,7 +423,7 @@ Sample sample_voxel(const Vol& V, const float* depth, const uint8_t* rgba, const
     S.upd = true;
     S.pix = q;
     S.clamped = !(eta < V.mu);
-    if (std::fabs(eta - V.mu) < g_tau_m) S.marginal = true;  // clamp kink (matters for gradients)
+    if (std::fabs(eta - V.mu) < g_tau_m) S.marginal = S.kink = true;  // clamp kink (matters for gradients)
     S.d = std::min(eta, V.mu);
     if (rgba) {
         for (int ch = 0; ch < 3; ++ch) S.c[ch] = (double)rgba[4 * q + ch];
@@ -461,8 +465,18 @@ void update_blocks(Vol& V, const std::vector<int64_t>& blocks, const std::vector
                 for (int lx = 0; lx < BS; ++lx) {
                     int vi = lx + BS * ly + BS * BS * lz;
                     Sample S = sample_voxel(V, depth, rgba, K, T, bx * BS + lx, by * BS + ly, bz * BS + lz);
-                    // vflag counts the value-changing marginal decisions (saturating)
-                    if (S.vmarg && blk->vflag[vi] < 255) ++blk->vflag[vi];
+                    // vflag counts the value-changing marginal decisions among the
+                    // samples currently integrated: Eq. 2 re-evaluates exactly the
+                    // samples of the integration it undoes, so whatever a float32
+                    // evaluation decided there it removes again (sticky once at 255)
+                    if (S.vmarg && blk->vflag[vi] < 255) {
+                        if (sign > 0) ++blk->vflag[vi];
+                        else if (blk->vflag[vi] > 0) --blk->vflag[vi];
+                    }
+                    if (S.kink && blk->kflag[vi] < 255) {
+                        if (sign > 0) ++blk->kflag[vi];
+                        else if (blk->kflag[vi] > 0) --blk->kflag[vi];
+                    }
                     n_proj += S.proj;
                     n_vmarg += S.vmarg;
                     if (!S.upd) continue;
@@ -611,6 +625,18 @@ extern "C" void or_vol_export(void* vol, int32_t* coords, double* D, double* Wt,
         if (bflag) bflag[i] = b.bflag | (V.ghosts.count(keys[i]) ? 1 : 0);
         if (vflag) std::memcpy(vflag + i * NV, b.vflag, NV);
     }
+}
+
+// Clamp-kink counts per voxel in the block order of or_vol_export: kflag [n][512].
+// The kink leaves D, W and C alone (d = min(eta, mu) is continuous) but decides
+// whether a sample has a derivative, so gradient comparisons need it.
+extern "C" void or_vol_export_kink(void* vol, uint8_t* kflag) {
+    Vol& V = *(Vol*)vol;
+    std::vector<int64_t> keys;
+    keys.reserve(V.blocks.size());
+    for (auto& kv : V.blocks) keys.push_back(kv.first);
+    std::sort(keys.begin(), keys.end());
+    for (size_t i = 0; i < keys.size(); ++i) std::memcpy(kflag + i * NV, V.blocks[keys[i]].kflag, NV);
 }
 
 // Blocks that some integration reached only marginally and that this reference

@@ -277,8 +277,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, SC_ADJ_MIN_BLOCKS) adjoint_kernel
                 const int ix = 8 * c.x + lx0 + j;
                 if (!decide(cam, P.ok[j], Z[j], P.pz[j], d, eta)) continue;
                 if (!(eta < cam.mu)) continue;  // clamped: no derivative
+                // a zero cotangent contributes nothing (and is skipped before the
+                // division, so an unobserved voxel with W = 0 never divides by it)
+                if (gj[j] == 0.f) continue;
                 const float gv = __fdiv_rn(gj[j], wj[j]);
-                if (gv == 0.f) continue;
                 if (it.grad_depth) atomicAdd(it.grad_depth + pix, gv);
                 a0 += gv;
                 a1 = fmaf(gv, __fsub_rn((float)(ix - cam.ti[0]), cam.tf[0]), a1);

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import compare_volumes, cuda, gpu_volume, oracle_volume, _keys
+from gpu_helpers import compare_volumes, cuda, flag_bound, gpu_volume, oracle_volume, _keys
 
 pytestmark = pytest.mark.gpu
 
@@ -42,7 +42,8 @@ def test_batch_matches_sequential_oracle(tinyg, colour):
     O.reintegrate_batch(ids, w.kf_depth[ids], w.kf_rgba[ids], w.kf_poses[ids], w.new_poses[ids], w.intr.as_tuple())
     # RGBA8: the batch rounds colour once per voxel, the sequential reference after every
     # keyframe operation; each rounding moves a channel by at most half a level
-    r = compare_volumes(V.extract(), O.export(), colour=colour, c_tol=0.5 if colour == "f32" else 2.0)
+    r = compare_volumes(V.extract(), O.export(), mu=w.trunc, max_flag_frac=flag_bound("tiny"), colour=colour,
+                        c_tol=0.5 if colour == "f32" else 2.0, label=f"tiny batch {colour}")
     # the new block lists equal the updated poses' allocation sets
     for k in ids:
         assert V.keyframe_blocks(k).numel() > 0
@@ -84,7 +85,7 @@ def test_batch_all_keyframes_and_identity_update(tinyg):
     new[w.update_ids] = w.new_poses[w.update_ids]
     V.reintegrate_batch(ids, D, C, w.kf_poses, new, w.intr)
     O.reintegrate_batch(ids, w.kf_depth, w.kf_rgba, w.kf_poses, new, w.intr.as_tuple())
-    compare_volumes(V.extract(), O.export())
+    compare_volumes(V.extract(), O.export(), mu=w.trunc, max_flag_frac=flag_bound("tiny"), label="tiny full update")
 
 
 def test_batch_then_reverse_batch_restores(tinyg):

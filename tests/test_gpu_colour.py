@@ -16,11 +16,20 @@ pytestmark = pytest.mark.gpu
 SLACK = 2e-3  # float32 bilinear arithmetic on values <= 255 (few ulp of 65280 / 256)
 
 
-def _compare(out_rgba, out_col, O, max_flag=0.02):
+# Flagged keyframe pixels (a sample footprint, occlusion test or the sample crossing half
+# the weight within its margin), as the oracle measures them: 0.28-0.33 % of the Kinect
+# keyframes' pixels, at most 0.71 % (6 of 851 pixels) in the ragged 37 x 23 groups; the
+# tests bound them at 1.5x that.
+FLAG_KINECT, FLAG_RAGGED = 1.5 * 0.0033, 1.5 * 0.0071
+
+
+def _compare(out_rgba, out_col, O, max_flag):
     """GPU keyframe colour vs the oracle's ColourFusion on the same inputs."""
     r = out_rgba.cpu().numpy()
     m = out_col.cpu().numpy().astype(np.float64)
     unfl = O.flag == 0
+    print(f"[colour parity] flagged {100 * (1.0 - unfl.mean()):.3f} % of keyframe pixels "
+          f"(bound {100 * max_flag:.3f} %)")
     assert 1.0 - unfl.mean() <= max_flag
     obs_o = O.nobs > 0
     assert np.array_equal((r[..., 3] == 255)[unfl], obs_o[unfl])
@@ -65,7 +74,7 @@ def test_colour_fusion_matches_oracle_kinect():
         O = oracle.fuse_colour(rgba[sl].cpu(), fd[sl].cpu(), poses[sl], kf_depth[k].cpu(), kf_poses[k], it)
         assert np.abs(wb[sl].cpu().numpy() - O.wb).max() <= 1e-6
         assert 0.0 < O.wb.min() and O.wb.max() < 1.0
-        n_cmp = _compare(out[k], col[k], O)
+        n_cmp = _compare(out[k], col[k], O, FLAG_KINECT)
         assert n_cmp > 0.5 * O.nobs.size
         # several frames observe most pixels
         assert np.median(O.nobs[O.nobs > 0]) >= kappa // 2
@@ -120,7 +129,7 @@ def test_colour_fusion_ragged_groups_and_chunks(counts):
             continue
         O = oracle.fuse_colour(rgba[sel], d[sel], fp[sel], kd[k], kp[k], it)
         assert np.abs(wb.cpu().numpy()[sel] - O.wb).max() <= 1e-6
-        compared += _compare(out[k], col[k], O, max_flag=0.1)
+        compared += _compare(out[k], col[k], O, FLAG_RAGGED)
     assert compared > 0
 
 

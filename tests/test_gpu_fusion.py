@@ -23,7 +23,10 @@ def test_fusion_matches_oracle():
     Zo, Wo, fl = oracle.fuse(d, poses, poses[0], synthetic.KINECT.as_tuple(), disc_rel=0.1)
     Zg, Wg = Zg.cpu().numpy().astype(np.float64), Wg.cpu().numpy().astype(np.float64)
     good = fl == 0
-    assert good.mean() > 0.95  # marginal roundings of 9 warped frames
+    # target pixels a marginal source may land on (the oracle flags x* and the pixel
+    # across the tie): 3.0 % for these 9 warped frames, bounded at 1.5x
+    print(f"[fusion parity] flagged {100 * (1 - good.mean()):.2f} % of keyframe pixels")
+    assert 1 - good.mean() <= 1.5 * 0.0301
     cov = good & (Wo > 0)
     assert cov.sum() > 0.5 * Wo.size
     assert np.all((Wg[good] > 0) == (Wo[good] > 0))

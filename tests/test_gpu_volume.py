@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import compare_volumes, cuda, gpu_volume, oracle_volume, _keys
+from gpu_helpers import compare_volumes, cuda, flag_bound, gpu_volume, oracle_volume, _keys
 
 pytestmark = pytest.mark.gpu
 
@@ -48,7 +48,8 @@ def test_integrate_all_keyframes_matches_oracle(tinyg, colour):
         V.integrate(k, D[k], C[k], w.intr, w.kf_poses[k])
         O.integrate(k, w.kf_depth[k], w.kf_rgba[k], it, w.kf_poses[k])
     V.check()
-    r = compare_volumes(V.extract(), O.export(), colour=colour, c_tol=0.5 if colour == "f32" else 0.0)
+    r = compare_volumes(V.extract(), O.export(), mu=w.trunc, max_flag_frac=flag_bound("tiny"), colour=colour,
+                        c_tol=0.5 if colour == "f32" else 0.0, label=f"tiny integrate {colour}")
     assert r["observed"] > 100000
 
 
@@ -68,7 +69,8 @@ def test_plain_deintegrate_reintegrate_matches_oracle(tinyg, colour):
         V.integrate(int(k), D[k], C[k], w.intr, w.new_poses[k])
         O.integrate(int(k), w.kf_depth[k], w.kf_rgba[k], it, w.new_poses[k])
     V.check()
-    compare_volumes(V.extract(), O.export(), colour=colour, c_tol=0.5 if colour == "f32" else 0.0)
+    compare_volumes(V.extract(), O.export(), mu=w.trunc, max_flag_frac=flag_bound("tiny"), colour=colour,
+                    c_tol=0.5 if colour == "f32" else 0.0, label=f"tiny plain update {colour}")
 
 
 def test_integrate_then_deintegrate_is_exact_inverse(tinyg):
@@ -120,7 +122,7 @@ def test_ragged_image_and_empty_keyframe(tiny):
     V.integrate(0, d.cuda(), c.cuda(), intr, w.kf_poses[2])
     O = oracle_volume(w)
     O.integrate(0, d, c, intr, w.kf_poses[2])
-    compare_volumes(V.extract(), O.export())
+    compare_volumes(V.extract(), O.export(), mu=w.trunc, max_flag_frac=flag_bound("tiny_ragged"), label="ragged")
     E = gpu_volume(w)
     E.integrate(0, torch.zeros_like(d).cuda(), c.cuda(), intr, w.kf_poses[2])
     E.check()
@@ -142,7 +144,8 @@ def test_integrate_many_matches_oracle(tinyg, colour):
         O.integrate(k, w.kf_depth[k], w.kf_rgba[k], it, w.kf_poses[k])
     V.check()
     # RGBA8: one rounding per voxel instead of one per keyframe
-    compare_volumes(V.extract(), O.export(), colour=colour, c_tol=0.5 if colour == "f32" else 2.0)
+    compare_volumes(V.extract(), O.export(), mu=w.trunc, max_flag_frac=flag_bound("tiny"), colour=colour,
+                    c_tol=0.5 if colour == "f32" else 2.0, label=f"tiny integrate_many {colour}")
     # and the keyframes are integrated: their lists de-integrate them again
     for k in range(10):
         V.deintegrate(k, D[k], C[k], w.intr, w.kf_poses[k])

@@ -39,6 +39,8 @@ def test_clamp_kink_is_not_counted_and_band_edge_is():
     obs = e.W > 0
     assert (obs & (iz == 28)).sum() > 100 and (obs & (iz == 36)).sum() > 100
     assert np.all(e.vflag[obs & (iz == 28)] == 0)
+    kf = V.kink_flags()
+    assert np.all(kf[obs & (iz == 28)] == 1) and np.all(kf[obs & (iz != 28)] == 0)
     assert np.all(e.vflag[obs & (iz == 36)] == 1)
     # layers 27 and 29: 30 i / k never puts u + 1/2 within the margin of a tie
     assert np.all(e.vflag[obs & ((iz == 27) | (iz == 29))] == 0)
@@ -48,6 +50,9 @@ def test_clamp_kink_is_not_counted_and_band_edge_is():
     assert np.array_equal(e2.vflag, 2 * e.vflag)
     n_proj, n_marg = V.stats()
     assert n_marg == int(e2.vflag.sum()) and n_proj > n_marg
+    # de-integration (Eq. 2) re-takes the same decisions and removes them again
+    V.deintegrate(1, plane_depth(INTR, z0), uniform_rgba(INTR, (5, 5, 5)), INTR, identity_pose())
+    assert np.array_equal(V.export().vflag, e.vflag)
 
 
 def test_marginal_rounding_rate_matches_the_margin():
