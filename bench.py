@@ -16,11 +16,14 @@ One step = one pass of the whole hot path over that input:
 value = 60 re-integrations / step time.  The JSON line also reports the update
 alone, batched (one graph) vs plain (120 per-keyframe calls), the roofline of the
 dominant kernel, the oracle on the host cores, clocks and the kernel count, and,
-under "rows", colour keyframe fusion of the 600 textured frames into the 60
-keyframes (its CUDA-event time, HBM roofline and the oracle beside it), Marching
-Cubes of the corrected volume, the KF_OVRLP keyframe grouping of the 600 frames and
-one streamed pose update of 10 keyframes (Eq. 3 vs the 10 most-moved), all measured
-outside the step.
+under "rows", the batching workload (2000 keyframes of 640x480 over a 30x20x3 m room
+grid; 10 pose updates of 10-200 keyframes, each batched as one graph launch against
+the plain per-keyframe path, with the net-delta kernel's HBM fraction), the batched
+forward + backward of 256 of those keyframes against per-keyframe calls, colour
+keyframe fusion of the 600 textured frames into the 60 keyframes (its CUDA-event
+time, HBM roofline and the oracle beside it), Marching Cubes of the corrected
+volume, the KF_OVRLP keyframe grouping of the 600 frames and one streamed pose
+update of 10 keyframes (Eq. 3 vs the 10 most-moved), all measured outside the step.
 
 --gpus N > 1 (under torchrun) runs N independent replicas (the path does not
 shard across GPUs in this build); value sums the replicas' throughput.
@@ -86,6 +89,8 @@ def parse():
                          "step's volume between cudaProfilerStart/Stop (for ncu) and exit")
     ap.add_argument("--keyframes", type=int, default=60, help="keyframes of the workload (small ncu cases)")
     ap.add_argument("--max-blocks", type=int, default=1 << 21)
+    ap.add_argument("--no-batching", action="store_true", help="skip the 2000-keyframe batching rows")
+    ap.add_argument("--batching-reps", type=int, default=10, help="replays per pose update in the batching rows")
     return ap.parse_args()
 
 
@@ -502,6 +507,198 @@ def cpu_baseline(n_kf, w, reps=3):
                       f"{reps} passes, {dt:.1f} s each"}
 
 
+def fp32_peak():
+    """Measured FP32 FMA rate of this GPU (lane FMAs per second, in T/s), or None."""
+    import ctypes
+    from paper_1709_03763_b300 import lib
+    r, ms = ctypes.c_double(0), ctypes.c_double(0)
+    rc = lib().sc_measure_fp32_rate(4096, ctypes.byref(r), ctypes.byref(ms), None)
+    return (r.value / 1e12, ms.value) if rc == 0 else (None, None)
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def _event_ms(fn):
+    """CUDA-event time of fn() on the current stream (host work inside fn included)."""
+    import torch
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def batching_rows(dev, hbm_peak, peak_kind, reps, cpu_sample, ws):
+    """The batching workload (2000 keyframes of 640x480 over a 30x20x3 m room grid, 1 cm
+    voxels, 2^22 buckets, RGBA8) and its 10 pose updates of a seeded 10-200 keyframes
+    chosen by largest pose change (Section 4.3): per update, the batched path (one graph
+    launch, autotuned on the first update) against the plain path (n de-integrations then
+    n integrations), each the median of `reps` replays that alternate the update and its
+    reverse (the reverse is an update of the same keyframes back to their former poses,
+    so every replay starts from a volume integrated at the poses it de-integrates);
+    then 256 of those keyframes as one batched forward + backward (one integration graph,
+    the loss at 1 M points, one adjoint launch) against 256 plain integrations, the loss
+    and 256 per-keyframe adjoint calls."""
+    import torch
+    from paper_1709_03763_b300 import Volume, make_intrinsics, make_pose, pose_distance, select_topm, synthetic
+    t0 = time.perf_counter()
+    w = synthetic.workload_batching(device=dev)
+    K = len(w.kf_poses)
+    D, C = w.kf_depth, w.kf_rgba
+    intr = make_intrinsics(w.intr)
+    V = Volume(w.voxel_size, w.trunc, w.n_buckets, colour="rgba8", max_blocks=1 << 21, max_keyframes=K,
+               max_blocks_per_keyframe=1 << 16, max_batch=256)
+    for s0 in range(0, K, 256):
+        ids = list(range(s0, min(K, s0 + 256)))
+        V.integrate_many(ids, [D[k] for k in ids], [C[k] for k in ids], w.kf_poses[ids], intr)
+    V.check()
+    counts = np.array([V.keyframe_blocks(k).numel() for k in range(K)])
+    setup_s = time.perf_counter() - t0
+    cur = w.kf_poses.copy()
+    ups, tuned = [], None
+    for u, upd in enumerate(w.updates):
+        tgt = upd["target_poses"]
+        dist = np.array([pose_distance(cur[k], tgt[k]) for k in range(K)])
+        ids = [int(i) for i in select_topm(dist, upd["n"])]
+        n = len(ids)
+        dl, cl = [D[k] for k in ids], [C[k] for k in ids]
+        fwd = V.prepare_batch(ids, dl, cl, cur[ids], tgt[ids])
+        rev = V.prepare_batch(ids, dl, cl, tgt[ids], cur[ids])
+        if tuned is None:
+            tuned, _ = V.autotune_batch(ids, dl, cl, cur[ids], tgt[ids], intr)
+        for _ in range(2):
+            V.reintegrate_batch(intr=intr, prepared=fwd)
+            V.reintegrate_batch(intr=intr, prepared=rev)
+        tb = [_event_ms(lambda r=r: V.reintegrate_batch(intr=intr, prepared=fwd if r % 2 == 0 else rev))
+              for r in range(reps)]
+        V.set_profiling(True)
+        V.reintegrate_batch(intr=intr, prepared=fwd)
+        pr = V.profile()
+        V.set_profiling(False)
+        V.reintegrate_batch(intr=intr, prepared=rev)
+        po = {k: make_pose(cur[k]) for k in ids}
+        pn = {k: make_pose(tgt[k]) for k in ids}
+        n_old = sum(V.keyframe_blocks(k).numel() for k in ids)
+
+        def plain(a, b):
+            for k in ids:
+                V.deintegrate(k, D[k], C[k], intr, a[k])
+            for k in ids:
+                V.integrate(k, D[k], C[k], intr, b[k])
+        plain(po, pn)
+        n_new = sum(V.keyframe_blocks(k).numel() for k in ids)
+        plain(pn, po)
+        tp = [_event_ms(lambda r=r: plain(po, pn) if r % 2 == 0 else plain(pn, po)) for r in range(reps)]
+        # advance to the updated poses (batched)
+        V.reintegrate_batch(intr=intr, prepared=fwd)
+        V.check()
+        cur[ids] = tgt[ids]
+        U, P = pr["batch_union_blocks"], pr["batch_pairs"]
+        net_bytes = U * 512 * VOXEL_BYTES_RW + n * IMG_BYTES + P * 4
+        plain_bytes = (n_old + n_new) * 512 * VOXEL_BYTES_RW + 2 * n * IMG_BYTES + (n_old + n_new) * 32
+        bm, pm = statistics.median(tb), statistics.median(tp)
+        ups.append({"n": n, "union_blocks": U, "pairs": P, "batched_ms": bm, "plain_ms": pm,
+                    "batched_reint_per_s": n / (bm / 1e3), "plain_reint_per_s": n / (pm / 1e3),
+                    "speedup": pm / bm, "net_delta_ms": pr["batch_net_ms"], "alloc_ms": pr["batch_alloc_ms"],
+                    "mark_ms": pr["batch_mark_ms"], "net_delta_bytes": net_bytes,
+                    "net_delta_hbm_frac": net_bytes / (pr["batch_net_ms"] / 1e3) / 1e9 / hbm_peak,
+                    "update_hbm_frac": net_bytes / (bm / 1e3) / 1e9 / hbm_peak,
+                    "plain_hbm_frac": plain_bytes / (pm / 1e3) / 1e9 / hbm_peak})
+    nsum = sum(x["n"] for x in ups)
+    tb_sum = sum(x["batched_ms"] for x in ups)
+    tp_sum = sum(x["plain_ms"] for x in ups)
+    nd_bytes = sum(x["net_delta_bytes"] for x in ups)
+    nd_ms = sum(x["net_delta_ms"] for x in ups)
+    row = {"workload": "batching: 2000 keyframes 640x480 over a 30x20x3 m room grid, voxel 1 cm, trunc 4 cm, "
+                       "2^22 buckets, RGBA8; 10 pose updates of 10-200 keyframes (largest pose change)",
+           "allocated_blocks": V.info()["allocated_blocks"],
+           "touched_blocks_per_keyframe": {"min": int(counts.min()), "median": int(np.median(counts)),
+                                           "max": int(counts.max())},
+           "batch_config": tuned, "replays": reps,
+           "batched_reint_per_s": ws * nsum / (tb_sum / 1e3), "plain_reint_per_s": ws * nsum / (tp_sum / 1e3),
+           "speedup": tp_sum / tb_sum,
+           "net_delta_hbm": {"achieved": nd_bytes / (nd_ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": nd_bytes / (nd_ms / 1e3) / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                             "min_frac": min(x["net_delta_hbm_frac"] for x in ups),
+                             "max_frac": max(x["net_delta_hbm_frac"] for x in ups)},
+           "update_hbm_frac": nd_bytes / (tb_sum / 1e3) / 1e9 / hbm_peak,
+           "updates": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in x.items()
+                        if k not in ("net_delta_bytes",)} for x in ups],
+           "setup_s": setup_s}
+
+    # ---- 256 keyframes: batched forward + backward vs per-keyframe
+    nfb = 256
+    ids = list(range(nfb))
+    dl, cl = [D[k] for k in ids], [C[k] for k in ids]
+    pts = torch.tensor(synthetic.surface_points(w.scene, N_POINTS, 5), dtype=torch.float32, device=dev)
+    prep_i = V.prepare_integrate_many(ids, dl, cl, w.kf_poses[ids])
+    prep_a = V.prepare_adjoint(ids, dl, w.kf_poses[ids])
+    prep_a1 = [V.prepare_adjoint([k], [D[k]], w.kf_poses[k:k + 1]) for k in ids]
+    pz = [make_pose(w.kf_poses[k]) for k in ids]
+    gD = V.grad_buffer()
+    lo = torch.empty(5, dtype=torch.float64, device=dev)
+    gx = torch.empty((nfb, 6), dtype=torch.float64, device=dev)
+    gd = torch.empty((nfb, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
+
+    def fb_batched():
+        V.reset()
+        V.integrate_many(intr=intr, prepared=prep_i)
+        V.sdf_loss(pts, LAMBDA, grad_D=gD, out=lo)
+        V.sdf_adjoint(intr=intr, grad_D=gD, prepared=prep_a, out=(gx, gd))
+
+    def fb_plain():
+        V.reset()
+        for k in ids:
+            V.integrate(k, D[k], C[k], intr, pz[k])
+        V.sdf_loss(pts, LAMBDA, grad_D=gD, out=lo)
+        for k in ids:
+            V.sdf_adjoint(intr=intr, grad_D=gD, prepared=prep_a1[k], out=(gx[k:k + 1], gd[k:k + 1]))
+    fb_batched()
+    fb_plain()
+    tfb = statistics.median(_event_ms(fb_batched) for _ in range(3))
+    tfp = statistics.median(_event_ms(fb_plain) for _ in range(3))
+    fb_row = {"workload": "256 keyframes of the batching workload: integration + loss at 1 M surface points + "
+                          "adjoint (pose and depth gradients)",
+              "batched_ms": tfb, "plain_ms": tfp, "batched_keyframes_per_s": ws * nfb / (tfb / 1e3),
+              "plain_keyframes_per_s": ws * nfb / (tfp / 1e3), "speedup": tfp / tfb,
+              "batched": "one integration graph launch, one loss, one adjoint launch for all 256",
+              "plain": "256 sc_integrate_keyframe calls, one loss, 256 sc_sdf_adjoint calls"}
+    V.close()
+    del w, D, C
+    torch.cuda.empty_cache()
+    return row, fb_row
+
+
+def oracle_batching_sample(n_kf=2):
+    """The oracle re-integrating n_kf keyframes of the batching workload's first update
+    (FP64, host cores): (seconds per re-integration, threads)."""
+    import oracle
+    from paper_1709_03763_b300 import synthetic
+    oracle.build()
+    w = synthetic.workload_batching(device="cpu", n_keyframes=n_kf, n_updates=1)
+    it = w.intr.as_tuple()
+    O = oracle.Volume(w.voxel_size, w.trunc, rgba8=True)
+    d, c = w.kf_depth.numpy(), w.kf_rgba.numpy()
+    for k in range(n_kf):
+        O.integrate(k, d[k], c[k], it, w.kf_poses[k])
+    tgt = w.updates[0]["target_poses"]
+    t0 = time.perf_counter()
+    for k in range(n_kf):
+        O.deintegrate(k, d[k], c[k], it, w.kf_poses[k])
+        O.integrate(k, d[k], c[k], it, tgt[k])
+    return (time.perf_counter() - t0) / n_kf, oracle.get_threads()
+
+
 def run_reference(args):
     """--impl reference: the FP64 oracle on the host cores (rank 0 only)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -730,43 +927,63 @@ def main():
                   "roofline": {"bound": "hbm", "achieved": col_gbs, "peak": hbm_peak, "unit": "GB/s",
                                "frac": col_gbs / hbm_peak, "traffic": None, "peak_kind": peak_kind,
                                "algorithmic_bytes": col_b}}
-    issue_peak = SMS * SCHEDULERS * LANES * sm_mhz * 1e6 / 1e12  # Tinst/s (lane instructions)
-    # per-step time of the big kernels: (ms per launch, launches per step, units per launch)
+    # ---- roofline of the dominant kernel: algorithmic bytes per launch / live CUDA-event
+    # time per launch, against the measured HBM copy peak; the instruction-issue view
+    # beside it uses the FP32 FMA rate measured here
+    fma_tps, _ = fp32_peak()
+    derived_issue = SMS * SCHEDULERS * LANES * sm_mhz * 1e6 / 1e12
+    H, Wd = w.intr.height, w.intr.width
+    f_launches = max(fprof["launches"], 1)
+    f_frames = fprof["frames"] / f_launches
+    n_img = P.K
     cand = {
-        "batch_alloc_kernel": (prof_int["batch_alloc_ms"], 2, P.K),
-        "fuse_kernel": (fprof["ms"] / max(fprof["launches"], 1), fprof["launches"],
-                        fprof["frames"] / max(fprof["launches"], 1)),
+        # per launch: (ms, launches per step, units per launch, algorithmic bytes per launch)
+        "fuse_kernel": (fprof["ms"] / f_launches, fprof["launches"], f_frames,
+                        f_frames * H * Wd * 4 + (f_frames / KAPPA) * IMG_BYTES),
+        "batch_alloc_kernel": (prof_int["batch_alloc_ms"], 2, n_img,
+                               n_img * H * Wd * 4 + prof_int["batch_pairs"] * 20),
+        "net_delta_kernel": (prof_upd["batch_net_ms"], 1, n_img,
+                             prof_upd["batch_union_blocks"] * 512 * VOXEL_BYTES_RW + n_img * IMG_BYTES
+                             + prof_upd["batch_pairs"] * 4),
     }
     dom = max(cand, key=lambda k: cand[k][0] * cand[k][1])
-    t_ms, _, units = cand[dom]
-    lane_inst = WINST_PER_UNIT[dom] * LANES * units
-    achieved = lane_inst / (t_ms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": issue_peak,
-                "unit": "Tinst/s (lane instructions issued)", "frac": achieved / issue_peak,
-                "traffic": DRAM_PER_UNIT[dom] * units,
-                "peak_derivation": f"{SMS} SMs x {SCHEDULERS} schedulers x {LANES} lanes x {sm_mhz:.0f} MHz "
-                                   "(SM clock sampled during the timed region)",
-                "traffic_note": "ncu dram__bytes_read+write of the 12-keyframe case, scaled by units",
-                "ms_per_launch": t_ms, "units_per_launch": units,
-                "others": {k: {"ms_per_launch": v[0], "launches_per_step": v[1]} for k, v in cand.items()}}
+    t_ms, _, units, abytes = cand[dom]
+    achieved = abytes / (t_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": peak_kind,
+                "traffic": (DRAM_PER_UNIT[dom] * units if dom in DRAM_PER_UNIT else None),
+                "traffic_note": "ncu dram__bytes_read+write per unit of the 12-keyframe capture, scaled to the "
+                                "launch's units",
+                "algorithmic_bytes_per_launch": abytes, "ms_per_launch": t_ms, "units_per_launch": units,
+                "kernels": {k: {"ms_per_launch": round(v[0], 5), "launches_per_step": v[1],
+                                "GBps": round(v[3] / (v[0] / 1e3) / 1e9, 1),
+                                "hbm_frac": round(v[3] / (v[0] / 1e3) / 1e9 / hbm_peak, 4)}
+                            for k, v in cand.items()}}
+    if dom in WINST_PER_UNIT:
+        lane_inst = WINST_PER_UNIT[dom] * LANES * units
+        ach_i = lane_inst / (t_ms / 1000.0) / 1e12
+        roofline["issue_view"] = {"bound": "alu", "achieved": ach_i, "unit": "T lane instructions/s",
+                                  "peak_measured_fp32_fma": fma_tps,
+                                  "frac_of_measured": ach_i / fma_tps if fma_tps else None,
+                                  "peak_derived": derived_issue, "frac_of_derived": ach_i / derived_issue,
+                                  "note": "warp instructions per unit from ncu smsp__inst_executed of the "
+                                          "12-keyframe capture; measured peak = sc_measure_fp32_rate"}
     # HBM view of the voxel-update kernels (algorithmic bytes / live time)
     hbm = {}
     if prof_plain["update_launches"]:
         nb = prof_plain["update_blocks"] / prof_plain["update_launches"]
         t = prof_plain["update_ms"] / prof_plain["update_launches"]
         b = nb * 512 * VOXEL_BYTES_RW + IMG_BYTES + nb * 32
-        hbm["update_kernel (plain integrate)"] = {"GBps": b / (t / 1e3) / 1e9, "frac": b / (t / 1e3) / 1e9 / hbm_peak,
-                                                  "bytes_per_launch": b, "ms_per_launch": t}
+        hbm["update_kernel (plain integrate)"] = {"frac": round(b / (t / 1e3) / 1e9 / hbm_peak, 4),
+                                                  "ms_per_launch": round(t, 5)}
     for name, pr in (("net_delta_kernel (pose update)", prof_upd), ("net_delta_kernel (integration)", prof_int)):
         if pr["batch_launches"]:
             u = pr["batch_union_blocks"] / pr["batch_launches"]
             t = pr["batch_net_ms"] / pr["batch_launches"]
-            b = u * 512 * VOXEL_BYTES_RW + P.K * 640 * 480 * 8 + pr["batch_pairs"] * 4 / pr["batch_launches"]
-            hbm[name] = {"GBps": b / (t / 1e3) / 1e9, "frac": b / (t / 1e3) / 1e9 / hbm_peak,
-                         "bytes_per_launch": b, "ms_per_launch": t, "union_blocks": u,
-                         "block_item_pairs": pr["batch_pairs"] / pr["batch_launches"]}
-    roofline["hbm_view"] = {"peak_GBps": hbm_peak, "peak_kind": peak_kind, "kernels": hbm}
-    prof = {"update": prof_upd, "integrate": prof_int, "plain_integrate": prof_plain, "fusion": fprof}
+            b = u * 512 * VOXEL_BYTES_RW + P.K * IMG_BYTES + pr["batch_pairs"] * 4 / pr["batch_launches"]
+            hbm[name] = {"frac": round(b / (t / 1e3) / 1e9 / hbm_peak, 4), "ms_per_launch": round(t, 5),
+                         "union_blocks": u, "block_item_pairs": pr["batch_pairs"] / pr["batch_launches"]}
+    roofline["hbm_view"] = hbm
 
     # ---- Marching Cubes of the corrected volume (after the step's pose update), measured
     # on its own: one call = the slot-count read-back, one kernel launch, count + status
@@ -859,9 +1076,34 @@ def main():
                            "note": "each frame's depth read once; the call synchronises once per 32 frames "
                                    "evaluated (the grouping is sequential), so it is latency-bound"}}
 
+    # ---- the batching workload (2000 keyframes, 10 pose updates of 10-200 keyframes) and the
+    # batched forward + backward of 256 of its keyframes, measured on their own
+    batch_row = fb_row = None
+    if not args.no_batching:
+        torch.cuda.empty_cache()
+        batch_row, fb_row = batching_rows(dev, hbm_peak, peak_kind, args.batching_reps, rank == 0, ws)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_sample, w)
+        cpu["cpu_model"] = cpu_model()
+        cpu["nproc"] = os.cpu_count()
+        # the same oracle on one thread, over a smaller sample
+        import oracle
+        nt = oracle.get_threads()
+        oracle.set_threads(1)
+        n1 = 2
+        last = oracle_reintegration.last_volume
+        dt1, _ = oracle_reintegration(n1, steps=1, w=w)
+        oracle_reintegration.last_volume = last
+        oracle.set_threads(nt)
+        cpu["single_thread"] = {"value": n1 / dt1, "unit": UNIT, "cores": 1,
+                                "sample": f"{n1} keyframe re-integrations of the same workload, FP64, {dt1:.1f} s"}
+        if batch_row is not None:
+            spr, thr = oracle_batching_sample(2)
+            batch_row["cpu_baseline"] = {"value": 1.0 / spr, "unit": "re-integrations/s", "cores": thr,
+                                         "kind": "oracle", "sample": "2 keyframe re-integrations of the batching "
+                                         f"workload's first update (640x480, 1 cm, RGBA8), FP64, {2 * spr:.1f} s"}
         kps, threads, dt = oracle_colour(w, P.kf_depth)
         colour_row["cpu_baseline"] = {"value": kps, "unit": "keyframes/s", "cores": threads, "kind": "oracle",
                                       "sample": f"colour fusion of 3 keyframes (10 frames each, 640x480), FP64, "
@@ -884,6 +1126,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clocks,
             "config": {"workload": "kinect-scale: 600 frames 640x480 (16-bit sensor depth, 1/5000 m) fused 10 per "
                                    "keyframe into 60 keyframes, "
                                    "voxel 1 cm, trunc 4 cm, 2^20 buckets, one pose update of all 60, "
@@ -898,19 +1142,16 @@ def main():
                     "pipelining": "raw depth and keyframe colour double-buffered: step k+1's inputs cross on "
                                   "a copy stream while step k computes; each step waits for them before it ends",
                     "serial_float_depth": {"ms_per_step": e2e_serial_ms, "h2d_bytes_per_step": h2d_serial}},
-            "gpu_launches": int(round(launches_per_step * args.steps)),
             "gpu_launches_per_step": launches_per_step,
             "update_only": {"batched_ms": upd_batched_ms, "plain_ms": upd_plain_ms,
                             "batched_reint_per_s": P.K / (upd_batched_ms / 1000.0),
                             "plain_reint_per_s": P.K / (upd_plain_ms / 1000.0),
                             "union_blocks": prof_upd["batch_union_blocks"], "pairs": prof_upd["batch_pairs"]},
-            "stage_ms": stage,
-            "profile": prof,
+            "stage_ms": {k: round(v, 4) for k, v in stage.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "rows": {"colour_fusion": colour_row, "marching_cubes": mc_row, "keyframe_strategy": kf_row,
-                     "streaming": stream_row},
-            "clocks": clocks,
+            "rows": {"batching": batch_row, "forward_backward_256": fb_row, "colour_fusion": colour_row,
+                     "marching_cubes": mc_row, "keyframe_strategy": kf_row, "streaming": stream_row},
             "setup_s": setup_s,
         }
         print(json.dumps(line), flush=True)

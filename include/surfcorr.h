@@ -562,6 +562,15 @@ int sc_set_retry_limit(sc_volume* vol, int32_t limit);
 
 int sc_abi_version(void);
 
+/* Measurement support (no counterpart in the paper): the FP32 FMA rate of the
+ * current device, from one full-occupancy launch in which every thread runs
+ * `iters` x 32 independent-chain FMAs (after one shorter warm-up launch), timed
+ * with CUDA events on `stream`.  *lane_fma_per_s receives lane FMAs per second
+ * (counting FMAs only; the loop's own instructions take a few further issue
+ * slots), *ms_out (may be NULL) the timed launch's milliseconds.  Synchronises;
+ * writes no memory.  1 <= iters <= 2^24, else SC_ERR_INVALID_ARG. */
+int sc_measure_fp32_rate(int32_t iters, double* lane_fma_per_s, double* ms_out, sc_stream stream);
+
 /* Number of kernels this library has launched in the process so far (a graph
  * launch counts its kernel nodes). */
 uint64_t sc_kernel_launches(void);

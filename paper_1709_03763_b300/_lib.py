@@ -130,6 +130,7 @@ SIGNATURES = {
     "sc_set_retry_limit": (c_i32, [c_p, c_i32]),
     "sc_abi_version": (c_i32, []),
     "sc_kernel_launches": (c_u64, []),
+    "sc_measure_fp32_rate": (c_i32, [c_i32, P(c_d), P(c_d), c_p]),
     "sc_set_profiling": (c_i32, [c_p, c_i32]),
     "sc_fusion_profile": (c_i32, [c_i32, P(c_d), P(c_i64), P(c_i64)]),
     "sc_get_profile": (c_i32, [c_p, P(Profile)]),
