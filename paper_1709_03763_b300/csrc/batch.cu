@@ -191,29 +191,67 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
     }
 }
 
+// Per-voxel net sums of one voxel group.  Colour channels and the weight are
+// integers; when fewer than PACK_MAX_ITEMS item bits are set on the block they are
+// kept packed, two 16-bit lanes per register biased by 2^15 (r | b << 16 and
+// g | count << 16): every partial sum then stays inside [0, 2^16) -- at most
+// 128 x 255 < 2^15 is added or subtracted -- so the lanes never carry or borrow into
+// each other and the packed sums equal the separate integer sums exactly.
+constexpr uint32_t PACK_BIAS = 0x80008000u;
+constexpr int PACK_MAX_ITEMS = 128;
+
+struct NdAcc {
+    float aD[4];      // sum of signed distances (float, in item order)
+    uint32_t rb[4];   // packed: r | b << 16   (packed mode)
+    uint32_t gw[4];   // packed: g | count << 16
+};
+
+struct NdAccWide {
+    float aD[4];
+    int aW[4];
+    int aC[4][3];
+};
+
 // One item's contribution to the 4 voxels, given their projection and texels.
 template <int SIGN>
-__device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], float aD[4],
-                                               int aW[4], int aC[4][3], bool& touched) {
+__device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], NdAcc& A,
+                                               bool& touched) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float d, eta;
         if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
             touched = true;
             const uint32_t cw = t[j].y;
+            const uint32_t rb = cw & 0x00FF00FFu;
+            const uint32_t gw = ((cw >> 8) & 0xFFu) | 0x10000u;
             if (SIGN > 0) {
-                aD[j] = __fadd_rn(aD[j], d);
-                aW[j] += 1;
-                aC[j][0] += (int)(cw & 255u);
-                aC[j][1] += (int)((cw >> 8) & 255u);
-                aC[j][2] += (int)((cw >> 16) & 255u);
+                A.aD[j] = __fadd_rn(A.aD[j], d);
+                A.rb[j] += rb;
+                A.gw[j] += gw;
             } else {
-                aD[j] = __fsub_rn(aD[j], d);
-                aW[j] -= 1;
-                aC[j][0] -= (int)(cw & 255u);
-                aC[j][1] -= (int)((cw >> 8) & 255u);
-                aC[j][2] -= (int)((cw >> 16) & 255u);
+                A.aD[j] = __fsub_rn(A.aD[j], d);
+                A.rb[j] -= rb;
+                A.gw[j] -= gw;
             }
+        }
+    }
+}
+
+template <int SIGN>
+__device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], NdAccWide& A,
+                                               bool& touched) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float d, eta;
+        if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
+            touched = true;
+            const uint32_t cw = t[j].y;
+            const int s = SIGN;
+            A.aD[j] = SIGN > 0 ? __fadd_rn(A.aD[j], d) : __fsub_rn(A.aD[j], d);
+            A.aW[j] += s;
+            A.aC[j][0] += s * (int)(cw & 255u);
+            A.aC[j][1] += s * (int)((cw >> 8) & 255u);
+            A.aC[j][2] += s * (int)((cw >> 16) & 255u);
         }
     }
 }
@@ -230,38 +268,167 @@ __device__ __forceinline__ void net_delta_fetch(const NdCam& k, float vx, float 
 // `cams`), with sign SIGN (-1: old bits, de-integration; +1: new bits).  Weights and
 // colours are integer sums (exactly the float sums of the same integers); distances
 // are summed in float in item order.
-template <int SIGN>
+template <int SIGN, typename Acc>
 __device__ __forceinline__ void net_delta_word(const NdCam* cams, uint32_t word, float vx, float vy, float vz,
-                                               float aD[4], int aW[4], int aC[4][3], bool& touched) {
+                                               Acc& A, bool& touched) {
     while (word) {
         const int b0 = __ffs(word) - 1;
         word &= word - 1;
         Proj4 P0;
         uint2 t0[4];
         net_delta_fetch(cams[b0], vx, vy, vz, P0, t0);
-        net_delta_item<SIGN>(cams[b0], P0, t0, aD, aW, aC, touched);
+        net_delta_item<SIGN>(cams[b0], P0, t0, A, touched);
     }
 }
 
 // All items of the slot's mask: old bits (first half of the words) subtract, new
 // bits add, in item order.
+template <typename Acc>
 __device__ __forceinline__ void net_delta_group(const NdCam* cams, int n, const int4 c, int lx0, int ly, int lz,
-                                                uint32_t mw0, uint32_t mw1, int mw, float aD[4], int aW[4],
-                                                int aC[4][3], bool& touched) {
+                                                uint32_t mw0, uint32_t mw1, int mw, Acc& A, bool& touched) {
     const int half = mw / 2;
     const float vx = (float)(8 * c.x + lx0), vy = (float)(8 * c.y + ly), vz = (float)(8 * c.z + lz);
     for (int w = 0; w < half; ++w) {
         const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        net_delta_word<-1>(cams + (w << 5), word, vx, vy, vz, aD, aW, aC, touched);
+        net_delta_word<-1>(cams + (w << 5), word, vx, vy, vz, A, touched);
     }
     for (int w = half; w < mw; ++w) {
         const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        net_delta_word<1>(cams + n + ((w - half) << 5), word, vx, vy, vz, aD, aW, aC, touched);
+        net_delta_word<1>(cams + n + ((w - half) << 5), word, vx, vy, vz, A, touched);
     }
 }
 
-// Work unit u = (union block u / 4, voxel group u % 4): one warp, 128 voxels, four
-// per lane.  Units come from a queue in chunks of `grab`.
+// Net weight and colour sums of voxel j as integers.
+__device__ __forceinline__ void nd_unpack(const NdAcc& A, int j, int& w, int c[3]) {
+    w = (int)(A.gw[j] >> 16) - 32768;
+    c[0] = (int)(A.rb[j] & 0xFFFFu) - 32768;
+    c[1] = (int)(A.gw[j] & 0xFFFFu) - 32768;
+    c[2] = (int)(A.rb[j] >> 16) - 32768;
+}
+__device__ __forceinline__ void nd_unpack(const NdAccWide& A, int j, int& w, int c[3]) {
+    w = A.aW[j];
+    c[0] = A.aC[j][0];
+    c[1] = A.aC[j][1];
+    c[2] = A.aC[j][2];
+}
+
+__device__ __forceinline__ void nd_init(NdAcc& A) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        A.aD[j] = 0.f;
+        A.rb[j] = PACK_BIAS;
+        A.gw[j] = PACK_BIAS;
+    }
+}
+__device__ __forceinline__ void nd_init(NdAccWide& A) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        A.aD[j] = 0.f;
+        A.aW[j] = 0;
+        A.aC[j][0] = A.aC[j][1] = A.aC[j][2] = 0;
+    }
+}
+
+// The read-modify-write of one voxel group (4 voxels per lane) with its net sums:
+// D' = (D W + sum d) / W', W' = W + sum w, colour likewise (W' = 0 resets the voxel).
+// RGBA8: Dv, Wv, Cv were loaded before the samples (zero for a fresh block).
+template <bool F32, typename Acc>
+__device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_t off, int lane, int g, bool fresh,
+                                         const Acc& A, float4 Dv, float4 Wv, uint4 Cv) {
+    float aW[4], aC[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        int w, c[3];
+        nd_unpack(A, j, w, c);
+        aW[j] = (float)w;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) aC[j][ch] = (float)c[ch];
+    }
+    float* Dp = &Dv.x;
+    float* Wp = &Wv.x;
+    float Wn[4];
+    bool nz[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Wn[j] = __fadd_rn(Wp[j], aW[j]);
+        nz[j] = Wn[j] != 0.f;
+    }
+    if (F32) {
+        const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float4 Cf = fresh ? make_float4(0.f, 0.f, 0.f, 0.f) : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
+            float* Cp = &Cf.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (aW[j] != 0.f || aC[j][ch] != 0.f)
+                    Cp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), Wn[j]) : 0.f;
+            *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cf;
+        }
+    } else {
+        uint32_t* Cp = &Cv.x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (aW[j] == 0.f && aC[j][0] == 0.f && aC[j][1] == 0.f && aC[j][2] == 0.f) continue;
+            if (!nz[j]) {
+                Cp[j] = 0u;
+                continue;
+            }
+            uint32_t out = 0;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
+                out |= u8_sat(__fdiv_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), Wn[j])) << (8 * ch);
+            }
+            Cp[j] = out;
+        }
+        __stcs(reinterpret_cast<uint4*>(V.C8 + off), Cv);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (aW[j] == 0.f && A.aD[j] == 0.f) continue;
+        Dp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Dp[j], Wp[j], A.aD[j]), Wn[j]) : 0.f;
+        Wp[j] = Wn[j];
+    }
+    __stcs(reinterpret_cast<float4*>(V.D + off), Dv);
+    __stcs(reinterpret_cast<float4*>(V.W + off), Wv);
+}
+
+// One voxel group of a block: the samples of every item with a bit on the block,
+// then one read-modify-write.  In RGBA8 the voxel state is requested before the
+// samples (evict-first: it is read and written once), so its latency overlaps them.
+template <bool F32, typename Acc>
+__device__ __forceinline__ void nd_group(const DevVolume& V, const NdCam* cams, int n_items, int32_t slot, int4 c,
+                                         bool fresh, uint32_t mw0, uint32_t mw1, int mw, int lane, int g) {
+    int lx0, ly, lz;
+    lane_voxels(lane, g, lx0, ly, lz);
+    const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+    float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
+    uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
+    if (!F32) {
+        Dv = __ldcs(reinterpret_cast<const float4*>(V.D + off));
+        Wv = __ldcs(reinterpret_cast<const float4*>(V.W + off));
+        Cv = __ldcs(reinterpret_cast<const uint4*>(V.C8 + off));
+    } else if (!fresh) {
+        Dv = *reinterpret_cast<const float4*>(V.D + off);
+        Wv = *reinterpret_cast<const float4*>(V.W + off);
+    }
+    Acc A;
+    nd_init(A);
+    bool touched = false;
+    net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, A, touched);
+    if (!touched && !fresh) return;
+    if (fresh) {  // first update of a new block: its memory holds no prior state
+        Dv = make_float4(0.f, 0.f, 0.f, 0.f);
+        Wv = Dv;
+        Cv = make_uint4(0u, 0u, 0u, 0u);
+    }
+    nd_apply<F32>(V, slot, off, lane, g, fresh, A, Dv, Wv, Cv);
+}
+
+// Work unit = one union block (512 voxels, four groups of 128, one warp).  Blocks come
+// from a queue in chunks of `grab`; the block's slot, coordinate, fresh flag and item
+// masks are read once for its four groups.
 #ifndef SC_ND_MIN_BLOCKS
 #define SC_ND_MIN_BLOCKS 4  // CTAs of 256 threads per SM the register budget must allow
 #endif
@@ -277,7 +444,6 @@ __global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVol
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t n_union = min((uint32_t)counters[0], V.max_blocks);
-    const uint32_t n_units = 4 * n_union;
     if (V.prof && blockIdx.x == 0 && threadIdx.x == 0) {
         unsigned long long pairs = 0;
         for (int i = 0; i < hdr->n; ++i)
@@ -289,88 +455,25 @@ __global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVol
         uint32_t base = 0;
         if (lane == 0) base = (uint32_t)atomicAdd(&counters[1], grab);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_units) break;
-        const uint32_t end = min(base + (uint32_t)grab, n_units);
-        for (uint32_t unit = base; unit < end; ++unit) {
-            const int32_t slot = ulist[unit >> 2];
-            const int g = unit & 3;
+        if (base >= n_union) break;
+        const uint32_t end = min(base + (uint32_t)grab, n_union);
+        for (uint32_t u = base; u < end; ++u) {
+            const int32_t slot = ulist[u];
             const int4 c = V.coord[slot];
             const bool fresh = (V.flags[slot] & FLAG_FRESH) != 0;
             const uint32_t* mp = masks + (size_t)slot * mw;
             const uint32_t mw0 = lane < mw ? mp[lane] : 0u;
             const uint32_t mw1 = lane + 32 < mw ? mp[lane + 32] : 0u;
-            int lx0, ly, lz;
-            lane_voxels(lane, g, lx0, ly, lz);
-            float aD[4] = {0.f, 0.f, 0.f, 0.f};
-            int iW[4] = {0, 0, 0, 0};
-            int iC[4][3] = {};
-            bool touched = false;
-            net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, aD, iW, iC, touched);
-            if (!touched && !fresh) continue;
-            float aW[4], aC[4][3];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                aW[j] = (float)iW[j];
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) aC[j][ch] = (float)iC[j][ch];
-            }
-            const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
-            float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
-            if (!fresh) {
-                Dv = *reinterpret_cast<const float4*>(V.D + off);
-                Wv = *reinterpret_cast<const float4*>(V.W + off);
-            }
-            float* Dp = &Dv.x;
-            float* Wp = &Wv.x;
-            float Wn[4];
-            bool nz[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                Wn[j] = __fadd_rn(Wp[j], aW[j]);
-                nz[j] = Wn[j] != 0.f;
-            }
-            if (F32) {
-                const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
-#pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    float4 Cv = fresh ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                      : *reinterpret_cast<const float4*>(V.Cf + cb + ch * NVOX);
-                    float* Cp = &Cv.x;
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (aW[j] != 0.f || aC[j][ch] != 0.f)
-                            Cp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), Wn[j]) : 0.f;
-                    *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cv;
-                }
+            // items with a bit on this block bound every voxel's count of samples
+            const int n_bits = (int)__reduce_add_sync(0xffffffffu, (unsigned)(__popc(mw0) + __popc(mw1)));
+            if (n_bits <= PACK_MAX_ITEMS) {
+#pragma unroll 1
+                for (int g = 0; g < 4; ++g) nd_group<F32, NdAcc>(V, cams, n_items, slot, c, fresh, mw0, mw1, mw, lane, g);
             } else {
-                uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
-                if (!fresh) Cv = *reinterpret_cast<const uint4*>(V.C8 + off);
-                uint32_t* Cp = &Cv.x;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (aW[j] == 0.f && aC[j][0] == 0.f && aC[j][1] == 0.f && aC[j][2] == 0.f) continue;
-                    if (!nz[j]) {
-                        Cp[j] = 0u;
-                        continue;
-                    }
-                    uint32_t out = 0;
-#pragma unroll
-                    for (int ch = 0; ch < 3; ++ch) {
-                        const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
-                        out |= u8_sat(__fdiv_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), Wn[j])) << (8 * ch);
-                    }
-                    Cp[j] = out;
-                }
-                *reinterpret_cast<uint4*>(V.C8 + off) = Cv;
+#pragma unroll 1
+                for (int g = 0; g < 4; ++g)
+                    nd_group<F32, NdAccWide>(V, cams, n_items, slot, c, fresh, mw0, mw1, mw, lane, g);
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (aW[j] == 0.f && aD[j] == 0.f) continue;
-                Dp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Dp[j], Wp[j], aD[j]), Wn[j]) : 0.f;
-                Wp[j] = Wn[j];
-            }
-            *reinterpret_cast<float4*>(V.D + off) = Dv;
-            *reinterpret_cast<float4*>(V.W + off) = Wv;
         }
     }
 }

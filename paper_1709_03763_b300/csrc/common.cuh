@@ -115,7 +115,11 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // floor(x) for 0 <= x < 2^23 without a conversion instruction: adding 2^23 rounded
-// down leaves floor(x) in the mantissa.
+// down leaves floor(x) in the mantissa.  Any other x (negative, >= 2^23, infinite or
+// NaN) gives a value outside [0, 2^23): x < 0 sums to a float below 2^23 (negative
+// integer result), x >= 2^23 to one of at least 2^24, and inf / NaN keep exponent bits
+// that are either far above 2^23 or negative, so one unsigned comparison against an
+// image size in [1, 2^23) tests "0 <= x < size" and takes the floor together.
 __device__ __forceinline__ int floor_small(float x) { return __float_as_int(__fadd_rd(x, 8388608.f)) - 0x4b000000; }
 
 // Projection of the 4 voxels (ix0 + j, iy, iz), j = 0..3, that one thread owns,
@@ -150,12 +154,14 @@ __device__ __forceinline__ void project4(const Cam& k, float ix0, float iy, floa
             py = __fadd_rn(py, k.Pr[3]);
         }
         const float rz = rcp_approx(pz);
-        // NaN / inf fail the range test
         const float uu = __fmaf_rn(px, rz, k.cxh);
         const float vv = __fmaf_rn(py, rz, k.cyh);
+        // nearest pixel and the range test in one: (unsigned) floor(u + 1/2) < W holds
+        // exactly when 0 <= u + 1/2 < W (NaN / inf fail it)
+        const int iu = floor_small(uu), iv = floor_small(vv);
         p.pz[j] = pz;
-        p.ok[j] = pz > 0.f && uu >= 0.f && uu < (float)k.W && vv >= 0.f && vv < (float)k.H;
-        p.pix[j] = p.ok[j] ? floor_small(vv) * k.W + floor_small(uu) : 0;
+        p.ok[j] = pz > 0.f && (unsigned)iu < (unsigned)k.W && (unsigned)iv < (unsigned)k.H;
+        p.pix[j] = p.ok[j] ? iv * k.W + iu : 0;
     }
 }
 

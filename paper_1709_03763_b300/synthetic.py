@@ -149,14 +149,35 @@ def _slab(o, d_inv, lo, hi):
     return torch.minimum(t1, t2), torch.maximum(t1, t2)
 
 
+def _near(scene: Scene, o, radius):
+    """Indices of the boxes, spheres and cylinders within `radius` of point o (closest
+    point of each primitive's bounding box)."""
+    def box_dist(lo, hi):
+        q = np.clip(o[None, :], lo, hi)
+        return np.linalg.norm(q - o[None, :], axis=1)
+    b = scene.boxes.reshape(-1, 6)
+    sp = scene.spheres.reshape(-1, 4)
+    cy = scene.cylinders.reshape(-1, 5)
+    bi = np.nonzero(box_dist(b[:, :3], b[:, 3:]) <= radius)[0]
+    si = np.nonzero(np.linalg.norm(sp[:, :3] - o[None, :], axis=1) - sp[:, 3] <= radius)[0]
+    clo = np.stack([cy[:, 0] - cy[:, 2], cy[:, 1] - cy[:, 2], cy[:, 3]], 1)
+    chi = np.stack([cy[:, 0] + cy[:, 2], cy[:, 1] + cy[:, 2], cy[:, 4]], 1)
+    ci = np.nonzero(box_dist(clo, chi) <= radius)[0] if len(cy) else np.zeros(0, np.int64)
+    return bi, si, ci
+
+
 def render(scene: Scene, intr: Intrinsics, poses, *, device="cpu", dtype=torch.float64,
-           chunk_prims: int = 64, texture: bool = False):
+           chunk_prims: int = 64, texture: bool = False, cull_radius: float | None = None):
     """Ray-cast z-depth and colour for each pose.
 
     poses: [n,3,4] world_from_camera.  Returns (depth [n,H,W] float32 torch on
     `device`, rgba [n,H,W,4] uint8 torch on `device`), noise-free, 0 where no hit.
     texture=True modulates each surface colour by a smooth procedural pattern of the
     world position (the same surface point has the same colour in every view).
+    cull_radius: skip primitives farther than this from the camera.  A hit at distance
+    r has z-depth at least r / |(x_n, y_n, 1)| (>= r / 1.23 at 640x480, f = 525), so with
+    cull_radius = 6 m every skipped hit lies beyond 4.8 m of depth, where the sensor
+    model reports no depth: valid depth pixels are exactly those of a full render.
     """
     poses = np.asarray(poses, np.float64).reshape(-1, 3, 4)
     H, W = intr.height, intr.width
@@ -178,7 +199,14 @@ def render(scene: Scene, intr: Intrinsics, poses, *, device="cpu", dtype=torch.f
     shell_col = _tt(scene.shell_colours.reshape(6, 3), device, torch.int32)
     inf = torch.tensor(float("inf"), device=device, dtype=dtype)
 
+    boxes_all, box_col_all, sph_all, sph_col_all, cyl_all, cyl_col_all = boxes, box_col, sph, sph_col, cyl, cyl_col
     for k, T in enumerate(poses):
+        if cull_radius is not None:
+            bi, si, ci = (torch.as_tensor(i, device=device, dtype=torch.long)
+                          for i in _near(scene, np.asarray(T[:, 3], np.float64), cull_radius))
+            boxes, box_col = boxes_all[bi], box_col_all[bi]
+            sph, sph_col = sph_all[si], sph_col_all[si]
+            cyl, cyl_col = cyl_all[ci], cyl_col_all[ci]
         R = _tt(T[:, :3], device, dtype)
         o = _tt(T[:, 3], device, dtype).expand(P, 3)
         d = dcam @ R.T
@@ -295,17 +323,28 @@ def colour_frames(scene: Scene, intr: Intrinsics, poses, config: int, *, device=
     return rgba
 
 
-def add_sensor_noise(depth: torch.Tensor, config: int, *, first_frame: int = 0) -> torch.Tensor:
+def noise_streams(config: int):
+    """The noise and invalid-mask generators of a config, for add_sensor_noise(streams=...)."""
+    return rng(config, STREAM_NOISE), rng(config, STREAM_MASK)
+
+
+def add_sensor_noise(depth: torch.Tensor, config: int, *, first_frame: int = 0, streams=None) -> torch.Tensor:
     """Kinect-class noise: z += N(0, sigma(z)); z outside [0.4, 4] -> 0; then 2% i.i.d.
     pixels -> 0.  Noise is drawn per frame from the config's noise / mask streams,
-    frame by frame in order, so a frame's noise does not depend on batch size."""
+    frame by frame in order, so a frame's noise does not depend on batch size.
+    streams: generators from noise_streams(config) that earlier calls have advanced
+    to this batch's first frame (batches rendered in order); without them the streams
+    are advanced to `first_frame` here (the same draws, recomputed)."""
     n, H, W = depth.shape
-    gn = rng(config, STREAM_NOISE)
-    gm = rng(config, STREAM_MASK)
-    # advance the streams to `first_frame`
-    if first_frame:
-        gn.standard_normal(first_frame * H * W)
-        gm.random(first_frame * H * W)
+    if streams is not None:
+        gn, gm = streams
+    else:
+        gn = rng(config, STREAM_NOISE)
+        gm = rng(config, STREAM_MASK)
+        # advance the streams to `first_frame`
+        if first_frame:
+            gn.standard_normal(first_frame * H * W)
+            gm.random(first_frame * H * W)
     out = torch.empty_like(depth)
     for k in range(n):
         z = depth[k].double().cpu().numpy()
@@ -586,10 +625,12 @@ def workload_batching(device="cpu", n_keyframes=2000, n_updates=10, intr: Intrin
     poses = grid_keyframe_poses(scene, n_keyframes, gt)
     depth = torch.empty((n_keyframes, intr.height, intr.width), dtype=torch.float32, device=device)
     rgba = torch.empty((n_keyframes, intr.height, intr.width, 4), dtype=torch.uint8, device=device)
+    streams = noise_streams(3)  # batches in order: each continues the previous one's draws
     for s in range(0, n_keyframes, render_batch):
+        # primitives beyond 6 m cannot give a valid (<= 4 m) depth (see render)
         d, c = render(scene, intr, poses[s:s + render_batch], device=device,
-                      dtype=torch.float32 if str(device).startswith("cuda") else torch.float64)
-        depth[s:s + render_batch] = add_sensor_noise(d, 3, first_frame=s)
+                      dtype=torch.float32 if str(device).startswith("cuda") else torch.float64, cull_radius=6.0)
+        depth[s:s + render_batch] = add_sensor_noise(d, 3, streams=streams)
         rgba[s:s + render_batch] = c
     gp = rng(3, STREAM_PERTURB)
     drifted = drift_poses(poses, math.radians(0.05), 0.002, gp)
