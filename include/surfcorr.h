@@ -135,6 +135,9 @@ typedef struct {
  *   - sc_autotune_batch: a snapshot of the volume's used blocks, freed on return;
  *   - the first sc_sdf_adjoint on a volume (and one with more keyframes than
  *     before, at least 256): its item tables and accumulators;
+ *   - sc_fuse_frames_into_keyframe / sc_fuse_keyframes: 8 bytes per keyframe
+ *     pixel of stream-ordered scratch per call, from a memory pool per device that
+ *     keeps its memory (so only the first call, or a larger one, reaches the driver);
  *   - sc_overlap_counts / sc_segment_keyframes (a stream-ordered count buffer
  *     per call), sc_stream_in_keyframes (a stream-ordered flag array per call),
  *     sc_create_block_store, and the first sc_marching_cubes on a device (its

@@ -346,12 +346,17 @@ __device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_
     }
     float* Dp = &Dv.x;
     float* Wp = &Wv.x;
-    float Wn[4];
+    float Wn[4], rW[4];
     bool nz[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         Wn[j] = __fadd_rn(Wp[j], aW[j]);
         nz[j] = Wn[j] != 0.f;
+        // one reciprocal per voxel for its four quotients (D and three colour channels):
+        // a few ulp where a division would give 0.5 ulp -- 1e-8 m for |D| <= mu, and a
+        // colour quotient moves by ~1e-5 of a level, which can only change the 8-bit
+        // rounding of a quotient that lies exactly on a half level
+        rW[j] = rcp_approx(Wn[j]);
     }
     if (F32) {
         const size_t cb = (size_t)slot * 3 * NVOX + 4 * lane + 128 * g;
@@ -362,7 +367,7 @@ __device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_
 #pragma unroll
             for (int j = 0; j < 4; ++j)
                 if (aW[j] != 0.f || aC[j][ch] != 0.f)
-                    Cp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), Wn[j]) : 0.f;
+                    Cp[j] = nz[j] ? __fmul_rn(__fmaf_rn(Cp[j], Wp[j], aC[j][ch]), rW[j]) : 0.f;
             *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cf;
         }
     } else {
@@ -378,7 +383,7 @@ __device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
-                out |= u8_sat(__fdiv_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), Wn[j])) << (8 * ch);
+                out |= u8_sat(__fmul_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), rW[j])) << (8 * ch);
             }
             Cp[j] = out;
         }
@@ -387,7 +392,7 @@ __device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (aW[j] == 0.f && A.aD[j] == 0.f) continue;
-        Dp[j] = nz[j] ? __fdiv_rn(__fmaf_rn(Dp[j], Wp[j], A.aD[j]), Wn[j]) : 0.f;
+        Dp[j] = nz[j] ? __fmul_rn(__fmaf_rn(Dp[j], Wp[j], A.aD[j]), rW[j]) : 0.f;
         Wp[j] = Wn[j];
     }
     __stcs(reinterpret_cast<float4*>(V.D + off), Dv);
@@ -426,9 +431,8 @@ __device__ __forceinline__ void nd_group(const DevVolume& V, const NdCam* cams, 
     nd_apply<F32>(V, slot, off, lane, g, fresh, A, Dv, Wv, Cv);
 }
 
-// Work unit = one union block (512 voxels, four groups of 128, one warp).  Blocks come
-// from a queue in chunks of `grab`; the block's slot, coordinate, fresh flag and item
-// masks are read once for its four groups.
+// Work unit u = (union block u / 4, voxel group u % 4): one warp, 128 voxels, four
+// per lane.  Units come from a queue in chunks of `grab`.
 #ifndef SC_ND_MIN_BLOCKS
 #define SC_ND_MIN_BLOCKS 4  // CTAs of 256 threads per SM the register budget must allow
 #endif
@@ -444,6 +448,7 @@ __global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVol
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint32_t n_union = min((uint32_t)counters[0], V.max_blocks);
+    const uint32_t n_units = 4 * n_union;
     if (V.prof && blockIdx.x == 0 && threadIdx.x == 0) {
         unsigned long long pairs = 0;
         for (int i = 0; i < hdr->n; ++i)
@@ -455,10 +460,11 @@ __global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVol
         uint32_t base = 0;
         if (lane == 0) base = (uint32_t)atomicAdd(&counters[1], grab);
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n_union) break;
-        const uint32_t end = min(base + (uint32_t)grab, n_union);
-        for (uint32_t u = base; u < end; ++u) {
-            const int32_t slot = ulist[u];
+        if (base >= n_units) break;
+        const uint32_t end = min(base + (uint32_t)grab, n_units);
+        for (uint32_t unit = base; unit < end; ++unit) {
+            const int32_t slot = ulist[unit >> 2];
+            const int g = unit & 3;
             const int4 c = V.coord[slot];
             const bool fresh = (V.flags[slot] & FLAG_FRESH) != 0;
             const uint32_t* mp = masks + (size_t)slot * mw;
@@ -466,14 +472,10 @@ __global__ void __launch_bounds__(256, SC_ND_MIN_BLOCKS) net_delta_kernel(DevVol
             const uint32_t mw1 = lane + 32 < mw ? mp[lane + 32] : 0u;
             // items with a bit on this block bound every voxel's count of samples
             const int n_bits = (int)__reduce_add_sync(0xffffffffu, (unsigned)(__popc(mw0) + __popc(mw1)));
-            if (n_bits <= PACK_MAX_ITEMS) {
-#pragma unroll 1
-                for (int g = 0; g < 4; ++g) nd_group<F32, NdAcc>(V, cams, n_items, slot, c, fresh, mw0, mw1, mw, lane, g);
-            } else {
-#pragma unroll 1
-                for (int g = 0; g < 4; ++g)
-                    nd_group<F32, NdAccWide>(V, cams, n_items, slot, c, fresh, mw0, mw1, mw, lane, g);
-            }
+            if (n_bits <= PACK_MAX_ITEMS)
+                nd_group<F32, NdAcc>(V, cams, n_items, slot, c, fresh, mw0, mw1, mw, lane, g);
+            else
+                nd_group<F32, NdAccWide>(V, cams, n_items, slot, c, fresh, mw0, mw1, mw, lane, g);
         }
     }
 }

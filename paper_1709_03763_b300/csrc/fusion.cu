@@ -4,8 +4,10 @@
 // p* = g(T*^-1, g(T_i, pi^-1(x, Z_i(x)))), rounded to its nearest keyframe pixel
 // x*, and accumulated as sum(w_z Z*_p) and sum(w_z) with w_z = cos(theta) / Z^2.
 // Applying Eq. 1 sequentially gives exactly that ratio of sums, so the kernel
-// scatters both sums with float atomics (order-free up to rounding) and a second
-// pass divides.  One thread per 4 pixels of a frame row; up to 64 frames per launch.
+// scatters both sums, interleaved per keyframe pixel, with one 8-byte vector float
+// atomic per pixel (order-free up to rounding) into pooled scratch, and a second pass
+// divides and writes Z* and W*.  One thread per 4 pixels of a frame row; up to 64
+// frames per launch.
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -48,37 +50,41 @@ cudaEvent_t fprof_event(cudaStream_t s) {
 struct FuseCam {
     float cx, cy, ifx, ify;  // ifx = 1/fx, ify = 1/fy
     float cxh, cyh;          // cx + 1/2, cy + 1/2: nearest pixel by one floor
-    float Wf, Hf;
     int W, H;
     float disc_rel;
-    float* S;     // sum w_z Z*_p (in the Z* output until normalised)
-    float* Wsum;  // sum w_z (the W* output)
+    float2* acc;  // per keyframe pixel (sum w_z Z*_p, sum w_z), interleaved
 };
 
-// floor(x) for 0 <= x < 2^23 without a conversion instruction: adding 2^23 rounded
-// down leaves floor(x) in the low mantissa bits
+// floor(x) for 0 <= x < 2^23 without a conversion instruction (adding 2^23 rounded
+// down leaves floor(x) in the low mantissa bits); every other x, inf and NaN included,
+// lands outside [0, 2^23), so "(unsigned) fuse_floor(x) < size" is the range test too
 __device__ __forceinline__ int fuse_floor(float x) { return __float_as_int(__fadd_rd(x, 8388608.f)) - 0x4b000000; }
 
 // Eq. 1 contribution of one frame pixel with depth z and 4-neighbours at normalised
-// image coordinates xn = (u - cx) / fx, yn = (v - cy) / fy.  Sk, Wk: the keyframe's images.
-// All tests fold into one predicate, so a warp takes no divergent early exits.
-__device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c, float xn, float yn, float z,
-                                           float zl, float zr, float zu, float zd, float* Sk, float* Wk) {
+// image coordinates xn = (u - cx) / fx, yn = (v - cy) / fy; rb[r] = Pr[r][1] yn + Pr[r][2]
+// is the part of the pixel's ray that its row shares.  All tests fold into one
+// predicate, so a warp takes no divergent early exits; the two sums go out as one
+// 8-byte vector atomic.
+__device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c, float xn, float yn,
+                                           const float rb[3], float z, float zl, float zr, float zu, float zd,
+                                           float2* acc) {
     // a valid depth whose four neighbours are valid and within disc_rel * z of it
     const float lim = c.disc_rel * z;
     bool ok = z > 0.f && zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f;
     ok = ok && fabsf(zl - z) <= lim && fabsf(zr - z) <= lim && fabsf(zu - z) <= lim && fabsf(zd - z) <= lim;
-    // warp into the keyframe: (fx X*, fy Y*, Z*) = Pr P + t
-    const float P0 = xn * z, P1 = yn * z;
-    const float X = fmaf(F.Pr[0], P0, fmaf(F.Pr[1], P1, fmaf(F.Pr[2], z, F.t[0])));
-    const float Y = fmaf(F.Pr[3], P0, fmaf(F.Pr[4], P1, fmaf(F.Pr[5], z, F.t[1])));
-    const float Zs = fmaf(F.Pr[6], P0, fmaf(F.Pr[7], P1, fmaf(F.Pr[8], z, F.t[2])));
+    // warp into the keyframe: (fx X*, fy Y*, Z*) = z Pr (xn, yn, 1) + t, the pixel's ray
+    // Pr (xn, yn, 1) formed first (one fma per row on top of the row's share)
+    const float a0 = fmaf(F.Pr[0], xn, rb[0]);
+    const float a1 = fmaf(F.Pr[3], xn, rb[1]);
+    const float a2 = fmaf(F.Pr[6], xn, rb[2]);
+    const float X = fmaf(a0, z, F.t[0]);
+    const float Y = fmaf(a1, z, F.t[1]);
+    const float Zs = fmaf(a2, z, F.t[2]);
     // approximate reciprocal (2 ulp): a few 1e-5 px at the nearest-pixel rounding
     const float rz = __fdividef(1.f, Zs);
-    const float uu = fmaf(X, rz, c.cxh);
-    const float vv = fmaf(Y, rz, c.cyh);
-    // NaN and inf fail these comparisons
-    ok = ok && Zs > 0.f && uu >= 0.f && uu < c.Wf && vv >= 0.f && vv < c.Hf;
+    const int iu = fuse_floor(fmaf(X, rz, c.cxh));
+    const int iv = fuse_floor(fmaf(Y, rz, c.cyh));
+    ok = ok && Zs > 0.f && (unsigned)iu < (unsigned)c.W && (unsigned)iv < (unsigned)c.H;
     // w_z = cos(theta) / Z^2, theta from the normal n = a x b of the central differences
     // a = P(u+1,v) - P(u-1,v) = dzx (xn, yn, 1) + (A, 0, 0),  A = (z_r + z_l) / fx
     // b = P(u,v+1) - P(u,v-1) = dzy (xn, yn, 1) + (0, B, 0),  B = (z_d + z_u) / fy
@@ -91,9 +97,7 @@ __device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c,
     ok = ok && n2 > 0.f;
     if (ok) {
         const float w = __fdividef(fabsf(nz) * rsqrtf(n2), z * z);
-        const int q = fuse_floor(vv) * c.W + fuse_floor(uu);
-        atomicAdd(Sk + q, w * Zs);
-        atomicAdd(Wk + q, w);
+        atomicAdd(acc + (iv * c.W + iu), make_float2(w * Zs, w));
     }
 }
 
@@ -114,15 +118,15 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     const float4 dn = __ldg(reinterpret_cast<const float4*>(Z + W));
     const float left = u0 > 0 ? __ldg(Z - 1) : 0.f;     // 0: the first pixel has no left neighbour
     const float right = u0 + 4 < W ? __ldg(Z + 4) : 0.f;  // 0: the last pixel has no right neighbour
-    float* Sk = c.S + (size_t)F.kf * npx;
-    float* Wk = c.Wsum + (size_t)F.kf * npx;
+    float2* acc = c.acc + (size_t)F.kf * npx;
     // pixel coordinates stepped in float (exact integers): one conversion per thread
     const float uf = (float)u0;
     const float yn = ((float)v - c.cy) * c.ify;
-    fuse_pixel(F, c, (uf - c.cx) * c.ifx, yn, row.x, left, row.y, up.x, dn.x, Sk, Wk);
-    fuse_pixel(F, c, ((uf + 1.f) - c.cx) * c.ifx, yn, row.y, row.x, row.z, up.y, dn.y, Sk, Wk);
-    fuse_pixel(F, c, ((uf + 2.f) - c.cx) * c.ifx, yn, row.z, row.y, row.w, up.z, dn.z, Sk, Wk);
-    fuse_pixel(F, c, ((uf + 3.f) - c.cx) * c.ifx, yn, row.w, row.z, right, up.w, dn.w, Sk, Wk);
+    const float rb[3] = {fmaf(F.Pr[1], yn, F.Pr[2]), fmaf(F.Pr[4], yn, F.Pr[5]), fmaf(F.Pr[7], yn, F.Pr[8])};
+    fuse_pixel(F, c, (uf - c.cx) * c.ifx, yn, rb, row.x, left, row.y, up.x, dn.x, acc);
+    fuse_pixel(F, c, ((uf + 1.f) - c.cx) * c.ifx, yn, rb, row.y, row.x, row.z, up.y, dn.y, acc);
+    fuse_pixel(F, c, ((uf + 2.f) - c.cx) * c.ifx, yn, rb, row.z, row.y, row.w, up.z, dn.z, acc);
+    fuse_pixel(F, c, ((uf + 3.f) - c.cx) * c.ifx, yn, rb, row.w, row.z, right, up.w, dn.w, acc);
 }
 
 // Any width: one thread per pixel.
@@ -136,27 +140,62 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel_any(const float*
     const size_t npx = (size_t)W * H;
     const float* Z = depths + (size_t)blockIdx.z * npx;
     const size_t p = (size_t)v * W + u;
-    fuse_pixel(F, c, ((float)u - c.cx) * c.ifx, ((float)v - c.cy) * c.ify, __ldg(Z + p), __ldg(Z + p - 1),
-               __ldg(Z + p + 1), __ldg(Z + p - W), __ldg(Z + p + W), c.S + (size_t)F.kf * npx,
-               c.Wsum + (size_t)F.kf * npx);
+    const float yn = ((float)v - c.cy) * c.ify;
+    const float rb[3] = {fmaf(F.Pr[1], yn, F.Pr[2]), fmaf(F.Pr[4], yn, F.Pr[5]), fmaf(F.Pr[7], yn, F.Pr[8])};
+    fuse_pixel(F, c, ((float)u - c.cx) * c.ifx, yn, rb, __ldg(Z + p), __ldg(Z + p - 1), __ldg(Z + p + 1),
+               __ldg(Z + p - W), __ldg(Z + p + W), c.acc + (size_t)F.kf * npx);
 }
 
-__global__ void fuse_normalise_kernel(float* Z, const float* Wsum, size_t n) {
-    const size_t n4 = n / 4;  // both arrays 16-byte aligned
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-        const float4 w = reinterpret_cast<const float4*>(Wsum)[i];
-        float4 z = reinterpret_cast<float4*>(Z)[i];
-        z.x = w.x > 0.f ? z.x / w.x : 0.f;
-        z.y = w.y > 0.f ? z.y / w.y : 0.f;
-        z.z = w.z > 0.f ? z.z / w.z : 0.f;
-        z.w = w.w > 0.f ? z.w / w.w : 0.f;
-        reinterpret_cast<float4*>(Z)[i] = z;
+// Z* = S / W* where W* > 0, else 0; W* out as is.  Two pixels' sums per 16-byte load.
+__global__ void fuse_normalise_kernel(const float2* __restrict__ acc, float* __restrict__ Z, float* __restrict__ Wsum,
+                                      size_t n) {
+    const size_t n2 = n / 2;  // pairs of pixels: 16-byte loads, 8-byte stores
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n2; i += (size_t)gridDim.x * blockDim.x) {
+        const float4 sw = __ldcs(reinterpret_cast<const float4*>(acc) + i);
+        reinterpret_cast<float2*>(Z)[i] =
+            make_float2(sw.y > 0.f ? sw.x / sw.y : 0.f, sw.w > 0.f ? sw.z / sw.w : 0.f);
+        reinterpret_cast<float2*>(Wsum)[i] = make_float2(sw.y, sw.w);
     }
-    for (size_t i = 4 * n4 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const float w = Wsum[i];
-        Z[i] = w > 0.f ? Z[i] / w : 0.f;
+    for (size_t i = 2 * n2 + blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float2 sw = acc[i];
+        Z[i] = sw.y > 0.f ? sw.x / sw.y : 0.f;
+        Wsum[i] = sw.y;
     }
 }
+
+// Stream-ordered scratch for the interleaved sums: a memory pool per device that keeps
+// its memory between calls (release threshold at the maximum), so after the first call
+// a fusion takes its scratch from memory the pool already holds; concurrent calls on
+// other streams get blocks of their own.
+cudaMemPool_t g_fuse_pool[64] = {};
+std::mutex g_fuse_pool_mu;
+
+cudaError_t fuse_pool(int dev, cudaMemPool_t* out) {
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_fuse_pool_mu);
+    if (!g_fuse_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p = nullptr;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t keep = UINT64_MAX;
+        e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return e;
+        }
+        g_fuse_pool[dev] = p;
+    }
+    *out = g_fuse_pool[dev];
+    return cudaSuccess;
+}
+
+int fuse_launch(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n,
+                const sc_pose* kf_poses, const sc_intrinsics* K, const sc_fusion_params* fusion, float2* acc,
+                size_t acc_bytes, int sms, float* kf_depth, float* kf_weight, int32_t n_kf, cudaStream_t s);
 
 // Fuse frames [0, n) into keyframe images; frame f goes to image frame_kf[f] at pose kf_poses[frame_kf[f]].
 int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n,
@@ -175,10 +214,28 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
     }
     const int W = K->width, H = K->height;
     const size_t npx = (size_t)W * H;
-    SC_CUDA(cudaMemsetAsync(kf_depth, 0, n_kf * npx * sizeof(float), s));
-    SC_CUDA(cudaMemsetAsync(kf_weight, 0, n_kf * npx * sizeof(float), s));
+    int dev = 0, sms = 148;
+    SC_CUDA(cudaGetDevice(&dev));
+    SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaMemPool_t pool = nullptr;
+    SC_CUDA(fuse_pool(dev, &pool));
+    float2* acc = nullptr;
+    const size_t acc_bytes = (size_t)n_kf * npx * sizeof(float2);
+    SC_CUDA(cudaMallocFromPoolAsync((void**)&acc, acc_bytes, pool, s));
+    const int rc = fuse_launch(depths, frame_poses, frame_kf, n, kf_poses, K, fusion, acc, acc_bytes, sms,
+                               kf_depth, kf_weight, n_kf, s);
+    cudaFreeAsync(acc, s);
+    return rc;
+}
+
+int fuse_launch(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n,
+                const sc_pose* kf_poses, const sc_intrinsics* K, const sc_fusion_params* fusion, float2* acc,
+                size_t acc_bytes, int sms, float* kf_depth, float* kf_weight, int32_t n_kf, cudaStream_t s) {
+    const int W = K->width, H = K->height;
+    const size_t npx = (size_t)W * H;
+    SC_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s));
     FuseCam c{K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), (float)((double)K->cx + 0.5),
-              (float)((double)K->cy + 0.5), (float)W, (float)H, W, H, fusion->disc_rel, kf_depth, kf_weight};
+              (float)((double)K->cy + 0.5), W, H, fusion->disc_rel, acc};
     for (int f0 = 0; f0 < n; f0 += FUSE_MAX_FRAMES) {
         const int nf = (n - f0) < FUSE_MAX_FRAMES ? (n - f0) : FUSE_MAX_FRAMES;
         FuseArgs a;
@@ -223,10 +280,7 @@ int fuse_impl(const float* depths, const sc_pose* frame_poses, const int32_t* fr
         sc::count_launches(1);
         SC_CUDA(cudaGetLastError());
     }
-    int dev = 0, sms = 148;
-    SC_CUDA(cudaGetDevice(&dev));
-    SC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    fuse_normalise_kernel<<<sms * 8, 256, 0, s>>>(kf_depth, kf_weight, n_kf * npx);
+    fuse_normalise_kernel<<<sms * 8, 256, 0, s>>>(acc, kf_depth, kf_weight, n_kf * npx);
     sc::count_launches(1);
     SC_CUDA(cudaGetLastError());
     return SC_OK;
