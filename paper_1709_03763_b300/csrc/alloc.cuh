@@ -4,8 +4,9 @@
 // A(k, T): every 8^3 block whose closed box meets the band segment
 // {pi^-1(x, z) : z in [Z(x) - mu, Z(x) + mu]} of a valid pixel x, in world
 // coordinates.  Computed per 32x16 pixel tile by one CTA:
-//   A  enumerate each pixel's candidate blocks (slab test) into a shared-memory
-//      set, which removes the many duplicates neighbouring pixels produce;
+//   A  enumerate each pixel's blocks (a walk across block faces) into a shared-memory
+//      set of 32-bit camera-relative keys, which removes the many duplicates
+//      neighbouring pixels produce;
 //   B  claim every unique key in the global hash table (64-bit CAS); the tile's
 //      new entries get consecutive pool slots from one atomic add;
 //   C  read each key's slot and let the Sink decide whether this call lists it
@@ -31,7 +32,8 @@ constexpr int ALLOC_TX = 32;           // pixel tile 32 x SC_ALLOC_TY, one CTA o
 constexpr int ALLOC_TY = SC_ALLOC_TY;  // SC_ALLOC_TY / 8 pixels (rows r, r+8, ...) per thread
 constexpr int ALLOC_THREADS = 256;
 constexpr int ALLOC_PPT = ALLOC_TX * ALLOC_TY / ALLOC_THREADS;
-constexpr int SET_SIZE = ALLOC_TY >= 32 ? 1024 : 512;  // unique blocks of a tile before overflow handling
+constexpr int SET_BITS = ALLOC_TY >= 32 ? 10 : 9;
+constexpr int SET_SIZE = 1 << SET_BITS;  // unique blocks of a tile before overflow handling
 constexpr int MAX_BLOCK_WALK = 48;   // block-face crossings of one band segment
 constexpr float MAX_DEPTH = 1.0e4f;  // metres; larger depth values are treated as invalid
 
@@ -46,22 +48,18 @@ __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, floa
     const float xn = __fmul_rn(__fsub_rn((float)u, k.cx), k.ifx);
     const float yn = __fmul_rn(__fsub_rn((float)v, k.cy), k.ify);
     const float z0 = __fsub_rn(Z, k.mu), z1 = __fadd_rn(Z, k.mu);
-    const float c0[3] = {__fmul_rn(xn, z0), __fmul_rn(yn, z0), z0};
-    const float c1[3] = {__fmul_rn(xn, z1), __fmul_rn(yn, z1), z1};
+
     float q0[3], q1[3];
     int b[3], rem[3], step[3];
     float tmax[3], tdel[3];
     int n = 0;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        q0[r] = __fadd_rn(
-            __fmaf_rn(k.Ms[3 * r + 2], c0[2], __fmaf_rn(k.Ms[3 * r + 1], c0[1], __fmul_rn(k.Ms[3 * r], c0[0]))),
-            k.tf[r]);
-        q1[r] = __fadd_rn(
-            __fmaf_rn(k.Ms[3 * r + 2], c1[2], __fmaf_rn(k.Ms[3 * r + 1], c1[1], __fmul_rn(k.Ms[3 * r], c1[0]))),
-            k.tf[r]);
-        b[r] = ((int)floorf(q0[r]) + k.ti[r]) >> 3;
-        const int e = ((int)floorf(q1[r]) + k.ti[r]) >> 3;
+        const float ray = __fmaf_rn(k.Ms[3 * r], xn, __fmaf_rn(k.Ms[3 * r + 1], yn, k.Ms[3 * r + 2]));
+        q0[r] = __fmaf_rn(z0, ray, k.tf[r]);
+        q1[r] = __fmaf_rn(z1, ray, k.tf[r]);
+        b[r] = (__float2int_rd(q0[r]) + k.ti[r]) >> 3;
+        const int e = (__float2int_rd(q1[r]) + k.ti[r]) >> 3;
         rem[r] = abs(e - b[r]);
         n += rem[r];
         const float d = __fsub_rn(q1[r], q0[r]);
@@ -107,33 +105,49 @@ __device__ inline void for_each_segment_block(const KfCam& k, int u, int v, floa
     }
 }
 
-// Slot of a key in the CTA's shared set (Fibonacci hashing: one multiply).
-__device__ __forceinline__ uint32_t set_hash(unsigned long long key) {
-    return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> 40) & (SET_SIZE - 1);
+// The CTA's shared set holds 32-bit keys: each block coordinate relative to the
+// camera's block, 10 bits per axis (+-512 blocks, 41 m at 1 cm voxels, beyond any
+// sensor range).  A block outside that range (a depth of kilometres) is counted as an
+// overflow and claimed by phase D with its full key.
+constexpr uint32_t KEY32_EMPTY = 0xFFFFFFFFu;  // never a key: keys use 30 bits
+
+__device__ __forceinline__ bool key32(int bx, int by, int bz, const int3& ref, uint32_t* k) {
+    const uint32_t dx = (uint32_t)(bx - ref.x + 512), dy = (uint32_t)(by - ref.y + 512),
+                   dz = (uint32_t)(bz - ref.z + 512);
+    *k = dx | (dy << 10) | (dz << 20);
+    return (dx | dy | dz) < 1024u;
 }
+
+__device__ __forceinline__ unsigned long long key64_of(uint32_t k, const int3& ref) {
+    return pack_key((int)(k & 1023u) - 512 + ref.x, (int)((k >> 10) & 1023u) - 512 + ref.y,
+                    (int)(k >> 20) - 512 + ref.z);
+}
+
+// Slot of a key in the CTA's shared set (Fibonacci hashing: one multiply).
+__device__ __forceinline__ uint32_t set_hash(uint32_t key) { return (key * 0x9E3779B1u) >> (32 - SET_BITS); }
 
 // Insert into the CTA's shared set.  Most inserts find their key already there:
 // read before CAS so that those do not serialise on the shared atomic unit.
-__device__ inline bool set_insert(unsigned long long* set, unsigned long long key) {
+__device__ inline bool set_insert(uint32_t* set, uint32_t key) {
     uint32_t h = set_hash(key);
     for (int i = 0; i < SET_SIZE; ++i) {
-        unsigned long long k = ((volatile unsigned long long*)set)[h];
+        uint32_t k = ((volatile uint32_t*)set)[h];
         if (k == key) return true;
-        if (k == KEY_EMPTY) {
-            k = atomicCAS(&set[h], KEY_EMPTY, key);
-            if (k == KEY_EMPTY || k == key) return true;
+        if (k == KEY32_EMPTY) {
+            k = atomicCAS(&set[h], KEY32_EMPTY, key);
+            if (k == KEY32_EMPTY || k == key) return true;
         }
         h = (h + 1) & (SET_SIZE - 1);
     }
     return false;
 }
 
-__device__ inline bool set_contains(const unsigned long long* set, unsigned long long key) {
+__device__ inline bool set_contains(const uint32_t* set, uint32_t key) {
     uint32_t h = set_hash(key);
     for (int i = 0; i < SET_SIZE; ++i) {
-        const unsigned long long k = set[h];
+        const uint32_t k = set[h];
         if (k == key) return true;
-        if (k == KEY_EMPTY) return false;
+        if (k == KEY32_EMPTY) return false;
         h = (h + 1) & (SET_SIZE - 1);
     }
     return false;
@@ -155,7 +169,7 @@ __device__ inline void publish(const DevVolume& V, int entry, unsigned long long
 }
 
 struct AllocShared {
-    unsigned long long set[SET_SIZE];  // open-addressing set of the tile's block keys
+    uint32_t set[SET_SIZE];  // open-addressing set of the tile's block keys (key32)
     int uk[SET_SIZE];    // compacted: set positions of the n_keys occupied entries
     int ent[SET_SIZE];   // per compacted key: hash entry index (-1: failed)
     int slot[SET_SIZE];  // per compacted key: pool slot if known, else -1
@@ -183,7 +197,7 @@ __device__ inline void append_one(const DevVolume& V, int32_t* list, int32_t* co
 template <typename Sink>
 __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, int ty, Sink& sk, AllocShared& sh) {
     const int tid = threadIdx.x;
-    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY_EMPTY;
+    for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY32_EMPTY;
     if (tid == 0) {
         sh.n_keys = 0;
         sh.n_new = 0;
@@ -194,6 +208,10 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     __syncthreads();
 
     // A: every pixel's band-segment blocks into the shared set
+    const int3 ref = make_int3(k.ti[0] >> 3, k.ti[1] >> 3, k.ti[2] >> 3);  // the camera's block
+    // every 32-bit key of this camera decodes to a valid block coordinate (else all its
+    // blocks take phase D, which checks each one)
+    const bool ref_ok = coord_ok(ref.x - 512, ref.y - 512, ref.z - 512) && coord_ok(ref.x + 511, ref.y + 511, ref.z + 511);
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
     const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
     bool my_ovf = false;
@@ -203,11 +221,8 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
         float Z = 0.f;
         if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
         auto ins = [&](int bx, int by, int bz) {
-            if (!coord_ok(bx, by, bz)) {
-                set_status(V.status, SC_ERR_INVALID_ARG);
-                return;
-            }
-            if (!set_insert(sh.set, pack_key(bx, by, bz))) my_ovf = true;
+            uint32_t kk;
+            if (!ref_ok || !key32(bx, by, bz, ref, &kk) || !set_insert(sh.set, kk)) my_ovf = true;
         };
         if (Z > 0.f && Z < MAX_DEPTH) for_each_segment_block(k, u, v, Z, ins);
     }
@@ -215,7 +230,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     __syncthreads();
     // compact the occupied entries so that the global phases run in one round
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS)
-        if (sh.set[i] != KEY_EMPTY) sh.uk[atomicAdd(&sh.n_keys, 1)] = i;
+        if (sh.set[i] != KEY32_EMPTY) sh.uk[atomicAdd(&sh.n_keys, 1)] = i;
     __syncthreads();
     const int nk = sh.n_keys;
 
@@ -223,7 +238,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     for (int i = tid; i < nk; i += ALLOC_THREADS) {
         bool won;
         int32_t seen;
-        const int e = hash_claim(V, sh.set[sh.uk[i]], &won, &seen);
+        const int e = hash_claim(V, key64_of(sh.set[sh.uk[i]], ref), &won, &seen);
         sh.ent[i] = e;
         sh.slot[i] = seen;
         sh.mine[i] = 0;
@@ -242,7 +257,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
             sh.slot[j] = (int)slot;
             sh.mine[j] = 1;
         }
-        publish(V, sh.ent[j], sh.set[sh.uk[j]], slot);
+        publish(V, sh.ent[j], key64_of(sh.set[sh.uk[j]], ref), slot);
     }
     __syncthreads();
 
@@ -285,9 +300,13 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
             if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
             if (!(Z > 0.f && Z < MAX_DEPTH)) continue;
             for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
-                if (!coord_ok(bx, by, bz)) return;
+                if (!coord_ok(bx, by, bz)) {
+                    set_status(V.status, SC_ERR_INVALID_ARG);
+                    return;
+                }
+                uint32_t kk;
+                if (ref_ok && key32(bx, by, bz, ref, &kk) && set_contains(sh.set, kk)) return;
                 const unsigned long long key = pack_key(bx, by, bz);
-                if (set_contains(sh.set, key)) return;
                 bool won;
                 int32_t seen;
                 const int e = hash_claim(V, key, &won, &seen);
