@@ -90,6 +90,9 @@ def parse():
     ap.add_argument("--keyframes", type=int, default=60, help="keyframes of the workload (small ncu cases)")
     ap.add_argument("--max-blocks", type=int, default=1 << 21)
     ap.add_argument("--no-batching", action="store_true", help="skip the 2000-keyframe batching rows")
+    ap.add_argument("--profile-batching", action="store_true",
+                    help="batching workload cut to --keyframes keyframes: one pose update of its first update's "
+                         "size (at most half the keyframes) between cudaProfilerStart/Stop (for ncu), then exit")
     ap.add_argument("--batching-reps", type=int, default=10, help="replays per pose update in the batching rows")
     return ap.parse_args()
 
@@ -679,6 +682,45 @@ def batching_rows(dev, hbm_peak, peak_kind, reps, cpu_sample, ws):
     return row, fb_row
 
 
+def profile_batching(dev, n_kf, max_blocks, steps, warmup):
+    """The batching workload with n_kf keyframes: integrate all, then replay one pose
+    update (the first update's size, at most n_kf / 2 keyframes chosen by largest pose
+    change) and its reverse; the timed replays run between cudaProfilerStart/Stop."""
+    import torch
+    from paper_1709_03763_b300 import Volume, make_intrinsics, pose_distance, select_topm, synthetic
+    w = synthetic.workload_batching(device=dev, n_keyframes=n_kf, n_updates=1)
+    D, C = w.kf_depth, w.kf_rgba
+    intr = make_intrinsics(w.intr)
+    V = Volume(w.voxel_size, w.trunc, w.n_buckets, colour="rgba8", max_blocks=max_blocks, max_keyframes=n_kf,
+               max_blocks_per_keyframe=1 << 16, max_batch=256)
+    for s0 in range(0, n_kf, 256):
+        ids = list(range(s0, min(n_kf, s0 + 256)))
+        V.integrate_many(ids, [D[k] for k in ids], [C[k] for k in ids], w.kf_poses[ids], intr)
+    upd = w.updates[0]
+    tgt = upd["target_poses"]
+    dist = np.array([pose_distance(w.kf_poses[k], tgt[k]) for k in range(n_kf)])
+    ids = [int(i) for i in select_topm(dist, min(upd["n"], n_kf // 2))]
+    dl, cl = [D[k] for k in ids], [C[k] for k in ids]
+    fwd = V.prepare_batch(ids, dl, cl, w.kf_poses[ids], tgt[ids])
+    rev = V.prepare_batch(ids, dl, cl, tgt[ids], w.kf_poses[ids])
+    for _ in range(warmup):
+        V.reintegrate_batch(intr=intr, prepared=fwd)
+        V.reintegrate_batch(intr=intr, prepared=rev)
+    V.check()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for r in range(steps):
+        V.reintegrate_batch(intr=intr, prepared=fwd if r % 2 == 0 else rev)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    V.set_profiling(True)
+    V.reintegrate_batch(intr=intr, prepared=fwd)
+    pr = V.profile()
+    print(json.dumps({"profile_batching": len(ids), "keyframes": n_kf, "blocks": V.info()["allocated_blocks"],
+                      "union_blocks": pr["batch_union_blocks"], "pairs": pr["batch_pairs"],
+                      "net_delta_ms": pr["batch_net_ms"], "alloc_ms": pr["batch_alloc_ms"]}), flush=True)
+
+
 def oracle_batching_sample(n_kf=2):
     """The oracle re-integrating n_kf keyframes of the batching workload's first update
     (FP64, host cores): (seconds per re-integration, threads)."""
@@ -732,6 +774,9 @@ def main():
     from paper_1709_03763_b300 import build as _build
     _build.build()
     dev = torch.device("cuda", torch.cuda.current_device())
+    if args.profile_batching:
+        profile_batching(dev, args.keyframes, args.max_blocks, args.steps, args.warmup)
+        return
 
     t_setup = time.perf_counter()
     w = make_workload(dev, args.keyframes)
