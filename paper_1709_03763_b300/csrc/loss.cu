@@ -232,7 +232,7 @@ struct AdjItem {
 constexpr int ADJ_THREADS = 256;
 
 #ifndef SC_ADJ_MIN_BLOCKS
-#define SC_ADJ_MIN_BLOCKS 1  // resident CTAs per SM the register budget must allow
+#define SC_ADJ_MIN_BLOCKS 4  // resident CTAs per SM: 64 registers, 32 warps (no spills)
 #endif
 __global__ void __launch_bounds__(ADJ_THREADS, SC_ADJ_MIN_BLOCKS) adjoint_kernel(DevVolume V, const AdjItem* items, uint32_t cap,
                                                               const float* grad, double* acc) {
