@@ -455,6 +455,19 @@ int sc_stream_in(sc_volume* vol, sc_block_store* store, const float* centre, flo
 int sc_stream_in_keyframes(sc_volume* vol, sc_block_store* store, const int32_t* kf_ids, int32_t n,
                            int64_t* n_moved, sc_stream stream);
 
+/* Stream in exactly the stored blocks that allocating A(k, T) (Section 3 "SDF
+ * volume") for n keyframe images at the given poses would reach: the allocation's own
+ * walk of every valid pixel's band segment, each block looked up in the store's key
+ * index.  Called before re-integrating keyframes at updated poses (Section 4.3 streams
+ * the spheres around the updated poses in; this streams in the blocks the new poses'
+ * allocation needs, each once), so that the allocation finds them resident instead of
+ * creating second copies.
+ *   depths  host [n] array of device [H][W] keyframe depth pointers
+ *   poses   host [n] updated poses;  intr: the images' intrinsics
+ * Same rules and errors as sc_stream_in; n = 0 moves nothing.  Synchronises. */
+int sc_stream_in_poses(sc_volume* vol, sc_block_store* store, const float* const* depths, const sc_pose* poses,
+                       int32_t n, const sc_intrinsics* intr, int64_t* n_moved, sc_stream stream);
+
 /* --------------------------------------------- loss and adjoint (extension) ---- */
 
 /* Loss on the fused SDF (no counterpart in the paper):

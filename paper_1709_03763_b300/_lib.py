@@ -119,6 +119,7 @@ SIGNATURES = {
     "sc_stream_out": (c_i32, [c_p, c_p, P(c_f), c_f, P(c_i64), c_p]),
     "sc_stream_in": (c_i32, [c_p, c_p, P(c_f), c_f, P(c_i64), c_p]),
     "sc_stream_in_keyframes": (c_i32, [c_p, c_p, P(c_i32), c_i32, P(c_i64), c_p]),
+    "sc_stream_in_poses": (c_i32, [c_p, c_p, P(c_p), P(Pose), c_i32, P(Intrinsics), P(c_i64), c_p]),
     "sc_get_keyframe_blocks": (c_i32, [c_p, c_i32, c_p, c_i32, P(c_i32), c_p]),
     "sc_sdf_loss": (c_i32, [c_p, c_p, c_i64, c_f, c_p, c_p, c_p]),
     "sc_sdf_adjoint": (c_i32, [c_p, P(c_i32), P(c_p), P(Pose), c_i32, P(Intrinsics), c_p, c_p, c_p, c_p]),

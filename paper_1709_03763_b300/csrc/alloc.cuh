@@ -194,8 +194,17 @@ __device__ inline void append_one(const DevVolume& V, int32_t* list, int32_t* co
 //   bool union_first(slot) : true the first time the batch reaches slot (batches only)
 //   int32_t* list, *count; uint32_t cap; int32_t* ulist, *ucount; uint32_t ucap
 // Must be called by all ALLOC_THREADS threads of the CTA.
-template <typename Sink>
-__device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, int ty, Sink& sk, AllocShared& sh) {
+// The camera's block: 32-bit set keys are relative to it.
+__device__ __forceinline__ int3 cam_block(const KfCam& k) {
+    return make_int3(k.ti[0] >> 3, k.ti[1] >> 3, k.ti[2] >> 3);
+}
+
+// Phase A of a tile, shared by the allocation and the stream-in probe: clear the set,
+// insert every pixel's band-segment blocks, compact the occupied entries into uk
+// (n_keys of them).  Returns this thread's overflow flag (a key that did not fit, or a
+// camera so far out that its 32-bit keys could decode to invalid coordinates); the
+// CTA-wide flag is sh.overflow.  Must be called by all ALLOC_THREADS threads.
+__device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared& sh) {
     const int tid = threadIdx.x;
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY32_EMPTY;
     if (tid == 0) {
@@ -206,11 +215,9 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
         sh.overflow = 0;
     }
     __syncthreads();
-
-    // A: every pixel's band-segment blocks into the shared set
-    const int3 ref = make_int3(k.ti[0] >> 3, k.ti[1] >> 3, k.ti[2] >> 3);  // the camera's block
+    const int3 ref = cam_block(k);
     // every 32-bit key of this camera decodes to a valid block coordinate (else all its
-    // blocks take phase D, which checks each one)
+    // blocks take the overflow path, which checks each one)
     const bool ref_ok = coord_ok(ref.x - 512, ref.y - 512, ref.z - 512) && coord_ok(ref.x + 511, ref.y + 511, ref.z + 511);
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
     const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
@@ -232,6 +239,42 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS)
         if (sh.set[i] != KEY32_EMPTY) sh.uk[atomicAdd(&sh.n_keys, 1)] = i;
     __syncthreads();
+    return my_ovf;
+}
+
+// Every block of this thread's pixels that the shared set does not hold (the overflow
+// path): f(bx, by, bz) for each, coordinates checked.
+template <typename F>
+__device__ inline void tile_overflow_blocks(const DevVolume& V, const KfCam& k, int tx, int ty, const AllocShared& sh,
+                                            F&& f) {
+    const int tid = threadIdx.x;
+    const int3 ref = cam_block(k);
+    const bool ref_ok = coord_ok(ref.x - 512, ref.y - 512, ref.z - 512) && coord_ok(ref.x + 511, ref.y + 511, ref.z + 511);
+    const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
+    const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
+    for (int r = 0; r < ALLOC_PPT; ++r) {
+        const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
+        float Z = 0.f;
+        if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
+        if (!(Z > 0.f && Z < MAX_DEPTH)) continue;
+        for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
+            if (!coord_ok(bx, by, bz)) {
+                set_status(V.status, SC_ERR_INVALID_ARG);
+                return;
+            }
+            uint32_t kk;
+            if (ref_ok && key32(bx, by, bz, ref, &kk) && set_contains(sh.set, kk)) return;
+            f(bx, by, bz);
+        });
+    }
+}
+
+template <typename Sink>
+__device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, int ty, Sink& sk, AllocShared& sh) {
+    const int tid = threadIdx.x;
+    // A: every pixel's band-segment blocks into the shared set
+    const bool my_ovf = tile_collect(k, tx, ty, sh);
+    const int3 ref = cam_block(k);
     const int nk = sh.n_keys;
 
     // B: claim each unique key; the tile's new entries get consecutive slots
@@ -292,32 +335,19 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     }
 
     // D: keys that did not fit in the shared set
-    const bool ovf = sh.overflow != 0;
-    if (ovf && my_ovf) {
-        for (int r = 0; r < ALLOC_PPT; ++r) {
-            const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
-            float Z = 0.f;
-            if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
-            if (!(Z > 0.f && Z < MAX_DEPTH)) continue;
-            for_each_segment_block(k, u, v, Z, [&](int bx, int by, int bz) {
-                if (!coord_ok(bx, by, bz)) {
-                    set_status(V.status, SC_ERR_INVALID_ARG);
-                    return;
-                }
-                uint32_t kk;
-                if (ref_ok && key32(bx, by, bz, ref, &kk) && set_contains(sh.set, kk)) return;
-                const unsigned long long key = pack_key(bx, by, bz);
-                bool won;
-                int32_t seen;
-                const int e = hash_claim(V, key, &won, &seen);
-                if (e < 0) return;
-                if (won) publish(V, e, key, atomicAdd(V.pool_count, 1u));
-                const int32_t slot = seen >= 0 ? seen : entry_slot(V, e);
-                if (slot < 0) return;
-                if (sk.list_first(slot)) append_one(V, sk.list, sk.count, sk.cap, slot);
-                if (Sink::kUnion && sk.union_first(slot)) append_one(V, sk.ulist, sk.ucount, sk.ucap, slot);
-            });
-        }
+    if (sh.overflow != 0 && my_ovf) {
+        tile_overflow_blocks(V, k, tx, ty, sh, [&](int bx, int by, int bz) {
+            const unsigned long long key = pack_key(bx, by, bz);
+            bool won;
+            int32_t seen;
+            const int e = hash_claim(V, key, &won, &seen);
+            if (e < 0) return;
+            if (won) publish(V, e, key, atomicAdd(V.pool_count, 1u));
+            const int32_t slot = seen >= 0 ? seen : entry_slot(V, e);
+            if (slot < 0) return;
+            if (sk.list_first(slot)) append_one(V, sk.list, sk.count, sk.cap, slot);
+            if (Sink::kUnion && sk.union_first(slot)) append_one(V, sk.ulist, sk.ucount, sk.ucap, slot);
+        });
     }
     __syncthreads();  // shared state is reused by the CTA's next tile
 }

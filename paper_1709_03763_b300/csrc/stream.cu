@@ -23,6 +23,7 @@
 #include <cmath>
 #include <vector>
 
+#include "alloc.cuh"
 #include "volume.cuh"
 
 struct sc_block_store {
@@ -42,6 +43,12 @@ struct sc_block_store {
     uint32_t* mark;     // [cap] store entries named by the keyframes of one stream-in (0 between calls)
     int32_t* dlist;     // [cap] device list of those entries
     int32_t* dcount;    // [1]
+    // device hash index of the stored blocks: block key -> store entry, open addressing
+    // (icap = a power of two >= 2 cap entries; deleted entries become tombstones that
+    // later inserts reuse)
+    unsigned long long* ikey;  // [icap]
+    int32_t* ival;             // [icap]
+    uint32_t imask;            // icap - 1
     // host bookkeeping
     std::vector<int32_t> free_ids;
     std::vector<uint8_t> used;
@@ -73,6 +80,53 @@ __host__ __device__ inline bool outside_sphere(int bx, int by, int bz, float s, 
     volatile float a = xx + yy;
     return a + zz > r2;
 #endif
+}
+
+constexpr unsigned long long IDX_TOMB = ~1ull;  // a deleted index entry (never a block key)
+
+// The store index's device view.
+struct StoreIndex {
+    unsigned long long* key;
+    int32_t* val;
+    uint32_t mask;
+};
+
+// Insert a stored block's key (keys are unique: a block is stored at most once).
+__device__ inline void index_insert(const StoreIndex& I, unsigned long long key, int32_t e) {
+    uint32_t h = hash_bucket(key, I.mask);
+    for (uint32_t i = 0; i <= I.mask; ++i) {
+        const unsigned long long k = I.key[h];
+        if ((k == KEY_EMPTY || k == IDX_TOMB) && atomicCAS(&I.key[h], k, key) == k) {
+            I.val[h] = e;
+            return;
+        }
+        if (k != KEY_EMPTY && k != IDX_TOMB) h = (h + 1) & I.mask;  // occupied: next; lost a race: re-read
+    }
+}
+
+// Store entry of a key, or -1.
+__device__ inline int32_t index_find(const StoreIndex& I, unsigned long long key) {
+    uint32_t h = hash_bucket(key, I.mask);
+    for (uint32_t i = 0; i <= I.mask; ++i) {
+        const unsigned long long k = I.key[h];
+        if (k == key) return I.val[h];
+        if (k == KEY_EMPTY) return -1;
+        h = (h + 1) & I.mask;
+    }
+    return -1;
+}
+
+__device__ inline void index_remove(const StoreIndex& I, unsigned long long key) {
+    uint32_t h = hash_bucket(key, I.mask);
+    for (uint32_t i = 0; i <= I.mask; ++i) {
+        const unsigned long long k = I.key[h];
+        if (k == key) {
+            I.key[h] = IDX_TOMB;
+            return;
+        }
+        if (k == KEY_EMPTY) return;
+        h = (h + 1) & I.mask;
+    }
 }
 
 // copy one block's payload between two (slot-indexed) block arrays, one warp
@@ -109,14 +163,17 @@ __global__ void so_mark_kernel(DevVolume V, uint32_t n, float s, float cx, float
 
 // evicted block i -> store entry ext[i]
 __global__ void so_copy_out_kernel(DevVolume V, const int32_t* ev, const int32_t* ext, int32_t n_out, int4* st_coord,
-                                   uint32_t* st_flags, float* st_D, float* st_W, void* st_C, int32_t* remap) {
+                                   uint32_t* st_flags, float* st_D, float* st_W, void* st_C, int32_t* remap,
+                                   StoreIndex I) {
     const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < n_out; i += gridDim.x * wpb) {
         const int32_t slot = ev[i], e = ext[i];
         if (lane == 0) {
-            st_coord[e] = V.coord[slot];
+            const int4 c = V.coord[slot];
+            st_coord[e] = c;
             st_flags[e] = V.flags[slot];
             remap[slot] = -(e + 2);
+            index_insert(I, pack_key(c.x, c.y, c.z), e);
         }
         copy_block(lane, V.colour_f32 != 0, V.D, V.W, V.colour_f32 ? (const void*)V.Cf : (const void*)V.C8,
                    (size_t)slot, st_D, st_W, st_C, (size_t)e);
@@ -199,7 +256,7 @@ __global__ void clear_table_kernel(HashEntry* t, size_t n) {
 // stored entries ext[0..k) back into the pool
 __global__ void si_copy_in_kernel(DevVolume V, const int32_t* ext, int32_t k, const int4* st_coord,
                                   const uint32_t* st_flags, const float* st_D, const float* st_W, const void* st_C,
-                                  int32_t* ext2slot, int32_t* slot_out) {
+                                  int32_t* ext2slot, int32_t* slot_out, StoreIndex I) {
     const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
     for (int i = blockIdx.x * wpb + (threadIdx.x >> 5); i < k; i += gridDim.x * wpb) {
         const int32_t e = ext[i];
@@ -222,6 +279,7 @@ __global__ void si_copy_in_kernel(DevVolume V, const int32_t* ext, int32_t k, co
                     V.flags[s] = st_flags[e];
                     V.stamp[s] = 0u;
                     slot = (int32_t)s;
+                    index_remove(I, pack_key(c.x, c.y, c.z));
                 }
             }
         }
@@ -265,6 +323,30 @@ __global__ void collect_ext_kernel(KfLists L, int n_lists, uint32_t cap, uint32_
             const int32_t e = L.list[l][i];
             if (e <= -2 && atomicExch(&mark[-e - 2], 1u) == 0u) out[atomicAdd(count, 1)] = -e - 2;
         }
+    }
+}
+
+// The stored blocks that allocating A(k, T) for cameras cams[0..n) would reach: the
+// allocation's own tile walk (tile_collect), each unique key looked up in the store
+// index; each entry found is listed once.  Persistent over (camera, tile).
+__global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) si_probe_kernel(
+        DevVolume V, const KfCam* cams, int n, int tiles_x, int tiles, StoreIndex I, uint32_t* mark, int32_t* out,
+        int32_t* count) {
+    __shared__ AllocShared sh;
+    for (int w = blockIdx.x; w < n * tiles; w += gridDim.x) {
+        const int i = w / tiles, t = w - i * tiles;
+        const KfCam& k = cams[i];
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        const bool my_ovf = tile_collect(k, tx, ty, sh);
+        const int3 ref = cam_block(k);
+        auto hit = [&](unsigned long long key) {
+            const int32_t e = index_find(I, key);
+            if (e >= 0 && atomicExch(&mark[e], 1u) == 0u) out[atomicAdd(count, 1)] = e;
+        };
+        for (int j = threadIdx.x; j < sh.n_keys; j += ALLOC_THREADS) hit(key64_of(sh.set[sh.uk[j]], ref));
+        if (sh.overflow != 0 && my_ovf)
+            tile_overflow_blocks(V, k, tx, ty, sh, [&](int bx, int by, int bz) { hit(pack_key(bx, by, bz)); });
+        __syncthreads();  // shared state is reused by the CTA's next tile
     }
 }
 
@@ -336,6 +418,12 @@ extern "C" int sc_create_block_store(int64_t capacity, int32_t colour_format, sc
     if (e == cudaSuccess) e = cudaMemset(S->mark, 0, cap * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&S->dlist, cap * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&S->dcount, sizeof(int32_t));
+    size_t icap = 1024;
+    while (icap < 2 * cap) icap *= 2;
+    S->imask = (uint32_t)(icap - 1);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S->ikey, icap * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(S->ikey, 0xff, icap * sizeof(unsigned long long));  // KEY_EMPTY
+    if (e == cudaSuccess) e = cudaMalloc((void**)&S->ival, icap * sizeof(int32_t));
     if (e != cudaSuccess) {
         sc_destroy_block_store(S);
         return cuda_status(e);
@@ -362,6 +450,8 @@ extern "C" int sc_destroy_block_store(sc_block_store* S) {
     if (S->mark) cudaFree(S->mark);
     if (S->dlist) cudaFree(S->dlist);
     if (S->dcount) cudaFree(S->dcount);
+    if (S->ikey) cudaFree(S->ikey);
+    if (S->ival) cudaFree(S->ival);
     delete S;
     return SC_OK;
 }
@@ -413,7 +503,7 @@ extern "C" int sc_stream_out(sc_volume* V, sc_block_store* S, const float* centr
             const uint32_t n_live = n - (uint32_t)n_out;
             const int wgrid = std::min((n_out + 7) / 8, V->num_sms * 16);
             so_copy_out_kernel<<<wgrid, 256, 0, s>>>(V->dv, X.ev, S->ext, n_out, S->coord, S->flags, S->D, S->W, S->C,
-                                                     X.remap);
+                                                     X.remap, StoreIndex{S->ikey, S->ival, S->imask});
             so_plan_kernel<<<grid, 256, 0, s>>>(n, n_live, X.out, X.holes, X.movers, X.cnt);
             so_move_kernel<<<wgrid, 256, 0, s>>>(V->dv, X.holes, X.movers, X.cnt, X.remap);
             dim3 lg;
@@ -448,7 +538,7 @@ namespace {
 int stream_in_entries(sc_volume* V, sc_block_store* S, int32_t k, int64_t* n_moved, cudaStream_t s) {
     const int wgrid = std::min((k + 7) / 8, V->num_sms * 16);
     si_copy_in_kernel<<<wgrid, 256, 0, s>>>(V->dv, S->ext, k, S->coord, S->flags, S->D, S->W, S->C, S->ext2slot,
-                                            S->slot_out);
+                                            S->slot_out, StoreIndex{S->ikey, S->ival, S->imask});
     dim3 lg;
     const int n_lists = lists_launch_shape(V, &lg);
     unmap_lists_kernel<<<lg, 256, 0, s>>>(V->lists, V->list_counts, n_lists, V->p.max_blocks_per_keyframe,
@@ -474,6 +564,21 @@ int stream_in_entries(sc_volume* V, sc_block_store* S, int32_t k, int64_t* n_mov
 
 bool stream_args_ok(sc_volume* V, sc_block_store* S) {
     return V && S && S->colour_f32 == (V->p.colour_format == SC_RGB_F32) && S->device == V->device;
+}
+
+// Stream in the S->dcount entries collected in S->dlist (marked in S->mark): copy the
+// list to the host staging, clear the marks, move the blocks.
+int stream_in_collected(sc_volume* V, sc_block_store* S, int64_t* n_moved, cudaStream_t s) {
+    int32_t k = 0;
+    SC_CUDA(cudaMemcpyAsync(&k, S->dcount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    SC_CUDA(cudaStreamSynchronize(s));
+    if (k == 0) return read_status(V, s);
+    SC_CUDA(cudaMemcpyAsync(S->ext, S->dlist, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    unmark_kernel<<<std::min((k + 255) / 256, 1024), 256, 0, s>>>(S->dlist, k, S->mark);
+    count_launches(1);
+    SC_CUDA(cudaGetLastError());
+    SC_CUDA(cudaStreamSynchronize(s));
+    return stream_in_entries(V, S, k, n_moved, s);
 }
 
 }  // namespace
@@ -523,14 +628,36 @@ extern "C" int sc_stream_in_keyframes(sc_volume* V, sc_block_store* S, const int
         count_launches(1);
         SC_CUDA(cudaGetLastError());
     }
-    int32_t k = 0;
-    SC_CUDA(cudaMemcpyAsync(&k, S->dcount, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    SC_CUDA(cudaStreamSynchronize(s));
-    if (k == 0) return read_status(V, s);
-    SC_CUDA(cudaMemcpyAsync(S->ext, S->dlist, (size_t)k * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-    unmark_kernel<<<std::min((k + 255) / 256, 1024), 256, 0, s>>>(S->dlist, k, S->mark);
+    return stream_in_collected(V, S, n_moved, s);
+}
+
+extern "C" int sc_stream_in_poses(sc_volume* V, sc_block_store* S, const float* const* depths, const sc_pose* poses,
+                                  int32_t n, const sc_intrinsics* K, int64_t* n_moved, sc_stream stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!stream_args_ok(V, S) || n < 0 || (n > 0 && (!depths || !poses)) || !intrinsics_ok(K) || !n_moved)
+        return SC_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!depths[i]) return SC_ERR_INVALID_ARG;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 4; ++c)
+                if (!std::isfinite(poses[i].m[r][c])) return SC_ERR_INVALID_ARG;
+    }
+    SC_CUDA(cudaSetDevice(V->device));
+    *n_moved = 0;
+    if (n == 0 || S->count == 0) return read_status(V, s);
+    std::vector<KfCam> h(n);
+    for (int i = 0; i < n; ++i) h[i] = make_cam(V, K, &poses[i], depths[i], nullptr);
+    KfCam* d = nullptr;
+    SC_CUDA(cudaMallocAsync((void**)&d, n * sizeof(KfCam), s));
+    SC_CUDA(cudaMemcpyAsync(d, h.data(), n * sizeof(KfCam), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaMemsetAsync(S->dcount, 0, sizeof(int32_t), s));
+    const int tiles_x = (K->width + ALLOC_TX - 1) / ALLOC_TX;
+    const int tiles = tiles_x * ((K->height + ALLOC_TY - 1) / ALLOC_TY);
+    si_probe_kernel<<<V->num_sms * SC_ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
+        V->dv, d, n, tiles_x, tiles, StoreIndex{S->ikey, S->ival, S->imask}, S->mark, S->dlist, S->dcount);
     count_launches(1);
-    SC_CUDA(cudaGetLastError());
-    SC_CUDA(cudaStreamSynchronize(s));
-    return stream_in_entries(V, S, k, n_moved, s);
+    const cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(d, s);
+    SC_CUDA(e);
+    return stream_in_collected(V, S, n_moved, s);
 }

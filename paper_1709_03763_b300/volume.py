@@ -329,6 +329,17 @@ class Volume:
               "sc_stream_in_keyframes")
         return n.value
 
+    def stream_in_poses(self, store: "BlockStore", depths, poses, intr, stream=None) -> int:
+        """Move back the stored blocks that allocating A(k, T) for these keyframe depth
+        images (device [n,H,W] or a list) at these poses would reach."""
+        n = len(poses)
+        dp = (ctypes.c_void_p * max(n, 1))(*[_dev(depths[i], torch.float32, "depth") for i in range(n)])
+        pz = (Pose * max(n, 1))(*[make_pose(p) for p in poses])
+        moved = ctypes.c_int64(0)
+        check(lib().sc_stream_in_poses(self.h, store.h, dp, pz, n, ctypes.byref(make_intrinsics(intr)),
+                                       ctypes.byref(moved), _stream(stream)), "sc_stream_in_poses")
+        return moved.value
+
     def keyframe_blocks(self, kf_id: int, stream=None) -> torch.Tensor:
         """Pool slots of kf_id's stored block list (its allocation set A(k, T))."""
         n = ctypes.c_int32(0)

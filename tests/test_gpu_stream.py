@@ -163,3 +163,66 @@ def test_store_capacity_and_empty_cases():
         V.stream_out(BlockStore(16, "f32"), _camera(w.kf_poses[0]), 0.0)
     for x in (V, small, big):
         x.close()
+
+
+def test_stream_in_poses_brings_back_exactly_what_the_new_allocation_reaches():
+    # Section 4.3: before re-integrating keyframes at updated poses, the blocks their
+    # lists name (sc_stream_in_keyframes) and the stored blocks the updated poses'
+    # allocation reaches (sc_stream_in_poses, the allocation's own walk) are brought in;
+    # the batch then allocates no second copy of a stored block (streaming everything
+    # back raises no conflict), equals the unstreamed volume bit for bit, and every
+    # block the poses brought in is in some updated keyframe's new block list
+    w = synthetic.workload_tiny()
+    V, R = _volume(w), _volume(w)
+    K = 6
+    for k in range(K):
+        for vol in (V, R):
+            vol.integrate(k, w.kf_depth[k].cuda(), w.kf_rgba[k].cuda(), w.intr, w.kf_poses[k])
+    g = synthetic.rng(1, 78)
+    new = w.kf_poses[:K].copy()
+    for k in range(K):
+        new[k] = synthetic.perturb_pose(w.kf_poses[k], np.radians(2.0), 0.05, g).astype(np.float32)
+    S = BlockStore(1 << 14, "f32")
+    cam = _camera(w.kf_poses[K - 1])
+    V.stream_out(S, cam, 0.7)
+    ids = [1, 2, 3]
+    D = torch.stack([w.kf_depth[k] for k in ids]).cuda()
+    C = torch.stack([w.kf_rgba[k] for k in ids]).cuda()
+    key = lambda c: {tuple(x) for x in c.tolist()}
+    V.stream_in_keyframes(S, ids)
+    mid = key(V.extract(payload=False)["coords"].cpu())
+    n_pose = V.stream_in_poses(S, D, new[ids], w.intr)
+    after = key(V.extract(payload=False)["coords"].cpu())
+    brought = after - mid
+    assert n_pose == len(brought) > 0
+    assert V.stream_in_poses(S, D, new[ids], w.intr) == 0  # nothing left to bring in for them
+    for vol in (V, R):
+        vol.reintegrate_batch(ids, D, C, w.kf_poses[ids], new[ids], w.intr)
+    ex = V.extract(payload=False)
+    slot2c = dict(zip(ex["slots"].cpu().tolist(), map(tuple, ex["coords"].cpu().tolist())))
+    listed = set()
+    for k in ids:
+        listed |= {slot2c[s] for s in V.keyframe_blocks(k).cpu().tolist()}
+    assert brought <= listed
+    V.stream_in(S, cam)  # everything back: raises SC_ERR_CONFLICT on a duplicated block
+    assert len(S) == 0
+    _same(_by_key(V.extract()), _by_key(R.extract()))
+    for x in (V, R, S):
+        x.close()
+
+
+def test_stream_in_poses_argument_errors():
+    w = synthetic.workload_tiny()
+    V = _volume(w)
+    S = BlockStore(64, "f32")
+    d = w.kf_depth[:1].cuda()
+    assert V.stream_in_poses(S, d[:0], w.kf_poses[:0], w.intr) == 0  # nothing to do
+    bad = w.kf_poses[:1].copy()
+    bad[0, 0, 3] = np.nan
+    with pytest.raises(SurfcorrError):
+        V.stream_in_poses(S, d, bad, w.intr)
+    S2 = BlockStore(64, "rgba8")  # colour format of another volume kind
+    with pytest.raises(SurfcorrError):
+        V.stream_in_poses(S2, d, w.kf_poses[:1], w.intr)
+    for x in (V, S, S2):
+        x.close()
