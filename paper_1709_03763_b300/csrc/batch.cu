@@ -288,13 +288,16 @@ __device__ __forceinline__ void net_delta_group(const NdCam* cams, int n, const 
                                                 uint32_t mw0, uint32_t mw1, int mw, Acc& A, bool& touched) {
     const int half = mw / 2;
     const float vx = (float)(8 * c.x + lx0), vy = (float)(8 * c.y + ly), vz = (float)(8 * c.z + lz);
-    for (int w = 0; w < half; ++w) {
+    // only the words with a bit set, in increasing word order (old words come first, so
+    // the items keep their order); lane w holds word w, lane w - 32 word w >= 32
+    unsigned long long nzw = (unsigned long long)__ballot_sync(0xffffffffu, mw0 != 0u) |
+                             ((unsigned long long)__ballot_sync(0xffffffffu, mw1 != 0u) << 32);
+    while (nzw) {
+        const int w = __ffsll(nzw) - 1;
+        nzw &= nzw - 1;
         const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        net_delta_word<-1>(cams + (w << 5), word, vx, vy, vz, A, touched);
-    }
-    for (int w = half; w < mw; ++w) {
-        const uint32_t word = __shfl_sync(0xffffffffu, w < 32 ? mw0 : mw1, w & 31);
-        net_delta_word<1>(cams + n + ((w - half) << 5), word, vx, vy, vz, A, touched);
+        if (w < half) net_delta_word<-1>(cams + (w << 5), word, vx, vy, vz, A, touched);
+        else net_delta_word<1>(cams + n + ((w - half) << 5), word, vx, vy, vz, A, touched);
     }
 }
 
