@@ -213,26 +213,31 @@ struct NdAccWide {
 };
 
 // One item's contribution to the 4 voxels, given their projection and texels.
+// Branch-free: the decision of decide() (ok, Z > 0, eta >= -mu; eta is finite whenever
+// ok and Z > 0) selects the contribution, and a voxel that is not updated adds exactly
+// zero (its distance sum is never -0, so +0 leaves it bit for bit).
 template <int SIGN>
 __device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], NdAcc& A,
                                                bool& touched) {
+    const float mu = k.mu;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float d, eta;
-        if (decide(k, P.ok[j], __uint_as_float(t[j].x), P.pz[j], d, eta)) {
-            touched = true;
-            const uint32_t cw = t[j].y;
-            const uint32_t rb = cw & 0x00FF00FFu;
-            const uint32_t gw = ((cw >> 8) & 0xFFu) | 0x10000u;
-            if (SIGN > 0) {
-                A.aD[j] = __fadd_rn(A.aD[j], d);
-                A.rb[j] += rb;
-                A.gw[j] += gw;
-            } else {
-                A.aD[j] = __fsub_rn(A.aD[j], d);
-                A.rb[j] -= rb;
-                A.gw[j] -= gw;
-            }
+        const float Z = __uint_as_float(t[j].x);
+        const float eta = __fsub_rn(Z, P.pz[j]);
+        const bool up = P.ok[j] && Z > 0.f && eta >= -mu;
+        const float d = up ? fminf(eta, mu) : 0.f;
+        const uint32_t cw = t[j].y;
+        const uint32_t rb = up ? (cw & 0x00FF00FFu) : 0u;
+        const uint32_t gw = up ? (((cw >> 8) & 0xFFu) | 0x10000u) : 0u;
+        touched |= up;
+        if (SIGN > 0) {
+            A.aD[j] = __fadd_rn(A.aD[j], d);
+            A.rb[j] += rb;
+            A.gw[j] += gw;
+        } else {
+            A.aD[j] = __fsub_rn(A.aD[j], d);
+            A.rb[j] -= rb;
+            A.gw[j] -= gw;
         }
     }
 }
@@ -260,7 +265,8 @@ __device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, c
 __device__ __forceinline__ void net_delta_fetch(const NdCam& k, float vx, float vy, float vz, Proj4& P, uint2 t[4]) {
     project4(k, vx, vy, vz, P);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) t[j] = P.ok[j] ? __ldg(k.tex + P.pix[j]) : make_uint2(0u, 0u);
+    // unconditional: a voxel outside the image has pix 0, whose texel is read and ignored
+    for (int j = 0; j < 4; ++j) t[j] = __ldg(k.tex + P.pix[j]);
 }
 
 // Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over the items whose
@@ -374,29 +380,28 @@ __device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_
             *reinterpret_cast<float4*>(V.Cf + cb + ch * NVOX) = Cf;
         }
     } else {
+        // branch-free: every voxel's new value is computed and selected (a voxel without
+        // a net change keeps its bytes; W' = 0 empties it)
         uint32_t* Cp = &Cv.x;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            if (aW[j] == 0.f && aC[j][0] == 0.f && aC[j][1] == 0.f && aC[j][2] == 0.f) continue;
-            if (!nz[j]) {
-                Cp[j] = 0u;
-                continue;
-            }
+            const bool ch_any = aW[j] != 0.f || aC[j][0] != 0.f || aC[j][1] != 0.f || aC[j][2] != 0.f;
             uint32_t out = 0;
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
                 const float a = (float)((Cp[j] >> (8 * ch)) & 255u);
                 out |= u8_sat(__fmul_rn(__fmaf_rn(a, Wp[j], aC[j][ch]), rW[j])) << (8 * ch);
             }
-            Cp[j] = out;
+            Cp[j] = ch_any ? (nz[j] ? out : 0u) : Cp[j];
         }
         __stcs(reinterpret_cast<uint4*>(V.C8 + off), Cv);
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if (aW[j] == 0.f && A.aD[j] == 0.f) continue;
-        Dp[j] = nz[j] ? __fmul_rn(__fmaf_rn(Dp[j], Wp[j], A.aD[j]), rW[j]) : 0.f;
-        Wp[j] = Wn[j];
+        const bool d_any = aW[j] != 0.f || A.aD[j] != 0.f;
+        const float Dn = nz[j] ? __fmul_rn(__fmaf_rn(Dp[j], Wp[j], A.aD[j]), rW[j]) : 0.f;
+        Dp[j] = d_any ? Dn : Dp[j];
+        Wp[j] = d_any ? Wn[j] : Wp[j];
     }
     __stcs(reinterpret_cast<float4*>(V.D + off), Dv);
     __stcs(reinterpret_cast<float4*>(V.W + off), Wv);
