@@ -507,7 +507,7 @@ int sc_sdf_adjoint(sc_volume* vol, const int32_t* kf_ids, const float* const* de
  * start-up, an application whose device memory belongs to another allocator.  Same
  * arguments and results as sc_sdf_adjoint (the caller still passes grad_D, grad_xi
  * and grad_depth); its keyframe table and accumulators live in a file-scope device
- * array of about 60 KB that every GPU loading the library holds until the process
+ * array of about 76 KB that every GPU loading the library holds until the process
  * exits.
  *   - n <= 256 keyframes; more returns SC_ERR_CAPACITY and launches nothing.
  *   - The volume's device must be the current device (else SC_ERR_INVALID_ARG).

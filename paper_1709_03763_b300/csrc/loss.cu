@@ -225,7 +225,9 @@ struct AdjItem {
     float* grad_depth;  // [H][W] or null
 };
 
-// acc [n][4]: sum g, sum g qx, sum g qy, sum g qz  (q = voxel - camera, voxel units).
+// acc [n][4]: sum g, sum g mx, sum g my, sum g mz  (m = i - ti, the voxel index relative
+// to the camera's integer voxel, exact in float; the finalize subtracts tf sum g to get
+// the sums over q = m - tf, the voxel relative to the camera in voxel units).
 // Grid (chunks, n): blockIdx.y is the keyframe; the chunk's warps stride over its
 // block list, one warp per block (4 voxels per lane per group); lane sums are float,
 // the warp and CTA reductions double, one set of 4 atomics per CTA.
@@ -260,6 +262,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, SC_ADJ_MIN_BLOCKS) adjoint_kernel
             lane_voxels(lane, g, lx0, ly, lz);
             const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
             const int iy = 8 * c.y + ly, iz = 8 * c.z + lz;
+            // the lane's 4 voxels share y and z; their x runs mx0 .. mx0 + 3 (exact floats)
+            const float mx0 = (float)(8 * c.x + lx0 - cam.ti[0]);
             // the lane's 4 voxels are contiguous: one 16-byte load each of dL/dD and W,
             // issued before the projection so that their latency overlaps it
             const float4 g4 = __ldg(reinterpret_cast<const float4*>(grad + off));
@@ -270,23 +274,25 @@ __global__ void __launch_bounds__(ADJ_THREADS, SC_ADJ_MIN_BLOCKS) adjoint_kernel
             float Z[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) Z[j] = P.ok[j] ? __ldg(cam.depth + P.pix[j]) : 0.f;
+            // branch-free: the update decision of decide() (ok, Z > 0, eta >= -mu; eta is
+            // finite whenever ok and Z > 0) and no clamp (eta < mu) select the sample; a
+            // zero cotangent contributes nothing and is never divided by its voxel's W
+            // (an unobserved voxel has W = 0)
+            float ag = 0.f, agx = 0.f;
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                float d, eta;
-                const int pix = P.pix[j];
-                const int ix = 8 * c.x + lx0 + j;
-                if (!decide(cam, P.ok[j], Z[j], P.pz[j], d, eta)) continue;
-                if (!(eta < cam.mu)) continue;  // clamped: no derivative
-                // a zero cotangent contributes nothing (and is skipped before the
-                // division, so an unobserved voxel with W = 0 never divides by it)
-                if (gj[j] == 0.f) continue;
-                const float gv = __fdiv_rn(gj[j], wj[j]);
-                if (it.grad_depth) atomicAdd(it.grad_depth + pix, gv);
-                a0 += gv;
-                a1 = fmaf(gv, __fsub_rn((float)(ix - cam.ti[0]), cam.tf[0]), a1);
-                a2 = fmaf(gv, __fsub_rn((float)(iy - cam.ti[1]), cam.tf[1]), a2);
-                a3 = fmaf(gv, __fsub_rn((float)(iz - cam.ti[2]), cam.tf[2]), a3);
+                const float eta = __fsub_rn(Z[j], P.pz[j]);
+                const bool on = P.ok[j] & (Z[j] > 0.f) & (eta >= -cam.mu) & (eta < cam.mu) & (gj[j] != 0.f);
+                // one approximate reciprocal (1 ulp) per sample instead of a division
+                const float gv = on ? __fmul_rn(gj[j], rcp_approx(wj[j])) : 0.f;
+                if (on && it.grad_depth) atomicAdd(it.grad_depth + P.pix[j], gv);
+                ag += gv;
+                agx = fmaf(gv, mx0 + (float)j, agx);
             }
+            a0 += ag;
+            a1 += agx;
+            a2 = fmaf(ag, (float)(iy - cam.ti[1]), a2);
+            a3 = fmaf(ag, (float)(iz - cam.ti[2]), a3);
         }
         d0 += a0;
         d1 += a1;
@@ -312,6 +318,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, SC_ADJ_MIN_BLOCKS) adjoint_kernel
 struct AdjPose {
     double r3[3];
     double t[3];
+    double tf[3];  // the camera's fractional voxel offset (KfCam tf)
 };
 
 __global__ void adjoint_finalize_kernel(const AdjPose* poses, const double* acc, int n, double s, double* grad_xi) {
@@ -320,7 +327,9 @@ __global__ void adjoint_finalize_kernel(const AdjPose* poses, const double* acc,
     const double* r = poses[k].r3;
     const double* t = poses[k].t;
     const double A = acc[4 * k];
-    const double B[3] = {s * acc[4 * k + 1], s * acc[4 * k + 2], s * acc[4 * k + 3]};
+    const double* tf = poses[k].tf;
+    const double B[3] = {s * (acc[4 * k + 1] - tf[0] * A), s * (acc[4 * k + 2] - tf[1] * A),
+                         s * (acc[4 * k + 3] - tf[2] * A)};
     double* g = grad_xi + 6 * k;
     for (int j = 0; j < 3; ++j) g[j] = r[j] * A;
     const double bx[3] = {B[1] * r[2] - B[2] * r[1], B[2] * r[0] - B[0] * r[2], B[0] * r[1] - B[1] * r[0]};
@@ -428,6 +437,7 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
         for (int r = 0; r < 3; ++r) {
             A.poses_h[i].r3[r] = (double)poses[i].m[r][2];
             A.poses_h[i].t[r] = (double)poses[i].m[r][3];
+            A.poses_h[i].tf[r] = (double)A.items_h[i].cam.tf[r];
         }
     }
     SC_CUDA(cudaMemcpyAsync(A.items_d, A.items_h, n * sizeof(AdjItem), cudaMemcpyHostToDevice, s));
@@ -471,7 +481,7 @@ std::mutex g_adj_static_mu;
 
 }  // namespace
 
-// about 60 KB on every GPU that loads the library, held until the process exits
+// about 76 KB on every GPU that loads the library, held until the process exits
 static __device__ __align__(256) unsigned char g_adj_static[sizeof(AdjStatic)];
 
 extern "C" int sc_sdf_adjoint_noalloc(sc_volume* V, const int32_t* kf_ids, const float* const* depths,
@@ -516,6 +526,7 @@ extern "C" int sc_sdf_adjoint_noalloc(sc_volume* V, const int32_t* kf_ids, const
         for (int r = 0; r < 3; ++r) {
             poses_h[i].r3[r] = (double)poses[i].m[r][2];
             poses_h[i].t[r] = (double)poses[i].m[r][3];
+            poses_h[i].tf[r] = (double)items_h[i].cam.tf[r];
         }
     }
     SC_CUDA(cudaMemcpyAsync(S->items, items_h, n * sizeof(AdjItem), cudaMemcpyHostToDevice, s));
