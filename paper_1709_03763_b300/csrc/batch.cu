@@ -165,9 +165,19 @@ __device__ __forceinline__ void load_ndcam(NdCam& o, const KfCam& k) {
     o.tex = k.tex;
 }
 
-// Packed copies of the items' keyframes: (depth bits, RGBA8) per pixel, so that a
-// sample reads depth and colour with one 8-byte gather.
-__global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr, uint2* tex, uint32_t npx) {
+// Packed copies of the items' keyframes, one 8-byte texel per pixel so that a sample
+// reads depth and colour with one gather: x = the depth bits, with every invalid depth
+// (Z <= 0 or NaN) stored as -inf; y = RGB8 with the alpha byte set to 1 (it counts the
+// samples: see NdAcc).  Item i's texels start at tex + i * stride (stride = the pixel
+// count rounded up to even, > npx: 16-byte aligned) and texel npx is a sentinel (-inf,
+// 0) that voxels projecting outside the image read, so that eta = Z - z_c >= -mu alone
+// decides a sample (-inf never passes it).
+__device__ __forceinline__ uint2 pack_texel(float z, uint32_t c) {
+    return make_uint2(z > 0.f ? __float_as_uint(z) : 0xff800000u, (c & 0x00ffffffu) | 0x01000000u);
+}
+
+__global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr, uint2* tex, uint32_t npx,
+                                  uint32_t stride) {
     const uint32_t q = npx / 4;  // 640 x 480 and every width multiple of 4: float4 / uint4 loads
     const size_t total = (size_t)hdr->n * q;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -176,18 +186,20 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
         const KfCam& k = items[it].newc;
         const float4 d = __ldg(reinterpret_cast<const float4*>(k.depth + p));
         const uint4 c = __ldg(reinterpret_cast<const uint4*>(k.rgba + p));
-        uint4* o = reinterpret_cast<uint4*>(tex + (size_t)it * npx + p);
-        o[0] = make_uint4(__float_as_uint(d.x), c.x, __float_as_uint(d.y), c.y);
-        o[1] = make_uint4(__float_as_uint(d.z), c.z, __float_as_uint(d.w), c.w);
+        const uint2 t0 = pack_texel(d.x, c.x), t1 = pack_texel(d.y, c.y), t2 = pack_texel(d.z, c.z),
+                    t3 = pack_texel(d.w, c.w);
+        uint4* o = reinterpret_cast<uint4*>(tex + (size_t)it * stride + p);
+        o[0] = make_uint4(t0.x, t0.y, t1.x, t1.y);
+        o[1] = make_uint4(t2.x, t2.y, t3.x, t3.y);
     }
-    // remainder pixels (npx % 4)
-    const uint32_t r0 = q * 4;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)hdr->n * (npx - r0);
+    // remainder pixels (npx % 4) and each item's sentinel
+    const uint32_t r0 = q * 4, nr = npx - r0 + 1;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)hdr->n * nr;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int it = (int)(i / (npx - r0));
-        const uint32_t p = r0 + (uint32_t)(i % (npx - r0));
+        const int it = (int)(i / nr);
+        const uint32_t p = r0 + (uint32_t)(i % nr);
         const KfCam& k = items[it].newc;
-        tex[(size_t)it * npx + p] = make_uint2(__float_as_uint(k.depth[p]), k.rgba[p]);
+        tex[(size_t)it * stride + p] = p < npx ? pack_texel(k.depth[p], k.rgba[p]) : make_uint2(0xff800000u, 0u);
     }
 }
 
@@ -213,23 +225,23 @@ struct NdAccWide {
 };
 
 // One item's contribution to the 4 voxels, given their projection and texels.
-// Branch-free: the decision of decide() (ok, Z > 0, eta >= -mu; eta is finite whenever
-// ok and Z > 0) selects the contribution, and a voxel that is not updated adds exactly
-// zero (its distance sum is never -0, so +0 leaves it bit for bit).
+// Branch-free: the update decision of decide() is eta >= -mu on the packed texel
+// (invalid depth and voxels outside the image read -inf, in front of the camera or
+// not), and it selects the contribution; a voxel that is not updated adds exactly zero
+// (its distance sum is never -0, so +0 leaves it bit for bit).  The texel's bytes give
+// the packed lanes directly: r | b << 16 and g | 1 << 16 (the alpha byte is the count).
 template <int SIGN>
 __device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], NdAcc& A,
                                                bool& touched) {
     const float mu = k.mu;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const float Z = __uint_as_float(t[j].x);
-        const float eta = __fsub_rn(Z, P.pz[j]);
-        const bool up = P.ok[j] && Z > 0.f && eta >= -mu;
+        const float eta = __fsub_rn(__uint_as_float(t[j].x), P.pz[j]);
+        const bool up = eta >= -mu;
         const float d = up ? fminf(eta, mu) : 0.f;
-        const uint32_t cw = t[j].y;
-        const uint32_t rb = up ? (cw & 0x00FF00FFu) : 0u;
-        const uint32_t gw = up ? (((cw >> 8) & 0xFFu) | 0x10000u) : 0u;
-        touched |= up;
+        const uint32_t cw = up ? t[j].y : 0u;
+        const uint32_t rb = __byte_perm(cw, 0u, 0x4240);
+        const uint32_t gw = __byte_perm(cw, 0u, 0x4341);
         if (SIGN > 0) {
             A.aD[j] = __fadd_rn(A.aD[j], d);
             A.rb[j] += rb;
@@ -242,6 +254,7 @@ __device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, c
     }
 }
 
+// The same with separate integer sums (more than PACK_MAX_ITEMS bits on a block).
 template <int SIGN>
 __device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, const uint2 t[4], NdAccWide& A,
                                                bool& touched) {
@@ -264,9 +277,10 @@ __device__ __forceinline__ void net_delta_item(const NdCam& k, const Proj4& P, c
 // Projection of the 4 voxels into item k and the texels (depth bits, RGBA8) they sample.
 __device__ __forceinline__ void net_delta_fetch(const NdCam& k, float vx, float vy, float vz, Proj4& P, uint2 t[4]) {
     project4(k, vx, vy, vz, P);
+    // a voxel outside the image reads the item's sentinel texel (index W H)
+    const int sentinel = k.W * k.H;
 #pragma unroll
-    // unconditional: a voxel outside the image has pix 0, whose texel is read and ignored
-    for (int j = 0; j < 4; ++j) t[j] = __ldg(k.tex + P.pix[j]);
+    for (int j = 0; j < 4; ++j) t[j] = __ldg(k.tex + (P.ok[j] ? P.pix[j] : sentinel));
 }
 
 // Net change of the 4 voxels (lx0..lx0+3, ly, lz) of block c over the items whose
@@ -320,6 +334,17 @@ __device__ __forceinline__ void nd_unpack(const NdAccWide& A, int j, int& w, int
     c[1] = A.aC[j][1];
     c[2] = A.aC[j][2];
 }
+
+// Whether any of the 4 voxels has a net change (the packed sums track no "touched"
+// flag per sample: a voxel whose samples cancel exactly is left as it is, which is
+// what the read-modify-write would write back).
+__device__ __forceinline__ bool nd_changed(const NdAcc& A, bool touched) {
+    bool c = false;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) c |= (A.aD[j] != 0.f) | (A.rb[j] != PACK_BIAS) | (A.gw[j] != PACK_BIAS);
+    return c;
+}
+__device__ __forceinline__ bool nd_changed(const NdAccWide&, bool touched) { return touched; }
 
 __device__ __forceinline__ void nd_init(NdAcc& A) {
 #pragma unroll
@@ -430,7 +455,7 @@ __device__ __forceinline__ void nd_group(const DevVolume& V, const NdCam* cams, 
     nd_init(A);
     bool touched = false;
     net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, A, touched);
-    if (!touched && !fresh) return;
+    if (!nd_changed(A, touched) && !fresh) return;
     if (fresh) {  // first update of a new block: its memory holds no prior state
         Dv = make_float4(0.f, 0.f, 0.f, 0.f);
         Wv = Dv;
@@ -507,8 +532,9 @@ __global__ void net_delta_clear_kernel(DevVolume V, uint32_t* masks, int mw, con
 struct BatchState {
     int mw = 0;
     int32_t* zero = nullptr;  // a device word holding 0: the old-list length of integrate-only items
-    uint2* tex = nullptr;     // packed keyframe images [max_batch][tex_px]
-    uint32_t tex_px = 0;
+    uint2* tex = nullptr;     // packed keyframe images [max_batch][tex_stride]
+    uint32_t tex_px = 0;      // pixels per image
+    uint32_t tex_stride = 0;  // texels per item: tex_px rounded up to even, plus one sentinel
     uint32_t* masks = nullptr;
     int32_t* ulist = nullptr;
     int32_t* counters = nullptr;
@@ -605,7 +631,7 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
         *items_node = deps[0];
     }
     batch_init_kernel<<<4, 256, 0, s>>>(B->items_d, B->hdr_d, B->counters);
-    batch_pack_kernel<<<V->num_sms * 8, 256, 0, s>>>(B->items_d, B->hdr_d, B->tex, B->tex_px);
+    batch_pack_kernel<<<V->num_sms * 8, 256, 0, s>>>(B->items_d, B->hdr_d, B->tex, B->tex_px, B->tex_stride);
     if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[0], s, cudaEventRecordExternal);
     batch_alloc_kernel<<<V->num_sms * ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
         V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
@@ -698,8 +724,10 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         if (B->tex) cudaFree(B->tex);
         B->tex = nullptr;
         B->tex_px = 0;
-        SC_CUDA(cudaMalloc((void**)&B->tex, (size_t)V->p.max_batch * npx * sizeof(uint2)));
+        const uint32_t stride = (npx + 2) & ~1u;  // > npx, even: every item's texels 16-byte aligned
+        SC_CUDA(cudaMalloc((void**)&B->tex, (size_t)V->p.max_batch * stride * sizeof(uint2)));
         B->tex_px = npx;
+        B->tex_stride = stride;
         if (B->exec) {
             cudaGraphExecDestroy(B->exec);
             B->exec = nullptr;
@@ -715,7 +743,7 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         b.old_count = it.oldp ? count_ptr(V, it.kf_id, cur) : B->zero;
         b.new_list = list_ptr(V, it.kf_id, 1 - cur);
         b.new_count = count_ptr(V, it.kf_id, 1 - cur);
-        b.oldc.tex = b.newc.tex = B->tex + (size_t)i * npx;
+        b.oldc.tex = b.newc.tex = B->tex + (size_t)i * B->tex_stride;
     }
     if (++V->call_id == 0) V->call_id = 1;  // (plain calls reset stamps on wrap)
     B->hdr_h->n = n;

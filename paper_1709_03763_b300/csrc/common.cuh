@@ -177,8 +177,10 @@ __device__ __forceinline__ bool decide(const Cam& k, bool ok, float Z, float pz,
 }
 
 __device__ __forceinline__ uint32_t u8_sat(float x) {
-    // round half to even, saturate to [0, 255]
-    return (uint32_t)fminf(fmaxf(rintf(x), 0.f), 255.f);
+    // round half to even, saturate to [0, 255] (NaN -> 0): one conversion instruction
+    uint32_t r;
+    asm("cvt.rni.sat.u8.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r & 0xffu;
 }
 
 // Running weighted average with w = 1 (sign +1) or its inverse, Eq. 2 (sign -1).
