@@ -141,24 +141,26 @@ __global__ void batch_mark_old_kernel(DevVolume V, const BatchItem* items, const
 // The part of a keyframe camera the net-delta kernel samples with, kept in shared
 // memory (96 bytes; old cameras of items 0..n-1, then their new cameras).
 struct __align__(16) NdCam {
-    float Pr[9];
+    float2 Pxy[3];  // as in KfCam
+    float2 cxyh;
+    float Pz[3];
     float tf[3];
     float tiF[3];
-    float cxh, cyh, mu;
+    float mu;
     int W, H;
     const uint2* tex;
 };
+static_assert(sizeof(NdCam) == 96, "camera table entry: 96 bytes");
 
 __device__ __forceinline__ void load_ndcam(NdCam& o, const KfCam& k) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) o.Pr[i] = k.Pr[i];
-#pragma unroll
     for (int i = 0; i < 3; ++i) {
+        o.Pxy[i] = k.Pxy[i];
+        o.Pz[i] = k.Pz[i];
         o.tf[i] = k.tf[i];
         o.tiF[i] = k.tiF[i];
     }
-    o.cxh = k.cxh;
-    o.cyh = k.cyh;
+    o.cxyh = k.cxyh;
     o.mu = k.mu;
     o.W = k.W;
     o.H = k.H;

@@ -92,6 +92,9 @@ __device__ inline void set_status(int32_t* status, int32_t code) { atomicCAS(sta
 //   Pr = diag(fx, fy, 1) M   the projection rows: pi(p_c) = (Pr_0 q, Pr_1 q) / (Pr_2 q) + (cx, cy)
 //   segment endpoint in relative voxel units: Ms * pi^-1(x, z) + tf, Ms = R / voxel_size
 struct KfCam {
+    float2 Pxy[3];   // the first two rows of Pr by columns, as f32x2 pairs: (Pr[q], Pr[3 + q])
+    float2 cxyh;     // (cx + 1/2, cy + 1/2)
+    float Pz[3];     // the third row of Pr
     float Pr[9];
     float Ms[9];
     float tf[3];
@@ -143,22 +146,22 @@ __device__ __forceinline__ void project4(const Cam& k, float ix0, float iy, floa
     const float qx = __fsub_rn(__fsub_rn(ix0, k.tiF[0]), k.tf[0]);
     const float qy = __fsub_rn(__fsub_rn(iy, k.tiF[1]), k.tf[1]);
     const float qz = __fsub_rn(__fsub_rn(iz, k.tiF[2]), k.tf[2]);
-    float pz = __fmaf_rn(k.Pr[8], qz, __fmaf_rn(k.Pr[7], qy, __fmul_rn(k.Pr[6], qx)));
-    float px = __fmaf_rn(k.Pr[2], qz, __fmaf_rn(k.Pr[1], qy, __fmul_rn(k.Pr[0], qx)));
-    float py = __fmaf_rn(k.Pr[5], qz, __fmaf_rn(k.Pr[4], qy, __fmul_rn(k.Pr[3], qx)));
+    // the image-plane rows x and y as one f32x2 pair (each component the same
+    // round-to-nearest operation as its scalar form), the depth row alone
+    float pz = __fmaf_rn(k.Pz[2], qz, __fmaf_rn(k.Pz[1], qy, __fmul_rn(k.Pz[0], qx)));
+    float2 pxy = __ffma2_rn(k.Pxy[2], make_float2(qz, qz),
+                            __ffma2_rn(k.Pxy[1], make_float2(qy, qy), __fmul2_rn(k.Pxy[0], make_float2(qx, qx))));
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (j > 0) {
-            pz = __fadd_rn(pz, k.Pr[6]);
-            px = __fadd_rn(px, k.Pr[0]);
-            py = __fadd_rn(py, k.Pr[3]);
+            pz = __fadd_rn(pz, k.Pz[0]);
+            pxy = __fadd2_rn(pxy, k.Pxy[0]);
         }
         const float rz = rcp_approx(pz);
-        const float uu = __fmaf_rn(px, rz, k.cxh);
-        const float vv = __fmaf_rn(py, rz, k.cyh);
-        // nearest pixel and the range test in one: (unsigned) floor(u + 1/2) < W holds
-        // exactly when 0 <= u + 1/2 < W (NaN / inf fail it)
-        const int iu = floor_small(uu), iv = floor_small(vv);
+        // nearest pixel and the range test in one (floor_small on both coordinates):
+        // (unsigned) floor(u + 1/2) < W holds exactly when 0 <= u + 1/2 < W (NaN / inf fail it)
+        const float2 f = __fadd2_rd(__ffma2_rn(pxy, make_float2(rz, rz), k.cxyh), make_float2(8388608.f, 8388608.f));
+        const int iu = __float_as_int(f.x) - 0x4b000000, iv = __float_as_int(f.y) - 0x4b000000;
         p.pz[j] = pz;
         p.ok[j] = pz > 0.f && (unsigned)iu < (unsigned)k.W && (unsigned)iv < (unsigned)k.H;
         p.pix[j] = p.ok[j] ? iv * k.W + iu : 0;

@@ -6,9 +6,13 @@
 // Applying Eq. 1 sequentially gives exactly that ratio of sums, so the kernel
 // scatters both sums, interleaved per keyframe pixel, with one 8-byte vector float
 // atomic per pixel (order-free up to rounding) into pooled scratch, and a second pass
-// divides and writes Z* and W*.  One thread per 4 pixels of a frame row; up to 64
-// frames per launch.
+// divides and writes Z* and W*.  A frame taken at the keyframe's own pose (the first
+// of a KF_CONST group) maps every pixel onto itself, so it initialises the sums with
+// plain stores, which also replaces zeroing them.  One thread per 4 pixels of a frame
+// row; up to 64 frames per launch.
+#include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -20,10 +24,21 @@ constexpr int FUSE_MAX_FRAMES = 64;  // frames per launch (kernel parameter spac
 
 constexpr int FUSE_TX = 32, FUSE_TY = 8;
 
+
 struct FuseFrame {
     float Pr[9];  // keyframe_from_frame rotation R*^T R_i, rows 0 and 1 scaled by fx and fy
     float t[3];   // keyframe_from_frame translation R*^T (t_i - t*), scaled likewise
     int kf;       // output keyframe image
+    int src;      // input frame index
+};
+
+// Frames whose pose is the keyframe's own (the first frame of a KF_CONST group, R6):
+// their warp is the identity, x* = x and Z*_p = z (exactly, in float as in exact
+// arithmetic), so each keyframe's first such frame initialises the sums with plain
+// stores instead of a memset followed by atomics.
+constexpr int FUSE_MAX_INIT = 1024;  // keyframe images per init launch (kernel parameter space)
+struct FuseInit {
+    int src[FUSE_MAX_INIT];  // per keyframe image: its identity frame, or -1 (the sums start at zero)
 };
 
 struct FuseArgs {
@@ -65,13 +80,39 @@ __device__ __forceinline__ int fuse_floor(float x) { return __float_as_int(__fad
 // is the part of the pixel's ray that its row shares.  All tests fold into one
 // predicate, so a warp takes no divergent early exits; the two sums go out as one
 // 8-byte vector atomic.
+// Whether pixel depth z and its 4-neighbours pass the discontinuity test of Eq. 1's
+// input: z valid and every neighbour valid and within disc_rel * z of it.  With
+// disc_rel < 1 (NEAR) a neighbour within disc_rel * z of a valid z is itself valid
+// (>= (1 - disc_rel) z > 0, and NaN fails the comparison), so its own test is implied.
+template <bool NEAR>
+__device__ __forceinline__ bool fuse_smooth(float disc_rel, float z, float zl, float zr, float zu, float zd) {
+    const float lim = disc_rel * z;
+    bool ok = z > 0.f;
+    if (!NEAR) ok = ok && zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f;
+    return ok && fabsf(zl - z) <= lim && fabsf(zr - z) <= lim && fabsf(zu - z) <= lim && fabsf(zd - z) <= lim;
+}
+
+// w_z = cos(theta) / z^2 of a pixel with depth z, theta from the normal n = a x b of
+// the central differences
+//   a = P(u+1,v) - P(u-1,v) = dzx (xn, yn, 1) + (A, 0, 0),  A = (z_r + z_l) / fx
+//   b = P(u,v+1) - P(u,v-1) = dzy (xn, yn, 1) + (0, B, 0),  B = (z_d + z_u) / fy
+// whose cross product expands to n = (-dzx B, -dzy A, A B + dzx B xn + dzy A yn): the
+// dzx dzy xn yn terms of a_x b_y and a_y b_x cancel algebraically, not in float.
+// Returns 0 when the normal is undefined (n = 0).
+__device__ __forceinline__ float fuse_weight(const FuseCam& c, float xn, float yn, float z, float zl, float zr,
+                                             float zu, float zd) {
+    const float A = (zr + zl) * c.ifx, B = (zd + zu) * c.ify;
+    const float m1 = (zr - zl) * B, m2 = (zd - zu) * A;
+    const float nz = fmaf(m1, xn, fmaf(m2, yn, A * B));
+    const float n2 = fmaf(m1, m1, fmaf(m2, m2, nz * nz));
+    return n2 > 0.f ? __fdividef(fabsf(nz) * rsqrtf(n2), z * z) : 0.f;
+}
+
+template <bool NEAR>
 __device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c, float xn, float yn,
                                            const float rb[3], float z, float zl, float zr, float zu, float zd,
                                            float2* acc) {
-    // a valid depth whose four neighbours are valid and within disc_rel * z of it
-    const float lim = c.disc_rel * z;
-    bool ok = z > 0.f && zl > 0.f && zr > 0.f && zu > 0.f && zd > 0.f;
-    ok = ok && fabsf(zl - z) <= lim && fabsf(zr - z) <= lim && fabsf(zu - z) <= lim && fabsf(zd - z) <= lim;
+    bool ok = fuse_smooth<NEAR>(c.disc_rel, z, zl, zr, zu, zd);
     // warp into the keyframe: (fx X*, fy Y*, Z*) = z Pr (xn, yn, 1) + t, the pixel's ray
     // Pr (xn, yn, 1) formed first (one fma per row on top of the row's share)
     const float a0 = fmaf(F.Pr[0], xn, rb[0]);
@@ -85,25 +126,16 @@ __device__ __forceinline__ void fuse_pixel(const FuseFrame& F, const FuseCam& c,
     const int iu = fuse_floor(fmaf(X, rz, c.cxh));
     const int iv = fuse_floor(fmaf(Y, rz, c.cyh));
     ok = ok && Zs > 0.f && (unsigned)iu < (unsigned)c.W && (unsigned)iv < (unsigned)c.H;
-    // w_z = cos(theta) / Z^2, theta from the normal n = a x b of the central differences
-    // a = P(u+1,v) - P(u-1,v) = dzx (xn, yn, 1) + (A, 0, 0),  A = (z_r + z_l) / fx
-    // b = P(u,v+1) - P(u,v-1) = dzy (xn, yn, 1) + (0, B, 0),  B = (z_d + z_u) / fy
-    // whose cross product expands to n = (-dzx B, -dzy A, A B + dzx B xn + dzy A yn):
-    // the dzx dzy xn yn terms of a_x b_y and a_y b_x cancel algebraically, not in float
-    const float A = (zr + zl) * c.ifx, B = (zd + zu) * c.ify;
-    const float m1 = (zr - zl) * B, m2 = (zd - zu) * A;
-    const float nz = fmaf(m1, xn, fmaf(m2, yn, A * B));
-    const float n2 = fmaf(m1, m1, fmaf(m2, m2, nz * nz));
-    ok = ok && n2 > 0.f;
     if (ok) {
-        const float w = __fdividef(fabsf(nz) * rsqrtf(n2), z * z);
-        atomicAdd(acc + (iv * c.W + iu), make_float2(w * Zs, w));
+        const float w = fuse_weight(c, xn, yn, z, zl, zr, zu, zd);
+        if (w > 0.f) atomicAdd(acc + (iv * c.W + iu), make_float2(w * Zs, w));
     }
 }
 
 // One thread per 4 consecutive pixels of a row (u0 = 4 * thread): the row and its two
 // neighbour rows come in as float4 loads plus the two pixels beyond the ends.
 // Border pixels have no full neighbourhood and are skipped.  Width multiple of 4.
+template <bool NEAR>
 __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __restrict__ depths, FuseArgs a,
                                                                  FuseCam c) {
     const int W = c.W, H = c.H;
@@ -112,7 +144,7 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     if (u0 >= W || v < 1 || v >= H - 1) return;
     const FuseFrame& F = a.f[blockIdx.z];
     const size_t npx = (size_t)W * H;
-    const float* Z = depths + (size_t)blockIdx.z * npx + (size_t)v * W + u0;
+    const float* Z = depths + (size_t)F.src * npx + (size_t)v * W + u0;
     const float4 row = __ldg(reinterpret_cast<const float4*>(Z));
     const float4 up = __ldg(reinterpret_cast<const float4*>(Z - W));
     const float4 dn = __ldg(reinterpret_cast<const float4*>(Z + W));
@@ -123,13 +155,51 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel(const float* __r
     const float uf = (float)u0;
     const float yn = ((float)v - c.cy) * c.ify;
     const float rb[3] = {fmaf(F.Pr[1], yn, F.Pr[2]), fmaf(F.Pr[4], yn, F.Pr[5]), fmaf(F.Pr[7], yn, F.Pr[8])};
-    fuse_pixel(F, c, (uf - c.cx) * c.ifx, yn, rb, row.x, left, row.y, up.x, dn.x, acc);
-    fuse_pixel(F, c, ((uf + 1.f) - c.cx) * c.ifx, yn, rb, row.y, row.x, row.z, up.y, dn.y, acc);
-    fuse_pixel(F, c, ((uf + 2.f) - c.cx) * c.ifx, yn, rb, row.z, row.y, row.w, up.z, dn.z, acc);
-    fuse_pixel(F, c, ((uf + 3.f) - c.cx) * c.ifx, yn, rb, row.w, row.z, right, up.w, dn.w, acc);
+    fuse_pixel<NEAR>(F, c, (uf - c.cx) * c.ifx, yn, rb, row.x, left, row.y, up.x, dn.x, acc);
+    fuse_pixel<NEAR>(F, c, ((uf + 1.f) - c.cx) * c.ifx, yn, rb, row.y, row.x, row.z, up.y, dn.y, acc);
+    fuse_pixel<NEAR>(F, c, ((uf + 2.f) - c.cx) * c.ifx, yn, rb, row.z, row.y, row.w, up.z, dn.z, acc);
+    fuse_pixel<NEAR>(F, c, ((uf + 3.f) - c.cx) * c.ifx, yn, rb, row.w, row.z, right, up.w, dn.w, acc);
+}
+
+// The sums of keyframe images [k0, k0 + gridDim.z) initialised from each image's
+// identity frame (or zero): every pixel is written, border pixels with zero.  One
+// thread per 4 pixels of a row, two 16-byte stores.  Width multiple of 4.
+template <bool NEAR>
+__global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_init_kernel(const float* __restrict__ depths, FuseInit a,
+                                                                      int k0, FuseCam c) {
+    const int W = c.W, H = c.H;
+    const int u0 = 4 * (blockIdx.x * FUSE_TX + threadIdx.x);
+    const int v = blockIdx.y * FUSE_TY + threadIdx.y;
+    if (u0 >= W || v >= H) return;
+    const size_t npx = (size_t)W * H;
+    const int src = a.src[blockIdx.z];
+    float4* out = reinterpret_cast<float4*>(c.acc + (size_t)(k0 + blockIdx.z) * npx + (size_t)v * W + u0);
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (src >= 0 && v >= 1 && v < H - 1) {
+        const float* Z = depths + (size_t)src * npx + (size_t)v * W + u0;
+        const float4 row = __ldg(reinterpret_cast<const float4*>(Z));
+        const float4 up = __ldg(reinterpret_cast<const float4*>(Z - W));
+        const float4 dn = __ldg(reinterpret_cast<const float4*>(Z + W));
+        const float left = u0 > 0 ? __ldg(Z - 1) : 0.f;
+        const float right = u0 + 4 < W ? __ldg(Z + 4) : 0.f;
+        const float z[6] = {left, row.x, row.y, row.z, row.w, right};
+        const float zu[4] = {up.x, up.y, up.z, up.w}, zd[4] = {dn.x, dn.y, dn.z, dn.w};
+        const float yn = ((float)v - c.cy) * c.ify;
+        const float uf = (float)u0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!fuse_smooth<NEAR>(c.disc_rel, z[j + 1], z[j], z[j + 2], zu[j], zd[j])) continue;
+            const float w = fuse_weight(c, ((uf + (float)j) - c.cx) * c.ifx, yn, z[j + 1], z[j], z[j + 2], zu[j], zd[j]);
+            s[2 * j] = w * z[j + 1];
+            s[2 * j + 1] = w;
+        }
+    }
+    out[0] = make_float4(s[0], s[1], s[2], s[3]);
+    out[1] = make_float4(s[4], s[5], s[6], s[7]);
 }
 
 // Any width: one thread per pixel.
+template <bool NEAR>
 __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel_any(const float* __restrict__ depths, FuseArgs a,
                                                                      FuseCam c) {
     const int u = blockIdx.x * FUSE_TX + threadIdx.x;
@@ -138,12 +208,12 @@ __global__ void __launch_bounds__(FUSE_TX* FUSE_TY) fuse_kernel_any(const float*
     if (u < 1 || v < 1 || u >= W - 1 || v >= H - 1) return;
     const FuseFrame& F = a.f[blockIdx.z];
     const size_t npx = (size_t)W * H;
-    const float* Z = depths + (size_t)blockIdx.z * npx;
+    const float* Z = depths + (size_t)F.src * npx;
     const size_t p = (size_t)v * W + u;
     const float yn = ((float)v - c.cy) * c.ify;
     const float rb[3] = {fmaf(F.Pr[1], yn, F.Pr[2]), fmaf(F.Pr[4], yn, F.Pr[5]), fmaf(F.Pr[7], yn, F.Pr[8])};
-    fuse_pixel(F, c, ((float)u - c.cx) * c.ifx, yn, rb, __ldg(Z + p), __ldg(Z + p - 1), __ldg(Z + p + 1),
-               __ldg(Z + p - W), __ldg(Z + p + W), c.acc + (size_t)F.kf * npx);
+    fuse_pixel<NEAR>(F, c, ((float)u - c.cx) * c.ifx, yn, rb, __ldg(Z + p), __ldg(Z + p - 1), __ldg(Z + p + 1),
+                     __ldg(Z + p - W), __ldg(Z + p + W), c.acc + (size_t)F.kf * npx);
 }
 
 // Z* = S / W* where W* > 0, else 0; W* out as is.  Two pixels' sums per 16-byte load.
@@ -233,15 +303,47 @@ int fuse_launch(const float* depths, const sc_pose* frame_poses, const int32_t* 
                 size_t acc_bytes, int sms, float* kf_depth, float* kf_weight, int32_t n_kf, cudaStream_t s) {
     const int W = K->width, H = K->height;
     const size_t npx = (size_t)W * H;
-    SC_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s));
     FuseCam c{K->cx, K->cy, (float)(1.0 / K->fx), (float)(1.0 / K->fy), (float)((double)K->cx + 0.5),
               (float)((double)K->cy + 0.5), W, H, fusion->disc_rel, acc};
-    for (int f0 = 0; f0 < n; f0 += FUSE_MAX_FRAMES) {
-        const int nf = (n - f0) < FUSE_MAX_FRAMES ? (n - f0) : FUSE_MAX_FRAMES;
+    const bool near = fusion->disc_rel < 1.f;
+    dim3 block(FUSE_TX, FUSE_TY);
+    // each keyframe image's first frame at the keyframe's own pose initialises its sums
+    // (widths multiple of 4); the other frames are scattered with atomics
+    std::vector<int> init_src(n_kf, -1);
+    std::vector<char> is_init(n, 0);
+    if (W % 4 == 0) {
+        for (int f = 0; f < n; ++f) {
+            const int kf = frame_kf ? frame_kf[f] : 0;
+            if (init_src[kf] < 0 && !memcmp(&frame_poses[f], &kf_poses[kf], sizeof(sc_pose))) {
+                init_src[kf] = f;
+                is_init[f] = 1;
+            }
+        }
+        for (int k0 = 0; k0 < n_kf; k0 += FUSE_MAX_INIT) {
+            const int nk = std::min(n_kf - k0, FUSE_MAX_INIT);
+            FuseInit a;
+            for (int k = 0; k < nk; ++k) a.src[k] = init_src[k0 + k];
+            dim3 grid((W / 4 + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nk);
+            if (near) fuse_init_kernel<true><<<grid, block, 0, s>>>(depths, a, k0, c);
+            else fuse_init_kernel<false><<<grid, block, 0, s>>>(depths, a, k0, c);
+            sc::count_launches(1);
+            SC_CUDA(cudaGetLastError());
+        }
+    } else {
+        SC_CUDA(cudaMemsetAsync(acc, 0, acc_bytes, s));
+    }
+    std::vector<int> rest;
+    rest.reserve(n);
+    for (int f = 0; f < n; ++f)
+        if (!is_init[f]) rest.push_back(f);
+    const int n_rest = (int)rest.size();
+    for (int f0 = 0; f0 < n_rest; f0 += FUSE_MAX_FRAMES) {
+        const int nf = (n_rest - f0) < FUSE_MAX_FRAMES ? (n_rest - f0) : FUSE_MAX_FRAMES;
         FuseArgs a;
         for (int f = 0; f < nf; ++f) {
-            const sc_pose& T = frame_poses[f0 + f];
-            const int kf = frame_kf ? frame_kf[f0 + f] : 0;
+            const int src = rest[f0 + f];
+            const sc_pose& T = frame_poses[src];
+            const int kf = frame_kf ? frame_kf[src] : 0;
             const sc_pose& Tk = kf_poses[kf];
             // keyframe_from_frame with the focal lengths folded into rows 0 and 1,
             // composed in double and rounded once
@@ -257,8 +359,8 @@ int fuse_launch(const float* depths, const sc_pose* frame_poses, const int32_t* 
                 a.f[f].t[r] = (float)(scale[r] * acc);
             }
             a.f[f].kf = kf;
+            a.f[f].src = src;
         }
-        dim3 block(FUSE_TX, FUSE_TY);
         cudaEvent_t e0 = nullptr;
         {
             std::lock_guard<std::mutex> lock(g_fprof.mu);
@@ -266,10 +368,12 @@ int fuse_launch(const float* depths, const sc_pose* frame_poses, const int32_t* 
         }
         if (W % 4 == 0) {
             dim3 grid((W / 4 + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
-            fuse_kernel<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c);
+            if (near) fuse_kernel<true><<<grid, block, 0, s>>>(depths, a, c);
+            else fuse_kernel<false><<<grid, block, 0, s>>>(depths, a, c);
         } else {
             dim3 grid((W + FUSE_TX - 1) / FUSE_TX, (H + FUSE_TY - 1) / FUSE_TY, nf);
-            fuse_kernel_any<<<grid, block, 0, s>>>(depths + (size_t)f0 * npx, a, c);
+            if (near) fuse_kernel_any<true><<<grid, block, 0, s>>>(depths, a, c);
+            else fuse_kernel_any<false><<<grid, block, 0, s>>>(depths, a, c);
         }
         if (e0) {
             std::lock_guard<std::mutex> lock(g_fprof.mu);

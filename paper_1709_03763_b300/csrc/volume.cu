@@ -62,6 +62,11 @@ KfCam make_cam(const sc_volume* V, const sc_intrinsics* K, const sc_pose* T, con
     c.cy = K->cy;
     c.cxh = (float)((double)K->cx + 0.5);
     c.cyh = (float)((double)K->cy + 0.5);
+    c.cxyh = make_float2(c.cxh, c.cyh);
+    for (int q = 0; q < 3; ++q) {
+        c.Pxy[q] = make_float2(c.Pr[q], c.Pr[3 + q]);
+        c.Pz[q] = c.Pr[6 + q];
+    }
     c.ifx = (float)(1.0 / (double)K->fx);
     c.ify = (float)(1.0 / (double)K->fy);
     c.W = K->width;
