@@ -65,8 +65,8 @@ VOXEL_BYTES_RW = 24             # D, W, RGBA8: 12 B read + 12 B written per voxe
 # of the 12-keyframe case (profiles/instructions_kinect_small.md); units are frames
 # (fusion) and keyframe images (batched allocation).
 SMS, SCHEDULERS, LANES = 148, 4, 32
-WINST_PER_UNIT = {"fuse_kernel": 1051372.0, "batch_alloc_kernel": 4839404.0}
-DRAM_PER_UNIT = {"fuse_kernel": 1.497e6, "batch_alloc_kernel": 1.285e6}
+WINST_PER_UNIT = {"fuse_kernel": 877689.8, "batch_alloc_kernel": 4644525.9}
+DRAM_PER_UNIT = {"fuse_kernel": 1.499e6, "batch_alloc_kernel": 1.284e6}
 
 
 def parse():
@@ -92,6 +92,9 @@ def parse():
                     help="batching workload cut to --keyframes keyframes: one pose update of its first update's "
                          "size (at most half the keyframes) between cudaProfilerStart/Stop (for ncu), then exit")
     ap.add_argument("--batching-reps", type=int, default=10, help="replays per pose update in the batching rows")
+    ap.add_argument("--batch-config", default=None,
+                    help="warps_per_cta,ctas_per_sm,blocks_per_grab of the net-delta launch instead of the autotuned "
+                         "one (so that an ncu capture of a small case runs the full-size launch shape)")
     return ap.parse_args()
 
 
@@ -788,6 +791,10 @@ def main():
     P.integrate()
     torch.cuda.synchronize()
     cfg, tune_ms = V.autotune_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true, P.intr)
+    if args.batch_config:
+        wpc, cps, bpg = (int(x) for x in args.batch_config.split(","))
+        V.set_batch_config(wpc, cps, bpg)
+        cfg = V.batch_config()
     P.prep_upd = V.prepare_batch(P.ids, P.kf_depth, P.kf_rgba, P.drift, P.true)
     setup_s = time.perf_counter() - t_setup
 
@@ -983,8 +990,11 @@ def main():
     n_img = P.K
     cand = {
         # per launch: (ms, launches per step, units per launch, algorithmic bytes per launch)
+        # the scatter launches take the KAPPA - 1 frames of each group that are not at the
+        # keyframe pose (the first initialises the sums): per launch, their depth read
+        # and the sums of the keyframes they feed, written once
         "fuse_kernel": (fprof["ms"] / f_launches, fprof["launches"], f_frames,
-                        f_frames * H * Wd * 4 + (f_frames / KAPPA) * IMG_BYTES),
+                        f_frames * H * Wd * 4 + (f_frames / (KAPPA - 1)) * IMG_BYTES),
         "batch_alloc_kernel": (prof_int["batch_alloc_ms"], 2, n_img,
                                n_img * H * Wd * 4 + prof_int["batch_pairs"] * 20),
         "net_delta_kernel": (prof_upd["batch_net_ms"], 1, n_img,
@@ -1028,6 +1038,11 @@ def main():
             b = u * 512 * VOXEL_BYTES_RW + P.K * IMG_BYTES + pr["batch_pairs"] * 4 / pr["batch_launches"]
             hbm[name] = {"frac": round(b / (t / 1e3) / 1e9 / hbm_peak, 4), "ms_per_launch": round(t, 5),
                          "union_blocks": u, "block_item_pairs": pr["batch_pairs"] / pr["batch_launches"]}
+    # the whole fusion stage (init, scatter and normalisation launches): its inputs (the
+    # 600 depth frames) and outputs (Z*, W* of the 60 keyframes)
+    fb = P.K * KAPPA * H * Wd * 4 + P.K * IMG_BYTES
+    hbm["fusion stage (600 frames -> 60 keyframes)"] = {"frac": round(fb / (stage["fuse"] / 1e3) / 1e9 / hbm_peak, 4),
+                                                       "ms": round(stage["fuse"], 5)}
     roofline["hbm_view"] = hbm
 
     # ---- Marching Cubes of the corrected volume (after the step's pose update), measured

@@ -38,6 +38,27 @@ def test_fusion_matches_oracle():
     assert np.quantile(np.abs(Wg - Wo)[cov] / Wo[cov], 0.999) <= 1e-5
 
 
+@pytest.mark.parametrize("disc_rel", [0.1, 1.5])
+def test_fusion_keyframe_pose_of_no_frame(disc_rel):
+    # a keyframe pose that equals no frame's pose: every frame is warped (no identity
+    # frame initialises the sums); disc_rel >= 1 also checks every neighbour's validity
+    d, poses = _frames()
+    rng = synthetic.rng(2, 77)
+    kf = synthetic.perturb_pose(poses[4], np.radians(0.3), 0.004, rng).astype(np.float32)
+    Zg, Wg = fuse_frames_into_keyframe(d.cuda(), poses, kf, synthetic.KINECT, disc_rel=disc_rel)
+    Zo, Wo, fl = oracle.fuse(d, poses, kf, synthetic.KINECT.as_tuple(), disc_rel=disc_rel)
+    Zg, Wg = Zg.cpu().numpy().astype(np.float64), Wg.cpu().numpy().astype(np.float64)
+    good = fl == 0
+    # every frame warped (10 instead of 9): 3.4 % of target pixels flagged, bounded at 1.5x
+    print(f"[fusion parity, no identity frame, disc_rel {disc_rel}] flagged {100 * (1 - good.mean()):.2f} %")
+    assert 1 - good.mean() <= 1.5 * 0.0338
+    cov = good & (Wo > 0)
+    assert cov.sum() > 0.5 * Wo.size
+    assert np.all((Wg[good] > 0) == (Wo[good] > 0))
+    assert np.abs(Zg - Zo)[cov].max() <= 1e-5
+    assert (np.abs(Wg - Wo)[cov] * Zo[cov] ** 2).max() <= 1e-5
+
+
 def test_fusion_identical_frames_and_ragged_size():
     z0 = 1.37
     H, W = 37, 53
