@@ -4,16 +4,22 @@
 // A(k, T): every 8^3 block whose closed box meets the band segment
 // {pi^-1(x, z) : z in [Z(x) - mu, Z(x) + mu]} of a valid pixel x, in world
 // coordinates.  Computed per 32x16 pixel tile by one CTA:
-//   A  enumerate each pixel's blocks (a walk across block faces) into a shared-memory
-//      set of 32-bit camera-relative keys, which removes the many duplicates
-//      neighbouring pixels produce;
-//   B  claim every unique key in the global hash table (64-bit CAS); the tile's
-//      new entries get consecutive pool slots from one atomic add;
+//   A  enumerate each pixel's blocks (a walk across block faces) into shared memory,
+//      which removes the many duplicates neighbouring pixels produce: a block inside
+//      the tile's window (16^3 blocks around the surface at a reference pixel) sets its
+//      byte of a direct-indexed byte map with a plain store; any other block goes into a
+//      set of 32-bit camera-relative keys;
+//   B  claim every unique key in the global hash table (64-bit CAS); each warp's new
+//      entries get consecutive pool slots from one atomic add and are published at once;
 //   C  read each key's slot and let the Sink decide whether this call lists it
 //      (first time for this keyframe) and, for batches, whether it joins the
-//      batch's union of touched blocks; appends go through one atomic per CTA;
-//   D  only if the shared set overflowed: the overflowing keys one at a time.
+//      batch's union of touched blocks; appends go through one atomic per warp;
+//      B and C run warp by warp, with no barrier between them;
+//   D  only if the set or the compacted key list overflowed: the blocks they miss,
+//      one at a time.
 #pragma once
+
+#include <climits>
 
 #include "common.cuh"
 
@@ -168,18 +174,34 @@ __device__ inline void publish(const DevVolume& V, int entry, unsigned long long
     atomicExch(&V.table[entry].slot, (int32_t)slot);
 }
 
+constexpr int WIN = 16;  // tile window edge in blocks (byte map of WIN^3 entries)
+
 struct AllocShared {
-    uint32_t set[SET_SIZE];  // open-addressing set of the tile's block keys (key32)
-    int uk[SET_SIZE];    // compacted: set positions of the n_keys occupied entries
-    int ent[SET_SIZE];   // per compacted key: hash entry index (-1: failed)
-    int slot[SET_SIZE];  // per compacted key: pool slot if known, else -1
-    int idx[SET_SIZE];   // new keys (phase B), then list appends (phase C)
-    int uidx[SET_SIZE];  // union appends (batches)
-    unsigned char mine[SET_SIZE];  // key created by this CTA
-    int n_keys, n_new, n_app, n_uapp, overflow;
-    uint32_t pool_base;
-    int app_base, uapp_base;
+    uint4 bmap[WIN * WIN * WIN / 16];  // byte per window block (x + WIN y + WIN^2 z): 1 = met
+    uint32_t set[SET_SIZE];  // open-addressing set of the tile's other block keys (key32)
+    uint32_t uk[SET_SIZE];   // compacted: the n_keys unique keys (key32) of the tile
+    int n_keys;
+    int overflow;  // 1: a key did not fit the set (its threads run phase D); 2: more unique keys
+                   // than uk holds (every thread runs phase D over all its blocks)
+    int3 wo;       // window origin (block coordinates); window off when wo.x == INT_MIN
 };
+
+// Append the slots of the lanes with `pred` through a global counter: one atomic add
+// per warp.  Called by all 32 lanes.
+__device__ __forceinline__ void warp_append(const DevVolume& V, int32_t* list, int32_t* count, uint32_t cap, bool pred,
+                                            int32_t slot, int32_t full_code) {
+    const unsigned m = __ballot_sync(0xffffffffu, pred);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    int b = 0;
+    if (lane == 0) b = atomicAdd(count, __popc(m));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (pred) {
+        const uint32_t p = (uint32_t)b + (uint32_t)__popc(m & ((1u << lane) - 1u));
+        if (p < cap) list[p] = slot;
+        else set_status(V.status, full_code);
+    }
+}
 
 // Append one slot through a global counter (used by phase D).
 __device__ inline void append_one(const DevVolume& V, int32_t* list, int32_t* count, uint32_t cap, int32_t slot) {
@@ -199,35 +221,86 @@ __device__ __forceinline__ int3 cam_block(const KfCam& k) {
     return make_int3(k.ti[0] >> 3, k.ti[1] >> 3, k.ti[2] >> 3);
 }
 
-// Phase A of a tile, shared by the allocation and the stream-in probe: clear the set,
-// insert every pixel's band-segment blocks, compact the occupied entries into uk
-// (n_keys of them).  Returns this thread's overflow flag (a key that did not fit, or a
-// camera so far out that its 32-bit keys could decode to invalid coordinates); the
-// CTA-wide flag is sh.overflow.  Must be called by all ALLOC_THREADS threads.
+// Window of a tile: 16^3 blocks centred on the block of the surface point (depth Z, no
+// band) of a reference pixel -- the first valid one of the tile centre and eight points
+// around it -- so that a smooth surface's blocks fall inside.  Off (wo.x = INT_MIN) when
+// no reference pixel is valid or a window block would lie outside the 32-bit key range.
+__device__ inline int3 tile_window(const KfCam& k, int tx, int ty, const int3& ref, bool ref_ok) {
+    const int3 off = make_int3(INT_MIN, 0, 0);
+    if (!ref_ok) return off;
+    // the tile centre first, then the eight points halfway to its edges and corners:
+    // all nine depths requested together, the first valid one kept
+    constexpr int qx[9] = {2, 1, 3, 1, 3, 2, 2, 1, 3}, qy[9] = {2, 1, 1, 3, 3, 1, 3, 2, 2};
+    float Z = 0.f;
+    int uz = 0, vz = 0;
+#pragma unroll
+    for (int c = 8; c >= 0; --c) {
+        const int u = min(tx * ALLOC_TX + ALLOC_TX / 4 * qx[c], k.W - 1);
+        const int v = min(ty * ALLOC_TY + ALLOC_TY / 4 * qy[c], k.H - 1);
+        const float z = __ldg(k.depth + (size_t)v * k.W + u);
+        const bool ok = z > 0.f && z < MAX_DEPTH;
+        Z = ok ? z : Z;
+        uz = ok ? u : uz;
+        vz = ok ? v : vz;
+    }
+    if (!(Z > 0.f)) return off;
+    const float xn = __fmul_rn(__fsub_rn((float)uz, k.cx), k.ifx);
+    const float yn = __fmul_rn(__fsub_rn((float)vz, k.cy), k.ify);
+    int b[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float ray = __fmaf_rn(k.Ms[3 * r], xn, __fmaf_rn(k.Ms[3 * r + 1], yn, k.Ms[3 * r + 2]));
+        b[r] = ((__float2int_rd(__fmaf_rn(Z, ray, k.tf[r])) + k.ti[r]) >> 3) - WIN / 2;
+    }
+    // every window block must have a 32-bit key (|b - ref| <= 511 per axis)
+    if (b[0] - ref.x < -512 || b[0] + WIN - 1 - ref.x > 511 || b[1] - ref.y < -512 || b[1] + WIN - 1 - ref.y > 511 ||
+        b[2] - ref.z < -512 || b[2] + WIN - 1 - ref.z > 511)
+        return off;
+    return make_int3(b[0], b[1], b[2]);
+}
+
+// Phase A of a tile, shared by the allocation and the stream-in probe: clear the byte
+// map and the set, insert every pixel's band-segment blocks, compact the unique keys
+// into uk (n_keys of them).  Returns this thread's overflow flag (a key that did not
+// fit, or a camera so far out that its 32-bit keys could decode to invalid
+// coordinates); the CTA-wide flag is sh.overflow.  Must be called by all ALLOC_THREADS
+// threads.
 __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared& sh) {
     const int tid = threadIdx.x;
+    for (int i = tid; i < WIN * WIN * WIN / 16; i += ALLOC_THREADS) sh.bmap[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY32_EMPTY;
-    if (tid == 0) {
-        sh.n_keys = 0;
-        sh.n_new = 0;
-        sh.n_app = 0;
-        sh.n_uapp = 0;
-        sh.overflow = 0;
-    }
-    __syncthreads();
     const int3 ref = cam_block(k);
     // every 32-bit key of this camera decodes to a valid block coordinate (else all its
     // blocks take the overflow path, which checks each one)
     const bool ref_ok = coord_ok(ref.x - 512, ref.y - 512, ref.z - 512) && coord_ok(ref.x + 511, ref.y + 511, ref.z + 511);
+    if (tid == 0) {
+        sh.n_keys = 0;
+        sh.overflow = 0;
+        sh.wo = tile_window(k, tx, ty, ref, ref_ok);
+    }
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
     const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
+    float Zp[ALLOC_PPT];
+#pragma unroll
+    for (int r = 0; r < ALLOC_PPT; ++r) {
+        const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
+        Zp[r] = (u < k.W && v < k.H) ? __ldg(k.depth + (size_t)v * k.W + u) : 0.f;
+    }
+    __syncthreads();
+    const int3 wo = sh.wo;
+    unsigned char* bmap = reinterpret_cast<unsigned char*>(sh.bmap);
     bool my_ovf = false;
 #pragma unroll 1
     for (int r = 0; r < ALLOC_PPT; ++r) {
         const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
-        float Z = 0.f;
-        if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
+        const float Z = Zp[r];
         auto ins = [&](int bx, int by, int bz) {
+            const uint32_t dx = (uint32_t)bx - (uint32_t)wo.x, dy = (uint32_t)by - (uint32_t)wo.y,
+                           dz = (uint32_t)bz - (uint32_t)wo.z;
+            if ((dx | dy | dz) < (uint32_t)WIN) {  // inside the window (never when it is off)
+                bmap[dx + WIN * dy + WIN * WIN * dz] = 1;
+                return;
+            }
             uint32_t kk;
             if (!ref_ok || !key32(bx, by, bz, ref, &kk) || !set_insert(sh.set, kk)) my_ovf = true;
         };
@@ -235,14 +308,52 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
     }
     if (my_ovf) sh.overflow = 1;
     __syncthreads();
-    // compact the occupied entries so that the global phases run in one round
+    // compact the window's met blocks and the set's keys so that the global phases run
+    // in one round; more unique keys than uk holds send the whole tile to phase D
+    auto push = [&](uint32_t key) {
+        const int p = atomicAdd(&sh.n_keys, 1);
+        if (p < SET_SIZE) sh.uk[p] = key;
+        else sh.overflow = 2;
+    };
+    if (wo.x != INT_MIN) {
+        for (int i = tid; i < WIN * WIN * WIN / 16; i += ALLOC_THREADS) {
+            const uint4 q = sh.bmap[i];
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t m = w4[j];
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= ~(0xffu << (bit & ~7));
+                    const int e = 16 * i + 4 * j + (bit >> 3);
+                    uint32_t kk;
+                    key32(wo.x + (e % WIN), wo.y + (e / WIN) % WIN, wo.z + e / (WIN * WIN), ref, &kk);
+                    push(kk);
+                }
+            }
+        }
+    }
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS)
-        if (sh.set[i] != KEY32_EMPTY) sh.uk[atomicAdd(&sh.n_keys, 1)] = i;
+        if (sh.set[i] != KEY32_EMPTY) push(sh.set[i]);
+    __syncthreads();
+    if (tid == 0 && sh.n_keys > SET_SIZE) sh.n_keys = SET_SIZE;
     __syncthreads();
     return my_ovf;
 }
 
-// Every block of this thread's pixels that the shared set does not hold (the overflow
+// Whether block (bx, by, bz) of this tile was compacted into uk (in the window, or in
+// the set); false for every block once the tile has more unique keys than uk holds.
+__device__ __forceinline__ bool tile_holds(const AllocShared& sh, int bx, int by, int bz, const int3& ref,
+                                           bool ref_ok) {
+    if (sh.overflow == 2) return false;
+    const uint32_t dx = (uint32_t)bx - (uint32_t)sh.wo.x, dy = (uint32_t)by - (uint32_t)sh.wo.y,
+                   dz = (uint32_t)bz - (uint32_t)sh.wo.z;
+    if ((dx | dy | dz) < (uint32_t)WIN) return true;
+    uint32_t kk;
+    return ref_ok && key32(bx, by, bz, ref, &kk) && set_contains(sh.set, kk);
+}
+
+// Every block of this thread's pixels that the tile did not compact (the overflow
 // path): f(bx, by, bz) for each, coordinates checked.
 template <typename F>
 __device__ inline void tile_overflow_blocks(const DevVolume& V, const KfCam& k, int tx, int ty, const AllocShared& sh,
@@ -262,8 +373,7 @@ __device__ inline void tile_overflow_blocks(const DevVolume& V, const KfCam& k, 
                 set_status(V.status, SC_ERR_INVALID_ARG);
                 return;
             }
-            uint32_t kk;
-            if (ref_ok && key32(bx, by, bz, ref, &kk) && set_contains(sh.set, kk)) return;
+            if (tile_holds(sh, bx, by, bz, ref, ref_ok)) return;
             f(bx, by, bz);
         });
     }
@@ -277,65 +387,51 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     const int3 ref = cam_block(k);
     const int nk = sh.n_keys;
 
-    // B: claim each unique key; the tile's new entries get consecutive slots
-    for (int i = tid; i < nk; i += ALLOC_THREADS) {
-        bool won;
-        int32_t seen;
-        const int e = hash_claim(V, key64_of(sh.set[sh.uk[i]], ref), &won, &seen);
-        sh.ent[i] = e;
-        sh.slot[i] = seen;
-        sh.mine[i] = 0;
-        if (e >= 0 && won) sh.idx[atomicAdd(&sh.n_new, 1)] = i;
-    }
-    __syncthreads();
-    if (tid == 0 && sh.n_new > 0) sh.pool_base = atomicAdd(V.pool_count, (uint32_t)sh.n_new);
-    __syncthreads();
-    for (int i = tid; i < sh.n_new; i += ALLOC_THREADS) {
-        const int j = sh.idx[i];
-        const uint32_t slot = sh.pool_base + (uint32_t)i;
-        // nobody else can list a slot before it is published: mark it for this
-        // keyframe with a plain store, then publish
-        if (slot < V.max_blocks) {
-            sk.mark_new(slot);
-            sh.slot[j] = (int)slot;
-            sh.mine[j] = 1;
+    // B + C, warp by warp without CTA barriers: each warp claims its keys, takes pool
+    // slots for the entries it created with one atomic add, publishes them, then
+    // dedupes its keys' slots and appends them with one atomic add per list.  A warp
+    // publishes its own entries before it waits for anyone else's, so no wait is circular.
+    const int lane = tid & 31;
+    const int nk_w = (nk + 31) & ~31;  // warp-uniform trip count: the ballots see whole warps
+    for (int i = tid; i < nk_w; i += ALLOC_THREADS) {
+        const bool act = i < nk;
+        bool won = false;
+        int32_t seen = -1;
+        int e = -1;
+        unsigned long long key = 0;
+        if (act) {
+            key = key64_of(sh.uk[i], ref);
+            e = hash_claim(V, key, &won, &seen);
+            won = won && e >= 0;
         }
-        publish(V, sh.ent[j], key64_of(sh.set[sh.uk[j]], ref), slot);
-    }
-    __syncthreads();
-
-    // C: dedupe and append (the two membership atomics are independent)
-    for (int i = tid; i < nk; i += ALLOC_THREADS) {
-        if (sh.ent[i] < 0) continue;
-        int32_t slot = sh.slot[i];
-        if (slot < 0) slot = entry_slot(V, sh.ent[i]);
-        if (slot < 0) continue;
-        const bool first = sh.mine[i] ? true : sk.list_first(slot);
-        const bool ufirst = Sink::kUnion ? sk.union_first(slot) : false;
-        if (first) sh.idx[atomicAdd(&sh.n_app, 1)] = slot;
-        if (ufirst) sh.uidx[atomicAdd(&sh.n_uapp, 1)] = slot;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        if (sh.n_app > 0) sh.app_base = atomicAdd(sk.count, sh.n_app);
-        if (Sink::kUnion && sh.n_uapp > 0) sh.uapp_base = atomicAdd(sk.ucount, sh.n_uapp);
-    }
-    __syncthreads();
-    for (int i = tid; i < sh.n_app; i += ALLOC_THREADS) {
-        const uint32_t p = (uint32_t)sh.app_base + (uint32_t)i;
-        if (p < sk.cap) sk.list[p] = sh.idx[i];
-        else set_status(V.status, SC_ERR_LIST_FULL);
-    }
-    if (Sink::kUnion) {
-        for (int i = tid; i < sh.n_uapp; i += ALLOC_THREADS) {
-            const uint32_t p = (uint32_t)sh.uapp_base + (uint32_t)i;
-            if (p < sk.ucap) sk.ulist[p] = sh.uidx[i];
-            else set_status(V.status, SC_ERR_POOL_FULL);
+        const unsigned wm = __ballot_sync(0xffffffffu, won);
+        uint32_t base = 0;
+        if (wm) {
+            if (lane == 0) base = atomicAdd(V.pool_count, (uint32_t)__popc(wm));
+            base = __shfl_sync(0xffffffffu, base, 0);
         }
+        int32_t slot = seen;
+        if (won) {
+            const uint32_t ns = base + (uint32_t)__popc(wm & ((1u << lane) - 1u));
+            // nobody else can list a slot before it is published: mark it for this
+            // keyframe, then publish (a full pool publishes a failed entry instead)
+            if (ns < V.max_blocks) {
+                sk.mark_new((int32_t)ns);
+                slot = (int32_t)ns;
+            }
+            publish(V, e, key, ns);
+        } else if (act && e >= 0 && slot < 0) {
+            slot = entry_slot(V, e);
+        }
+        const bool ok = act && e >= 0 && slot >= 0;
+        const bool first = ok && (won || sk.list_first(slot));
+        const bool ufirst = Sink::kUnion && ok && sk.union_first(slot);
+        warp_append(V, sk.list, sk.count, sk.cap, first, slot, SC_ERR_LIST_FULL);
+        if (Sink::kUnion) warp_append(V, sk.ulist, sk.ucount, sk.ucap, ufirst, slot, SC_ERR_POOL_FULL);
     }
 
     // D: keys that did not fit in the shared set
-    if (sh.overflow != 0 && my_ovf) {
+    if (sh.overflow == 2 || (sh.overflow != 0 && my_ovf)) {
         tile_overflow_blocks(V, k, tx, ty, sh, [&](int bx, int by, int bz) {
             const unsigned long long key = pack_key(bx, by, bz);
             bool won;
