@@ -138,8 +138,10 @@ typedef struct {
  *   - sc_fuse_frames_into_keyframe / sc_fuse_keyframes: 8 bytes per keyframe
  *     pixel of stream-ordered scratch per call, from a memory pool per device that
  *     keeps its memory (so only the first call, or a larger one, reaches the driver);
- *   - sc_overlap_counts / sc_segment_keyframes (a stream-ordered count buffer
- *     per call), sc_stream_in_keyframes (a stream-ordered flag array per call),
+ *   - sc_overlap_counts (a stream-ordered count buffer per call),
+ *     sc_segment_keyframes with KF_OVRLP (stream-ordered pose and group buffers per
+ *     call; the first call on a device its grouping graph and state),
+ *     sc_stream_in_keyframes (a stream-ordered flag array per call),
  *     sc_create_block_store, and the first sc_marching_cubes on a device (its
  *     case table).
  * sc_sdf_adjoint_noalloc allocates nothing.  Colour fusion uses a caller-owned
@@ -275,9 +277,12 @@ int sc_overlap_counts(const float* depths, const sc_pose* frame_poses, int32_t n
  * [n]) receives each frame's group, *n_keyframes their number.  depths (device
  * [n][H][W]) and intr are needed for SC_KF_OVRLP only (otherwise may be NULL).  KF_DIST
  * distances are computed in double from the float poses; KF_OVRLP ratios from integer
- * counts.  Synchronises the stream (KF_OVRLP: once per group of 8 to 32 frames
- * evaluated against the current keyframe).  Concurrent KF_OVRLP calls on one device
- * share a pinned read-back buffer and take turns. */
+ * counts.  KF_OVRLP runs its grouping loop on the device (a CUDA graph with a while
+ * node: per step, the overlap counts of the next 8 to 32 frames and one decision
+ * kernel), then reads the groups back and synchronises the stream once.  The first
+ * KF_OVRLP call on a device, and the first with a new image size, builds that graph
+ * (it and its state stay allocated until exit); concurrent KF_OVRLP calls on one
+ * device take turns. */
 int sc_segment_keyframes(int32_t strategy, const double* params, const float* depths, const sc_pose* poses,
                          int32_t n, const sc_intrinsics* intr, int32_t* frame_kf, int32_t* n_keyframes,
                          sc_stream stream);

@@ -44,6 +44,19 @@ def make_pose(T) -> Pose:
     return p
 
 
+def pose_array(poses):
+    """Poses [n,3,4] (numpy / torch / sequence of [3,4] or Pose) as one contiguous buffer laid
+    out as sc_pose[n]; returns (buffer, pointer).  Keep the buffer alive during the call."""
+    n = len(poses)
+    if n and isinstance(poses[0], Pose):
+        buf = (Pose * n)(*poses)
+        return buf, ctypes.cast(buf, ctypes.POINTER(Pose))
+    if hasattr(poses, "detach"):
+        poses = poses.detach().cpu().numpy()
+    a = np.ascontiguousarray(np.asarray(poses, dtype=np.float32).reshape(n, 12)) if n else np.zeros((1, 12), np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(Pose))
+
+
 def _stream(stream) -> int:
     if stream is None:
         return torch.cuda.current_stream().cuda_stream
@@ -577,7 +590,7 @@ def segment_keyframes(strategy: int, params, poses, intr=None, depths: torch.Ten
     """Keyframe groups of frames in order (KF_CONST: params=(kappa,), KF_DIST: (thr_t, thr_r),
     KF_OVRLP: (thr,) with depths [n,H,W] on the device).  Returns (frame_kf [n] int32, keyframes)."""
     n = len(poses)
-    pz = (Pose * max(n, 1))(*[make_pose(p) for p in poses])
+    pbuf, pz = pose_array(poses)
     pr = (ctypes.c_double * 2)(*[float(x) for x in (list(params) + [0.0, 0.0])[:2]])
     fk = np.zeros(max(n, 1), np.int32)
     g = ctypes.c_int32(0)

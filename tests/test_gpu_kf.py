@@ -97,3 +97,29 @@ def test_overlap_counts_ragged_width_matches_oracle():
         assert c[f, 0] == valid
         assert abs(int(c[f, 1]) - inside) <= marg
     assert c[1, 1] == c[1, 0]
+
+
+def test_kf_ovrlp_grouping_ragged_width_matches_oracle():
+    # width 53: the grouping graph's one-pixel-per-thread overlap step; frames sliding
+    # sideways so that the overlap falls below the threshold every few frames, after
+    # a grouping of another image size (the per-device graph is rebuilt)
+    intr = (45.0, 45.0, 26.3, 18.1, 53, 37)
+    W, H = 53, 37
+    g = np.random.default_rng(12)
+    n = 40
+    d = np.full((n, H, W), 1.6, np.float32) + np.linspace(0.0, 0.4, W, dtype=np.float32)[None, None, :]
+    d[g.random(d.shape) < 0.1] = 0.0
+    poses = []
+    for i in range(n):
+        T = np.hstack([np.eye(3), np.zeros((3, 1))]).astype(np.float32)
+        T[0, 3] = np.float32(0.05 * i)
+        poses.append(T)
+    dt = torch.from_numpy(d).cuda()
+    for thr in (0.9, 0.7):
+        fk, gk = segment_keyframes(KF_OVRLP, (thr,), poses, intr, dt)
+        fo, flag, go = oracle.segment(oracle.KF_OVRLP, (thr,), poses, intr, torch.from_numpy(d))
+        stop = int(np.argmax(flag)) if flag.any() else n
+        assert np.array_equal(fk[:stop], fo[:stop])
+        if not flag.any():
+            assert gk == go
+        assert gk >= 3
