@@ -563,6 +563,8 @@ typedef struct {
     int64_t batch_launches;
     int64_t batch_union_blocks; /* sum over batches of the union of touched blocks */
     int64_t batch_pairs;        /* sum over batches of old + new block-list lengths */
+    double mc_ms;               /* Marching Cubes kernel (sc_marching_cubes) */
+    int64_t mc_launches;
 } sc_profile;
 
 /* Process-wide timing of the fusion launches: enable 1 / 0 resets the counters and

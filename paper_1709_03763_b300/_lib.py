@@ -77,7 +77,8 @@ class Profile(ctypes.Structure):
     _fields_ = [("enabled", c_i32), ("pad", c_i32), ("alloc_ms", c_d), ("alloc_launches", c_i64),
                 ("update_ms", c_d), ("update_launches", c_i64), ("update_blocks", c_i64),
                 ("batch_alloc_ms", c_d), ("batch_mark_ms", c_d), ("batch_net_ms", c_d),
-                ("batch_launches", c_i64), ("batch_union_blocks", c_i64), ("batch_pairs", c_i64)]
+                ("batch_launches", c_i64), ("batch_union_blocks", c_i64), ("batch_pairs", c_i64),
+                ("mc_ms", c_d), ("mc_launches", c_i64)]
 
 
 P = ctypes.POINTER

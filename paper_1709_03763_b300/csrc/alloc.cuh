@@ -3,7 +3,7 @@
 //
 // A(k, T): every 8^3 block whose closed box meets the band segment
 // {pi^-1(x, z) : z in [Z(x) - mu, Z(x) + mu]} of a valid pixel x, in world
-// coordinates.  Computed per 32x16 pixel tile by one CTA:
+// coordinates.  Computed per 32x32 pixel tile by one CTA:
 //   A  enumerate each pixel's blocks (a walk across block faces) into shared memory,
 //      which removes the many duplicates neighbouring pixels produce: a block inside
 //      the tile's window (16^3 blocks around the surface at a reference pixel) sets its
@@ -25,20 +25,20 @@
 
 namespace sc {
 
-#ifndef SC_ALLOC_TY
-#define SC_ALLOC_TY 16
-#endif
-#ifndef SC_ALLOC_WARP_DEDUPE
-#define SC_ALLOC_WARP_DEDUPE 0
-#endif
 #ifndef SC_ALLOC_CTAS_PER_SM
 #define SC_ALLOC_CTAS_PER_SM 8  // resident allocation CTAs per SM (caps registers at 32)
 #endif
-constexpr int ALLOC_TX = 32;           // pixel tile 32 x SC_ALLOC_TY, one CTA of 256 threads,
-constexpr int ALLOC_TY = SC_ALLOC_TY;  // SC_ALLOC_TY / 8 pixels (rows r, r+8, ...) per thread
+// Pixel tiles of 32 x TY pixels, one CTA of 256 threads, TY / 8 pixels per thread (one
+// column, rows r, r + 8, ...).  Batches and stream-in probes take 32 x 32 tiles (fewer
+// tiles, so less per-tile work: 13 % faster than 32 x 16 over 60 images); the plain path
+// allocates one keyframe per launch and takes 32 x 16, which doubles its CTAs.
+constexpr int ALLOC_TX = 32;
+constexpr int ALLOC_TY = 32;        // batched allocation, stream-in probe
+constexpr int ALLOC_TY_PLAIN = 16;  // one keyframe per launch
 constexpr int ALLOC_THREADS = 256;
-constexpr int ALLOC_PPT = ALLOC_TX * ALLOC_TY / ALLOC_THREADS;
-constexpr int SET_BITS = ALLOC_TY >= 32 ? 10 : 9;
+template <int TY>
+__host__ __device__ constexpr int alloc_ppt() { return ALLOC_TX * TY / ALLOC_THREADS; }
+constexpr int SET_BITS = 10;
 constexpr int SET_SIZE = 1 << SET_BITS;  // unique blocks of a tile before overflow handling
 constexpr int MAX_BLOCK_WALK = 48;   // block-face crossings of one band segment
 constexpr float MAX_DEPTH = 1.0e4f;  // metres; larger depth values are treated as invalid
@@ -225,6 +225,7 @@ __device__ __forceinline__ int3 cam_block(const KfCam& k) {
 // band) of a reference pixel -- the first valid one of the tile centre and eight points
 // around it -- so that a smooth surface's blocks fall inside.  Off (wo.x = INT_MIN) when
 // no reference pixel is valid or a window block would lie outside the 32-bit key range.
+template <int TY>
 __device__ inline int3 tile_window(const KfCam& k, int tx, int ty, const int3& ref, bool ref_ok) {
     const int3 off = make_int3(INT_MIN, 0, 0);
     if (!ref_ok) return off;
@@ -236,7 +237,7 @@ __device__ inline int3 tile_window(const KfCam& k, int tx, int ty, const int3& r
 #pragma unroll
     for (int c = 8; c >= 0; --c) {
         const int u = min(tx * ALLOC_TX + ALLOC_TX / 4 * qx[c], k.W - 1);
-        const int v = min(ty * ALLOC_TY + ALLOC_TY / 4 * qy[c], k.H - 1);
+        const int v = min(ty * TY + TY / 4 * qy[c], k.H - 1);
         const float z = __ldg(k.depth + (size_t)v * k.W + u);
         const bool ok = z > 0.f && z < MAX_DEPTH;
         Z = ok ? z : Z;
@@ -265,7 +266,9 @@ __device__ inline int3 tile_window(const KfCam& k, int tx, int ty, const int3& r
 // fit, or a camera so far out that its 32-bit keys could decode to invalid
 // coordinates); the CTA-wide flag is sh.overflow.  Must be called by all ALLOC_THREADS
 // threads.
+template <int TY>
 __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared& sh) {
+    constexpr int PPT = alloc_ppt<TY>();
     const int tid = threadIdx.x;
     for (int i = tid; i < WIN * WIN * WIN / 16; i += ALLOC_THREADS) sh.bmap[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY32_EMPTY;
@@ -276,13 +279,13 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
     if (tid == 0) {
         sh.n_keys = 0;
         sh.overflow = 0;
-        sh.wo = tile_window(k, tx, ty, ref, ref_ok);
+        sh.wo = tile_window<TY>(k, tx, ty, ref, ref_ok);
     }
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
-    const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
-    float Zp[ALLOC_PPT];
+    const int v0 = ty * TY + (tid / ALLOC_TX);
+    float Zp[PPT];
 #pragma unroll
-    for (int r = 0; r < ALLOC_PPT; ++r) {
+    for (int r = 0; r < PPT; ++r) {
         const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
         Zp[r] = (u < k.W && v < k.H) ? __ldg(k.depth + (size_t)v * k.W + u) : 0.f;
     }
@@ -291,7 +294,7 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
     unsigned char* bmap = reinterpret_cast<unsigned char*>(sh.bmap);
     bool my_ovf = false;
 #pragma unroll 1
-    for (int r = 0; r < ALLOC_PPT; ++r) {
+    for (int r = 0; r < PPT; ++r) {
         const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
         const float Z = Zp[r];
         auto ins = [&](int bx, int by, int bz) {
@@ -355,15 +358,15 @@ __device__ __forceinline__ bool tile_holds(const AllocShared& sh, int bx, int by
 
 // Every block of this thread's pixels that the tile did not compact (the overflow
 // path): f(bx, by, bz) for each, coordinates checked.
-template <typename F>
+template <int TY, typename F>
 __device__ inline void tile_overflow_blocks(const DevVolume& V, const KfCam& k, int tx, int ty, const AllocShared& sh,
                                             F&& f) {
     const int tid = threadIdx.x;
     const int3 ref = cam_block(k);
     const bool ref_ok = coord_ok(ref.x - 512, ref.y - 512, ref.z - 512) && coord_ok(ref.x + 511, ref.y + 511, ref.z + 511);
     const int u = tx * ALLOC_TX + (tid % ALLOC_TX);
-    const int v0 = ty * ALLOC_TY + (tid / ALLOC_TX);
-    for (int r = 0; r < ALLOC_PPT; ++r) {
+    const int v0 = ty * TY + (tid / ALLOC_TX);
+    for (int r = 0; r < alloc_ppt<TY>(); ++r) {
         const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
         float Z = 0.f;
         if (u < k.W && v < k.H) Z = __ldg(k.depth + (size_t)v * k.W + u);
@@ -379,11 +382,11 @@ __device__ inline void tile_overflow_blocks(const DevVolume& V, const KfCam& k, 
     }
 }
 
-template <typename Sink>
+template <int TY, typename Sink>
 __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, int ty, Sink& sk, AllocShared& sh) {
     const int tid = threadIdx.x;
     // A: every pixel's band-segment blocks into the shared set
-    const bool my_ovf = tile_collect(k, tx, ty, sh);
+    const bool my_ovf = tile_collect<TY>(k, tx, ty, sh);
     const int3 ref = cam_block(k);
     const int nk = sh.n_keys;
 
@@ -432,7 +435,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
 
     // D: keys that did not fit in the shared set
     if (sh.overflow == 2 || (sh.overflow != 0 && my_ovf)) {
-        tile_overflow_blocks(V, k, tx, ty, sh, [&](int bx, int by, int bz) {
+        tile_overflow_blocks<TY>(V, k, tx, ty, sh, [&](int bx, int by, int bz) {
             const unsigned long long key = pack_key(bx, by, bz);
             bool won;
             int32_t seen;

@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) batch_all
         const BatchItem& it = items[i];
         BatchSink sk{masks + half + (i >> 5), mw, 1u << (i & 31), V.stamp, call_id, it.new_list, it.new_count,
                      list_cap, ulist, counters, V.max_blocks};
-        alloc_tile(V, it.newc, t % tiles_x, t / tiles_x, sk, sh);
+        alloc_tile<ALLOC_TY>(V, it.newc, t % tiles_x, t / tiles_x, sk, sh);
     }
 }
 

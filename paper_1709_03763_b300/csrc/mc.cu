@@ -391,7 +391,9 @@ extern "C" int sc_marching_cubes(sc_volume* V, float* triangles, int32_t* cubes,
     SC_CUDA(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), s));
     if (n_slots > 0) {
         McOut o{triangles, cubes, dcount, (unsigned long long)capacity, V->p.voxel_size};
+        cudaEvent_t e0 = prof_mark(V, s);
         mc_kernel<<<n_slots, MC_THREADS, 0, s>>>(V->dv, T, o, n_slots);
+        prof_pair(V, e0, prof_mark(V, s), 5);
         count_launches(1);
         SC_CUDA(cudaGetLastError());
     }

@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) si_probe_
         const int i = w / tiles, t = w - i * tiles;
         const KfCam& k = cams[i];
         const int tx = t % tiles_x, ty = t / tiles_x;
-        const bool my_ovf = tile_collect(k, tx, ty, sh);
+        const bool my_ovf = tile_collect<ALLOC_TY>(k, tx, ty, sh);
         const int3 ref = cam_block(k);
         auto hit = [&](unsigned long long key) {
             const int32_t e = index_find(I, key);
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) si_probe_
         };
         for (int j = threadIdx.x; j < sh.n_keys; j += ALLOC_THREADS) hit(key64_of(sh.uk[j], ref));
         if (sh.overflow == 2 || (sh.overflow != 0 && my_ovf))
-            tile_overflow_blocks(V, k, tx, ty, sh, [&](int bx, int by, int bz) { hit(pack_key(bx, by, bz)); });
+            tile_overflow_blocks<ALLOC_TY>(V, k, tx, ty, sh, [&](int bx, int by, int bz) { hit(pack_key(bx, by, bz)); });
         __syncthreads();  // shared state is reused by the CTA's next tile
     }
 }

@@ -107,10 +107,10 @@ void prof_pair(sc_volume* V, cudaEvent_t a, cudaEvent_t b, int kind) {
 
 namespace {
 
-// Plain path: one CTA per 32x16 pixel tile of one keyframe.
+// Plain path: one CTA per 32x32 pixel tile of one keyframe.
 __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) alloc_kernel(DevVolume V, KfCam k, PlainSink sk) {
     __shared__ AllocShared sh;
-    alloc_tile(V, k, blockIdx.x, blockIdx.y, sk, sh);
+    alloc_tile<ALLOC_TY_PLAIN>(V, k, blockIdx.x, blockIdx.y, sk, sh);
 }
 
 // =================================================================== update ====
@@ -274,7 +274,7 @@ namespace sc {
 
 cudaError_t launch_alloc(sc_volume* V, const KfCam& cam, int32_t* list, int32_t* count, uint32_t call_id,
                          cudaStream_t s) {
-    dim3 grid((cam.W + ALLOC_TX - 1) / ALLOC_TX, (cam.H + ALLOC_TY - 1) / ALLOC_TY);
+    dim3 grid((cam.W + ALLOC_TX - 1) / ALLOC_TX, (cam.H + ALLOC_TY_PLAIN - 1) / ALLOC_TY_PLAIN);
     PlainSink sk{V->stamp, call_id, list, count, V->p.max_blocks_per_keyframe, nullptr, nullptr, 0};
     alloc_kernel<<<grid, ALLOC_THREADS, 0, s>>>(V->dv, cam, sk);
     count_launches(1);
@@ -674,6 +674,8 @@ extern "C" int sc_get_profile(sc_volume* V, sc_profile* out) {
     p.batch_launches = V->prof_n[2];
     p.batch_union_blocks = (int64_t)c[1];
     p.batch_pairs = (int64_t)c[2];
+    p.mc_ms = V->prof_ms[5];
+    p.mc_launches = V->prof_n[5];
     *out = p;
     return SC_OK;
 }

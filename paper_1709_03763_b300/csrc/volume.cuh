@@ -49,8 +49,8 @@ struct sc_volume {
     };
     std::vector<EvPair> ev_pending;
     std::vector<cudaEvent_t> ev_free;
-    double prof_ms[5];  // alloc, update, batch alloc, batch mark, batch net
-    int64_t prof_n[3];  // alloc launches, update launches, batch launches
+    double prof_ms[6];  // alloc, update, batch alloc, batch mark, batch net, marching cubes
+    int64_t prof_n[6];  // launches: alloc, update, batch, -, -, marching cubes
     cudaEvent_t graph_ev[4];
 };
 
