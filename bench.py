@@ -82,7 +82,7 @@ def parse():
                          "--profile-from-start off); prints only the timing")
     ap.add_argument("--profile-colour", action="store_true",
                     help="run colour fusion steps between cudaProfilerStart/Stop (for ncu) and exit")
-    ap.add_argument("--profile-extra", choices=["mc", "kf", "stream"], default=None,
+    ap.add_argument("--profile-extra", choices=["mc", "kf", "overlap", "stream"], default=None,
                     help="run Marching Cubes / KF_OVRLP grouping / a stream-out + stream-in of the "
                          "step's volume between cudaProfilerStart/Stop (for ncu) and exit")
     ap.add_argument("--keyframes", type=int, default=60, help="keyframes of the workload (small ncu cases)")
@@ -804,7 +804,7 @@ def main():
     setup_s = time.perf_counter() - t_setup
 
     if args.profile_extra:
-        from paper_1709_03763_b300 import KF_OVRLP, BlockStore, segment_keyframes
+        from paper_1709_03763_b300 import KF_OVRLP, BlockStore, overlap_counts, segment_keyframes
         P.step()
         torch.cuda.synchronize()
         nfr = P.K * KAPPA
@@ -817,6 +817,8 @@ def main():
                 V.marching_cubes(capacity=mc_out.shape[0], out=mc_out)
             elif args.profile_extra == "kf":
                 segment_keyframes(KF_OVRLP, (KF_OVRLP_THR,), w.frame_poses[:nfr], w.intr, w.frames_depth[:nfr])
+            elif args.profile_extra == "overlap":  # the overlap counts of 32 frames against frame 0
+                overlap_counts(w.frames_depth[:32], w.frame_poses[:32], w.frame_poses[0], w.intr)
             else:
                 V.stream_out(store, cam, STREAM_RADIUS)
                 V.stream_in(store, cam)
