@@ -100,12 +100,12 @@ __device__ __forceinline__ void overlap_reduce(unsigned valid, unsigned inside, 
 // thread.  counts: this frame's pair.
 template <bool VEC4>
 __device__ __forceinline__ void overlap_frame(const OvFrame& F, const OvCam& c, const float* __restrict__ depths,
-                                              unsigned long long* counts) {
+                                              unsigned long long* counts, int bx, int by) {
     unsigned valid = 0, inside = 0;
-    const int v = blockIdx.y * OV_TY + threadIdx.y;
+    const int v = by * OV_TY + threadIdx.y;
     const float* Z = depths + (size_t)F.frame * c.W * c.H;
     if (VEC4) {
-        const int u0 = 4 * (blockIdx.x * OV_TX + threadIdx.x);
+        const int u0 = 4 * (bx * OV_TX + threadIdx.x);
         if (u0 < c.W && v < c.H) {
             const float4 z = __ldg(reinterpret_cast<const float4*>(Z + (size_t)v * c.W + u0));
             const float uf = (float)u0, yn = ((float)v - c.cy) * c.ify;
@@ -115,7 +115,7 @@ __device__ __forceinline__ void overlap_frame(const OvFrame& F, const OvCam& c, 
             overlap_pixel(F, c, uf + 3.f, yn, z.w, valid, inside);
         }
     } else {
-        const int u = blockIdx.x * OV_TX + threadIdx.x;
+        const int u = bx * OV_TX + threadIdx.x;
         if (u < c.W && v < c.H)
             overlap_pixel(F, c, (float)u, ((float)v - c.cy) * c.ify, __ldg(Z + (size_t)v * c.W + u), valid, inside);
     }
@@ -125,7 +125,7 @@ __device__ __forceinline__ void overlap_frame(const OvFrame& F, const OvCam& c, 
 template <bool VEC4>
 __global__ void __launch_bounds__(OV_TX* OV_TY) overlap_kernel(const float* __restrict__ depths, const OvArgs a,
                                                                const OvCam c, unsigned long long* counts) {
-    overlap_frame<VEC4>(a.f[blockIdx.z], c, depths, counts + 2 * blockIdx.z);
+    overlap_frame<VEC4>(a.f[blockIdx.z], c, depths, counts + 2 * blockIdx.z, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------ the grouping loop on the device ----
@@ -179,13 +179,16 @@ __host__ __device__ inline void ov_compose(const sc_pose& Tk, const sc_pose& T, 
     F.pad = 0;
 }
 
-// The step's overlap counts: grid z = slot in the step (slots past the step's length
-// exit at once).
+// The step's overlap counts: persistent CTAs over (slot in the step, tile of the frame),
+// so a short step launches no idle CTAs.
 template <bool VEC4>
-__global__ void __launch_bounds__(OV_TX* OV_TY) overlap_step_kernel(OvState* st) {
-    const int z = blockIdx.z;
-    if (z >= st->step) return;
-    overlap_frame<VEC4>(st->tab[z], st->cam, st->depths, st->counts[z]);
+__global__ void __launch_bounds__(OV_TX* OV_TY) overlap_step_kernel(OvState* st, int tiles_x, int tiles) {
+    const int n = st->step * tiles;
+    for (int w = blockIdx.x; w < n; w += gridDim.x) {
+        const int z = w / tiles, t = w - z * tiles;
+        overlap_frame<VEC4>(st->tab[z], st->cam, st->depths, st->counts[z], t % tiles_x, t / tiles_x);
+        __syncthreads();  // the reduction's shared partials are reused by the next tile
+    }
 }
 
 // One warp: the step's decisions (ratio = inside / valid in double, below thr starts a
@@ -270,11 +273,15 @@ cudaError_t ov_graph_build(OvGraph& G, int W, int H, bool vec4) {
     }
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     OvState* st = G.st;
-    void* a1[] = {&st};
+    int tiles_x = vec4 ? (W / 4 + OV_TX - 1) / OV_TX : (W + OV_TX - 1) / OV_TX;
+    int tiles = tiles_x * ((H + OV_TY - 1) / OV_TY);
+    void* a1[] = {&st, &tiles_x, &tiles};
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaKernelNodeParams k1 = {};
     k1.func = vec4 ? (void*)overlap_step_kernel<true> : (void*)overlap_step_kernel<false>;
-    k1.gridDim = vec4 ? dim3((W / 4 + OV_TX - 1) / OV_TX, (H + OV_TY - 1) / OV_TY, OV_SPEC)
-                      : dim3((W + OV_TX - 1) / OV_TX, (H + OV_TY - 1) / OV_TY, OV_SPEC);
+    k1.gridDim = dim3(std::min(sms * 8, OV_SPEC * tiles));
     k1.blockDim = dim3(OV_TX, OV_TY);
     k1.kernelParams = a1;
     cudaGraphNode_t n1, n2;
