@@ -322,7 +322,12 @@ int sc_deintegrate_keyframe(sc_volume* vol, int32_t kf_id, const float* depth, c
  * voxel touched by any item receives its summed net change in one
  * read-modify-write.  Runs as one CUDA graph (replayed across calls) whose voxel
  * work is a single persistent launch.  items host [n], 1 <= n <= max_batch, kf_ids
- * distinct and integrated.  Synchronises the stream to read the device status. */
+ * distinct and integrated.  Asynchronous: argument errors return at once; device
+ * errors (full hash table, pool or block list) set the sticky status word that
+ * sc_get_status and the synchronising calls report, after which the volume's contents
+ * are undefined.  The call waits only until the launch two batch calls back has read
+ * its item table (two alternating host staging copies); with profiling on
+ * (sc_set_profiling) it synchronises and returns the device status. */
 int sc_reintegrate_batch(sc_volume* vol, const sc_reint_item* items, int32_t n, const sc_intrinsics* intr,
                          sc_stream stream);
 
@@ -331,7 +336,7 @@ int sc_reintegrate_batch(sc_volume* vol, const sc_reint_item* items, int32_t n, 
  * read-modify-write per touched voxel with the keyframes' summed contributions.
  * Equal to n sc_integrate_keyframe calls in order, up to float summation order.
  * kf_ids, depths (device pointers), rgbas (device pointers), poses: host [n],
- * 1 <= n <= max_batch, ids distinct.  Synchronises the stream. */
+ * 1 <= n <= max_batch, ids distinct.  Asynchronous, as sc_reintegrate_batch. */
 int sc_integrate_keyframes(sc_volume* vol, const int32_t* kf_ids, const float* const* depths,
                            const uint8_t* const* rgbas, const sc_pose* poses, int32_t n, const sc_intrinsics* intr,
                            sc_stream stream);
@@ -501,7 +506,8 @@ int sc_sdf_loss(sc_volume* vol, const float* points, int64_t n, float lambda, fl
  *   grad_depth     device [n][H][W] float or NULL, overwritten
  * Its keyframe tables and accumulators belong to the volume (allocated by the
  * first call, grown when n exceeds them), so calls on different volumes share no
- * scratch; the call synchronises the stream before it rewrites the tables. */
+ * scratch.  Asynchronous: before it rewrites the tables the call waits only until the
+ * previous call's copies of them have been made (not for other queued work). */
 int sc_sdf_adjoint(sc_volume* vol, const int32_t* kf_ids, const float* const* depths, const sc_pose* poses,
                    int32_t n, const sc_intrinsics* intr, const float* grad_D, double* grad_xi, float* grad_depth,
                    sc_stream stream);

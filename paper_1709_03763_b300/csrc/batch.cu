@@ -52,6 +52,7 @@ struct BatchHeader {
     int32_t tiles_x;
     int32_t tiles;
 };
+constexpr size_t STAGE_HDR = 256;  // header bytes ahead of the item table in a staging block
 
 constexpr int ALLOC_CTAS_PER_SM = SC_ALLOC_CTAS_PER_SM;  // persistent allocation CTAs per SM
 
@@ -540,10 +541,16 @@ struct BatchState {
     uint32_t* masks = nullptr;
     int32_t* ulist = nullptr;
     int32_t* counters = nullptr;
+    // the call's header and item table travel as one block: STAGE_HDR bytes of header,
+    // then the items; two pinned host copies alternate between calls, each guarded by an
+    // event recorded after the launch that read it, so a call waits only for the launch
+    // two calls back instead of synchronising the stream
+    unsigned char* stage_d = nullptr;
+    BatchHeader* hdr_d = nullptr;  // views into stage_d
     BatchItem* items_d = nullptr;
-    BatchHeader* hdr_d = nullptr;
-    BatchItem* items_h = nullptr;  // pinned
-    BatchHeader* hdr_h = nullptr;  // pinned
+    unsigned char* stage_h[2] = {nullptr, nullptr};  // pinned
+    cudaEvent_t staged[2] = {nullptr, nullptr};
+    int buf = 0;  // staging copy of the next call
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -564,10 +571,11 @@ void batch_destroy(sc_volume* V) {
     if (B->counters) cudaFree(B->counters);
     if (B->zero) cudaFree(B->zero);
     if (B->tex) cudaFree(B->tex);
-    if (B->items_d) cudaFree(B->items_d);
-    if (B->hdr_d) cudaFree(B->hdr_d);
-    if (B->items_h) cudaFreeHost(B->items_h);
-    if (B->hdr_h) cudaFreeHost(B->hdr_h);
+    if (B->stage_d) cudaFree(B->stage_d);
+    for (int k = 0; k < 2; ++k) {
+        if (B->stage_h[k]) cudaFreeHost(B->stage_h[k]);
+        if (B->staged[k]) cudaEventDestroy(B->staged[k]);
+    }
     delete B;
     V->batch = nullptr;
 }
@@ -588,10 +596,14 @@ int batch_init(sc_volume* V) {
     SC_CUDA(cudaMalloc((void**)&B->counters, 4 * sizeof(int32_t)));
     SC_CUDA(cudaMalloc((void**)&B->zero, sizeof(int32_t)));
     SC_CUDA(cudaMemset(B->zero, 0, sizeof(int32_t)));
-    SC_CUDA(cudaMalloc((void**)&B->items_d, (size_t)V->p.max_batch * sizeof(BatchItem)));
-    SC_CUDA(cudaMalloc((void**)&B->hdr_d, sizeof(BatchHeader)));
-    SC_CUDA(cudaMallocHost((void**)&B->items_h, (size_t)V->p.max_batch * sizeof(BatchItem)));
-    SC_CUDA(cudaMallocHost((void**)&B->hdr_h, sizeof(BatchHeader)));
+    const size_t stage_bytes = STAGE_HDR + (size_t)V->p.max_batch * sizeof(BatchItem);
+    SC_CUDA(cudaMalloc((void**)&B->stage_d, stage_bytes));
+    B->hdr_d = reinterpret_cast<BatchHeader*>(B->stage_d);
+    B->items_d = reinterpret_cast<BatchItem*>(B->stage_d + STAGE_HDR);
+    for (int k = 0; k < 2; ++k) {
+        SC_CUDA(cudaMallocHost((void**)&B->stage_h[k], stage_bytes));
+        SC_CUDA(cudaEventCreateWithFlags(&B->staged[k], cudaEventDisableTiming));
+    }
     SC_CUDA(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
     const size_t smem = nd_smem_bytes(V);
     if (smem > 48 * 1024) {
@@ -619,9 +631,8 @@ int ctas_per_sm_clamped(sc_volume* V, const sc_batch_config& c) {
 cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_node) {
     BatchState* B = V->batch;
     cudaError_t e;
-    if ((e = cudaMemcpyAsync(B->hdr_d, B->hdr_h, sizeof(BatchHeader), cudaMemcpyHostToDevice, s)) != cudaSuccess)
-        return e;
-    if ((e = cudaMemcpyAsync(B->items_d, B->items_h, sizeof(BatchItem), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(B->stage_d, B->stage_h[0], STAGE_HDR + sizeof(BatchItem), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
         return e;
     if (items_node) {
         cudaStreamCaptureStatus st;
@@ -662,6 +673,8 @@ int ensure_graph(sc_volume* V) {
     const bool same = B->exec && !memcmp(&B->graph_cfg, &V->bcfg, sizeof(sc_batch_config)) &&
                       !memcmp(&B->graph_dv, &V->dv, sizeof(DevVolume));
     if (same) return SC_OK;
+    // no launch of the old graph may still be in flight
+    for (int k = 0; k < 2; ++k) SC_CUDA(cudaEventSynchronize(B->staged[k]));
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);
         B->exec = nullptr;
@@ -735,9 +748,13 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
             B->exec = nullptr;
         }
     }
+    // this call's staging copy: free once the launch two calls back has read it
+    SC_CUDA(cudaEventSynchronize(B->staged[B->buf]));
+    BatchHeader* hdr_h = reinterpret_cast<BatchHeader*>(B->stage_h[B->buf]);
+    BatchItem* items_h = reinterpret_cast<BatchItem*>(B->stage_h[B->buf] + STAGE_HDR);
     for (int i = 0; i < n; ++i) {
         const ItemSpec& it = items[i];
-        BatchItem& b = B->items_h[i];
+        BatchItem& b = items_h[i];
         const int cur = V->cur[it.kf_id];
         b.oldc = make_cam(V, K, it.oldp ? it.oldp : it.newp, it.depth, it.rgba);
         b.newc = make_cam(V, K, it.newp, it.depth, it.rgba);
@@ -748,15 +765,15 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         b.oldc.tex = b.newc.tex = B->tex + (size_t)i * B->tex_stride;
     }
     if (++V->call_id == 0) V->call_id = 1;  // (plain calls reset stamps on wrap)
-    B->hdr_h->n = n;
-    B->hdr_h->call_id = V->call_id;
-    B->hdr_h->tiles_x = (K->width + ALLOC_TX - 1) / ALLOC_TX;
-    B->hdr_h->tiles = B->hdr_h->tiles_x * ((K->height + ALLOC_TY - 1) / ALLOC_TY);
+    hdr_h->n = n;
+    hdr_h->call_id = V->call_id;
+    hdr_h->tiles_x = (K->width + ALLOC_TX - 1) / ALLOC_TX;
+    hdr_h->tiles = hdr_h->tiles_x * ((K->height + ALLOC_TY - 1) / ALLOC_TY);
     rc = ensure_graph(V);
     if (rc) return rc;
-    // resize the item-table copy to the n items of this call
-    SC_CUDA(cudaGraphExecMemcpyNodeSetParams1D(B->exec, B->items_node, B->items_d, B->items_h,
-                                               (size_t)n * sizeof(BatchItem), cudaMemcpyHostToDevice));
+    // point the table copy at this call's staging copy, sized to its n items
+    SC_CUDA(cudaGraphExecMemcpyNodeSetParams1D(B->exec, B->items_node, B->stage_d, B->stage_h[B->buf],
+                                               STAGE_HDR + (size_t)n * sizeof(BatchItem), cudaMemcpyHostToDevice));
     return SC_OK;
 }
 
@@ -770,12 +787,19 @@ int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_
 
 constexpr int GRAPH_KERNELS = 6;  // init, pack, batched allocation, mark old, net-delta, clear
 
-int launch_and_check(sc_volume* V, cudaStream_t s) {
-    SC_CUDA(cudaGraphLaunch(V->batch->exec, s));
+// Launch the prepared graph.  Asynchronous: device errors stay in the volume's sticky
+// status word (sc_get_status); with profiling on, the call synchronises to read the
+// graph's event times and returns the status as well.
+int launch_batch(sc_volume* V, cudaStream_t s) {
+    BatchState* B = V->batch;
+    SC_CUDA(cudaGraphLaunch(B->exec, s));
     count_launches(GRAPH_KERNELS);
-    SC_CUDA(cudaStreamSynchronize(s));
+    SC_CUDA(cudaEventRecord(B->staged[B->buf], s));
+    B->buf ^= 1;
     V->last_stream = s;
-    if (V->prof_on) {
+    if (!V->prof_on) return SC_OK;
+    SC_CUDA(cudaStreamSynchronize(s));
+    {
         float a = 0.f, b = 0.f, c = 0.f;
         if (cudaEventElapsedTime(&a, V->graph_ev[0], V->graph_ev[1]) == cudaSuccess &&
             cudaEventElapsedTime(&b, V->graph_ev[1], V->graph_ev[2]) == cudaSuccess &&
@@ -797,7 +821,7 @@ extern "C" int sc_reintegrate_batch(sc_volume* V, const sc_reint_item* items, in
     int rc = prepare_items(V, items, n, K);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = launch_and_check(V, s);
+    rc = launch_batch(V, s);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) V->cur[items[i].kf_id] ^= 1;
     return SC_OK;
@@ -812,7 +836,7 @@ extern "C" int sc_integrate_keyframes(sc_volume* V, const int32_t* kf_ids, const
     int rc = prepare_specs(V, sp.data(), n, K);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = launch_and_check(V, s);
+    rc = launch_batch(V, s);
     if (rc) return rc;
     for (int i = 0; i < n; ++i) {
         V->cur[kf_ids[i]] ^= 1;

@@ -349,6 +349,7 @@ struct AdjScratch {
     double* acc_d = nullptr;
     AdjItem* items_h = nullptr;
     AdjPose* poses_h = nullptr;
+    cudaEvent_t staged = nullptr;  // recorded after the last call's copies from items_h / poses_h
 };
 
 namespace {
@@ -359,6 +360,7 @@ void adj_free(AdjScratch& A) {
     if (A.acc_d) cudaFree(A.acc_d);
     if (A.items_h) cudaFreeHost(A.items_h);
     if (A.poses_h) cudaFreeHost(A.poses_h);
+    if (A.staged) cudaEventDestroy(A.staged);
     A = AdjScratch();
 }
 
@@ -378,6 +380,7 @@ int adj_reserve(sc_volume* V, int n) {
     SC_CUDA(cudaMalloc((void**)&A.acc_d, cap * 4 * sizeof(double)));
     SC_CUDA(cudaMallocHost((void**)&A.items_h, cap * sizeof(AdjItem)));
     SC_CUDA(cudaMallocHost((void**)&A.poses_h, cap * sizeof(AdjPose)));
+    SC_CUDA(cudaEventCreateWithFlags(&A.staged, cudaEventDisableTiming));
     A.cap = cap;
     return SC_OK;
 }
@@ -425,8 +428,9 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
     int rc = adj_reserve(V, n);
     if (rc) return rc;
     AdjScratch& A = *V->adj;
-    // the pinned staging tables may still be read by a previous call's copies
-    SC_CUDA(cudaStreamSynchronize(s));
+    // the pinned staging tables may still be read by a previous call's copies: wait for
+    // those copies only, not for the work queued on the stream since
+    SC_CUDA(cudaEventSynchronize(A.staged));
     const size_t img = (size_t)K->width * K->height;
     for (int i = 0; i < n; ++i) {
         const int kf = kf_ids[i];
@@ -442,6 +446,7 @@ extern "C" int sc_sdf_adjoint(sc_volume* V, const int32_t* kf_ids, const float* 
     }
     SC_CUDA(cudaMemcpyAsync(A.items_d, A.items_h, n * sizeof(AdjItem), cudaMemcpyHostToDevice, s));
     SC_CUDA(cudaMemcpyAsync(A.poses_d, A.poses_h, n * sizeof(AdjPose), cudaMemcpyHostToDevice, s));
+    SC_CUDA(cudaEventRecord(A.staged, s));
     SC_CUDA(cudaMemsetAsync(A.acc_d, 0, n * 4 * sizeof(double), s));
     if (grad_depth) SC_CUDA(cudaMemsetAsync(grad_depth, 0, n * img * sizeof(float), s));
     const int chunks = std::max(1, std::min(64, (V->num_sms * 8 + n - 1) / n));
