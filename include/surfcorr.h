@@ -190,7 +190,10 @@ int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses
  * < n_kf) at pose kf_poses[frame_kf[f]] (host [n_kf]).  Outputs kf_depth and
  * kf_weight are device [n_kf][H][W], overwritten.  Same per-keyframe result as
  * sc_fuse_frames_into_keyframe on each keyframe's frames (up to float summation
- * order); one fusion launch per 64 frames and one normalisation launch. */
+ * order).  Widths a multiple of 4: one launch initialises each keyframe's sums from
+ * its first frame at the keyframe pose (no zeroing), then one scatter launch per 512
+ * other frames and one normalisation launch; other widths zero the sums and scatter
+ * every frame. */
 int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n_frames,
                       const sc_pose* kf_poses, int32_t n_kf, const sc_intrinsics* intr,
                       const sc_fusion_params* fusion, float* kf_depth, float* kf_weight, sc_stream stream);

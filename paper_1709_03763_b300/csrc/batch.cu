@@ -10,8 +10,10 @@
 // batch therefore computes each touched voxel's net change over all items and
 // applies it with ONE read-modify-write of its D / W / C, instead of 2n.
 //
-// Graph (captured once per launch configuration, replayed every call):
-//   1. H2D copy of the item table (pinned staging -> device; node resized per call)
+// Graph (captured once per launch configuration, replayed every call, launched without
+// a host synchronisation):
+//   1. H2D copy of the call's header and item table (one of two alternating pinned
+//      staging blocks; the node is pointed at it and resized per call)
 //   2. init: zero counters and the items' new block-list counts
 //   3. batched allocation of A(k, T_new) for all items (persistent over
 //      (item, pixel tile)); each item's new list is deduplicated with a per-slot

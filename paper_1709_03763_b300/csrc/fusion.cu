@@ -9,7 +9,8 @@
 // divides and writes Z* and W*.  A frame taken at the keyframe's own pose (the first
 // of a KF_CONST group) maps every pixel onto itself, so it initialises the sums with
 // plain stores, which also replaces zeroing them.  One thread per 4 pixels of a frame
-// row; up to 64 frames per launch.
+// row; up to 512 frames per launch (fewer launches, fewer partly filled last waves:
+// the 540 scattered frames of 60 keyframes take 2 launches, 5 % faster than 9).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -20,7 +21,7 @@
 
 namespace {
 
-constexpr int FUSE_MAX_FRAMES = 64;  // frames per launch (kernel parameter space)
+constexpr int FUSE_MAX_FRAMES = 512;  // frames per launch: 56 B each of the 32 KB kernel parameter space
 
 constexpr int FUSE_TX = 32, FUSE_TY = 8;
 
