@@ -330,7 +330,11 @@ int sc_deintegrate_keyframe(sc_volume* vol, int32_t kf_id, const float* depth, c
  * sc_get_status and the synchronising calls report, after which the volume's contents
  * are undefined.  The call waits only until the launch two batch calls back has read
  * its item table (two alternating host staging copies); with profiling on
- * (sc_set_profiling) it synchronises and returns the device status. */
+ * (sc_set_profiling) it synchronises and returns the device status.  The batch packs
+ * each item's depth and colour into one texel image per position in the batch; an
+ * item whose keyframe the previous batch packed at the same position from the same
+ * pointers, and which has stayed integrated since, is not packed again (an integrated
+ * keyframe's images must not change: its de-integration needs them). */
 int sc_reintegrate_batch(sc_volume* vol, const sc_reint_item* items, int32_t n, const sc_intrinsics* intr,
                          sc_stream stream);
 

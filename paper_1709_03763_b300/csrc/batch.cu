@@ -46,6 +46,7 @@ struct BatchItem {
     int32_t* old_count;
     int32_t* new_list;
     int32_t* new_count;
+    int32_t packed;  // the item's texel slot already holds its images (the pack skips it)
 };
 
 struct BatchHeader {
@@ -187,6 +188,7 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
     const size_t total = (size_t)hdr->n * q;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int it = (int)(i / q);
+        if (items[it].packed) continue;
         const uint32_t p = (uint32_t)(i - (size_t)it * q) * 4;
         const KfCam& k = items[it].newc;
         const float4 d = __ldg(reinterpret_cast<const float4*>(k.depth + p));
@@ -202,6 +204,7 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)hdr->n * nr;
          i += (size_t)gridDim.x * blockDim.x) {
         const int it = (int)(i / nr);
+        if (items[it].packed) continue;
         const uint32_t p = r0 + (uint32_t)(i % nr);
         const KfCam& k = items[it].newc;
         tex[(size_t)it * stride + p] = p < npx ? pack_texel(k.depth[p], k.rgba[p]) : make_uint2(0xff800000u, 0u);
@@ -553,6 +556,16 @@ struct BatchState {
     unsigned char* stage_h[2] = {nullptr, nullptr};  // pinned
     cudaEvent_t staged[2] = {nullptr, nullptr};
     int buf = 0;  // staging copy of the next call
+    // what each texel slot holds: the keyframe, its image pointers and image binding
+    // count, and the image size, when a batch packed it
+    struct PackedSlot {
+        int32_t kf = -1;
+        const float* depth = nullptr;
+        const uint8_t* rgba = nullptr;
+        uint32_t epoch = 0;
+        uint32_t px = 0;
+    };
+    std::vector<PackedSlot> slots;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -750,6 +763,7 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
             B->exec = nullptr;
         }
     }
+    if (B->slots.size() != (size_t)V->p.max_batch) B->slots.assign(V->p.max_batch, BatchState::PackedSlot());
     // this call's staging copy: free once the launch two calls back has read it
     SC_CUDA(cudaEventSynchronize(B->staged[B->buf]));
     BatchHeader* hdr_h = reinterpret_cast<BatchHeader*>(B->stage_h[B->buf]);
@@ -765,6 +779,18 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         b.new_list = list_ptr(V, it.kf_id, 1 - cur);
         b.new_count = count_ptr(V, it.kf_id, 1 - cur);
         b.oldc.tex = b.newc.tex = B->tex + (size_t)i * B->tex_stride;
+        // a keyframe that is not integrated yet binds its images now; an integrated one
+        // keeps the images of its integration (de-integration must use them), so a slot
+        // packed from the same pointers under the same binding still holds them
+        if (!it.oldp) ++V->img_epoch[it.kf_id];
+        BatchState::PackedSlot& ps = B->slots[i];
+        b.packed = it.oldp && ps.kf == it.kf_id && ps.depth == it.depth && ps.rgba == it.rgba &&
+                   ps.epoch == V->img_epoch[it.kf_id] && ps.px == B->tex_px;
+        ps.kf = it.kf_id;
+        ps.depth = it.depth;
+        ps.rgba = it.rgba;
+        ps.epoch = V->img_epoch[it.kf_id];
+        ps.px = B->tex_px;
     }
     if (++V->call_id == 0) V->call_id = 1;  // (plain calls reset stamps on wrap)
     hdr_h->n = n;

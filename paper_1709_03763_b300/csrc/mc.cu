@@ -362,6 +362,7 @@ extern "C" int sc_set_keyframe_blocks(sc_volume* V, int32_t kf_id, const int32_t
         return st;
     }
     V->integrated[kf_id] = 1;
+    ++V->img_epoch[kf_id];
     V->nonresident[kf_id] = 0;
     return SC_OK;
 }

@@ -369,6 +369,7 @@ extern "C" int sc_create_volume(const sc_volume_params* p, sc_volume** out) {
     if (!V) return SC_ERR_CUDA;
     V->p = *p;
     V->integrated.assign(p->max_keyframes, 0);
+    V->img_epoch.assign(p->max_keyframes, 0);
     V->cur.assign(p->max_keyframes, 0);
     V->nonresident.assign(p->max_keyframes, 0);
     V->call_id = 0;
@@ -554,6 +555,7 @@ extern "C" int sc_integrate_keyframe(sc_volume* V, int32_t kf_id, const float* d
     prof_pair(V, e0, e1, 0);
     prof_pair(V, e1 ? e1 : nullptr, e2, 1);
     V->integrated[kf_id] = 1;
+    ++V->img_epoch[kf_id];
     V->last_stream = s;
     return SC_OK;
 }

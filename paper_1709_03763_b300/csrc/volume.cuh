@@ -32,6 +32,10 @@ struct sc_volume {
     std::vector<uint8_t> integrated;
     std::vector<uint8_t> cur;  // which of the two list buffers holds the current list
     std::vector<uint8_t> nonresident;  // the current list names a block in a host block store
+    // per keyframe, counts the times it became integrated: its images (depth, colour) are
+    // bound from then until it is de-integrated, so a batch may reuse texels it packed
+    // from the same images under the same count
+    std::vector<uint32_t> img_epoch;
     uint32_t call_id;
     cudaStream_t last_stream;
     int32_t* h_status;  // pinned

@@ -82,3 +82,25 @@ def test_extract_capacity_reports_true_count(tinyg):
     assert e.value.code == _lib.SC_ERR_CAPACITY
     full = V.extract()
     assert full["coords"].shape[0] == n
+
+
+def test_batched_calls_report_device_errors_through_the_status(tinyg):
+    # batched integration and pose updates launch without synchronising: a full pool
+    # does not fail the call, it sets the sticky status that sc_get_status reads
+    w, D, C = tinyg
+    V = gpu_volume(w, max_blocks=64)
+    ids = [0, 1]
+    V.integrate_many(ids, D[ids], C[ids], w.kf_poses[ids], w.intr)
+    assert V.status() == _lib.SC_ERR_POOL_FULL
+    assert V.status() == 0  # read and cleared
+    # back-to-back batched calls alternate their staging tables: a third call reuses the
+    # first one's, after that launch has read it
+    W2 = gpu_volume(w)
+    for k in range(3):
+        W2.integrate_many([k], D[k:k + 1], C[k:k + 1], w.kf_poses[k:k + 1], w.intr)
+    W2.check()
+    O = gpu_volume(w)
+    for k in range(3):
+        O.integrate(k, D[k], C[k], w.intr, w.kf_poses[k])
+    a, b = W2.extract(), O.extract()
+    assert a["coords"].shape == b["coords"].shape
