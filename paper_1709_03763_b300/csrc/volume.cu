@@ -201,35 +201,67 @@ __global__ void __launch_bounds__(UPD_THREADS) update_kernel(DevVolume V, KfCam 
 
 // ============================================================== extraction ====
 
-__global__ void extract_kernel(DevVolume V, uint32_t n_entries, int32_t* coords, int32_t* slots, int32_t* tmp,
-                               uint32_t* count, uint32_t cap) {
-    const int lane = threadIdx.x & 31;
-    for (uint32_t base = blockIdx.x * blockDim.x; base < n_entries; base += gridDim.x * blockDim.x) {
-        const uint32_t e = base + threadIdx.x;
-        bool ok = false;
-        unsigned long long key = KEY_EMPTY;
-        int32_t slot = -1;
-        if (e < n_entries) {
-            key = V.table[e].key;
-            slot = V.table[e].slot;
-            ok = key != KEY_EMPTY && slot >= 0;
+constexpr int EXTRACT_THREADS = 256;
+constexpr int EXTRACT_PER = 4;  // hash entries per thread and round
+
+__global__ void __launch_bounds__(EXTRACT_THREADS) extract_kernel(DevVolume V, uint32_t n_entries, int32_t* coords,
+                                                                  int32_t* slots, int32_t* tmp, uint32_t* count,
+                                                                  uint32_t cap) {
+    // each round a CTA takes 1024 consecutive entries (warp w: 128 of them, four 16-byte
+    // loads per lane, all requested before any is examined); the CTA's occupied entries
+    // get their output positions from one atomic add per CTA and round
+    __shared__ uint32_t wbase[EXTRACT_THREADS / 32];
+    __shared__ uint32_t cta_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint32_t PER_CTA = EXTRACT_THREADS * EXTRACT_PER;
+    const uint4* tab = reinterpret_cast<const uint4*>(V.table);
+    for (uint32_t cb = blockIdx.x * PER_CTA; cb < n_entries; cb += gridDim.x * PER_CTA) {  // uniform in the CTA
+        uint4 ent[EXTRACT_PER];
+#pragma unroll
+        for (int j = 0; j < EXTRACT_PER; ++j) {
+            const uint32_t e = cb + warp * 32 * EXTRACT_PER + 32 * j + lane;
+            ent[j] = e < n_entries ? __ldg(tab + e) : make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0u);
         }
-        const unsigned m = __ballot_sync(0xffffffffu, ok);
-        if (!m) continue;
-        uint32_t b = 0;
-        if (lane == 0) b = atomicAdd(count, (uint32_t)__popc(m));
-        b = __shfl_sync(0xffffffffu, b, 0);
-        if (!ok) continue;
-        const uint32_t i = b + __popc(m & ((1u << lane) - 1u));
-        if (i >= cap) continue;
-        const int3 c = unpack_key(key);
-        if (coords) {
-            coords[3 * i] = c.x;
-            coords[3 * i + 1] = c.y;
-            coords[3 * i + 2] = c.z;
+        bool ok[EXTRACT_PER];
+        unsigned m[EXTRACT_PER];
+        uint32_t wc = 0;
+#pragma unroll
+        for (int j = 0; j < EXTRACT_PER; ++j) {
+            const unsigned long long key = (unsigned long long)ent[j].x | ((unsigned long long)ent[j].y << 32);
+            ok[j] = key != KEY_EMPTY && (int32_t)ent[j].z >= 0;
+            m[j] = __ballot_sync(0xffffffffu, ok[j]);
+            wc += (uint32_t)__popc(m[j]);
         }
-        if (slots) slots[i] = slot;
-        tmp[i] = slot;
+        if (lane == 0) wbase[warp] = wc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < EXTRACT_THREADS / 32; ++w) {
+                const uint32_t c = wbase[w];
+                wbase[w] = t;
+                t += c;
+            }
+            cta_base = t ? atomicAdd(count, t) : 0u;
+        }
+        __syncthreads();
+        uint32_t b = cta_base + wbase[warp];
+#pragma unroll
+        for (int j = 0; j < EXTRACT_PER; ++j) {
+            const uint32_t i = b + (uint32_t)__popc(m[j] & ((1u << lane) - 1u));
+            b += (uint32_t)__popc(m[j]);
+            if (!ok[j] || i >= cap) continue;
+            const unsigned long long key = (unsigned long long)ent[j].x | ((unsigned long long)ent[j].y << 32);
+            const int3 c = unpack_key(key);
+            if (coords) {
+                coords[3 * i] = c.x;
+                coords[3 * i + 1] = c.y;
+                coords[3 * i + 2] = c.z;
+            }
+            const int32_t slot = (int32_t)ent[j].z;
+            if (slots) slots[i] = slot;
+            tmp[i] = slot;
+        }
+        __syncthreads();  // wbase and cta_base are rewritten by the next round
     }
 }
 
@@ -585,7 +617,7 @@ extern "C" int sc_extract_block_list(sc_volume* V, int32_t* coords, int32_t* slo
     const uint32_t nent = V->p.n_buckets * V->p.bucket_size;
     const uint32_t cap = (uint32_t)capacity < V->p.max_blocks ? (uint32_t)capacity : V->p.max_blocks;
     SC_CUDA(cudaMemsetAsync(V->extract_count, 0, sizeof(uint32_t), s));
-    extract_kernel<<<grid_for(V, 8), 256, 0, s>>>(V->dv, nent, coords, slots, V->extract_slots, V->extract_count,
+    extract_kernel<<<grid_for(V, 8), EXTRACT_THREADS, 0, s>>>(V->dv, nent, coords, slots, V->extract_slots, V->extract_count,
                                                   cap);
     count_launches(1);
     SC_CUDA(cudaGetLastError());
