@@ -441,14 +441,21 @@ __device__ __forceinline__ void nd_apply(const DevVolume& V, int32_t slot, size_
 }
 
 // One voxel group of a block: the samples of every item with a bit on the block,
-// then one read-modify-write.  In RGBA8 the voxel state is requested before the
-// samples (evict-first: it is read and written once), so its latency overlaps them.
+// then one read-modify-write (in RGBA8 evict-first: the state is read and written
+// once).  The state is loaded after the samples: held across them, its 12 registers
+// kept the kernel at 4 CTAs per SM; loaded late, it fits 48 registers and 5 CTAs
+// (Kinect pose update -2 %, batching workload +4 % re-integrations/s).
 template <bool F32, typename Acc>
 __device__ __forceinline__ void nd_group(const DevVolume& V, const NdCam* cams, int n_items, int32_t slot, int4 c,
                                          bool fresh, uint32_t mw0, uint32_t mw1, int mw, int lane, int g) {
     int lx0, ly, lz;
     lane_voxels(lane, g, lx0, ly, lz);
     const size_t off = (size_t)slot * NVOX + 4 * lane + 128 * g;
+    Acc A;
+    nd_init(A);
+    bool touched = false;
+    net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, A, touched);
+    if (!nd_changed(A, touched) && !fresh) return;
     float4 Dv = make_float4(0.f, 0.f, 0.f, 0.f), Wv = Dv;
     uint4 Cv = make_uint4(0u, 0u, 0u, 0u);
     if (!F32) {
@@ -459,11 +466,6 @@ __device__ __forceinline__ void nd_group(const DevVolume& V, const NdCam* cams, 
         Dv = *reinterpret_cast<const float4*>(V.D + off);
         Wv = *reinterpret_cast<const float4*>(V.W + off);
     }
-    Acc A;
-    nd_init(A);
-    bool touched = false;
-    net_delta_group(cams, n_items, c, lx0, ly, lz, mw0, mw1, mw, A, touched);
-    if (!nd_changed(A, touched) && !fresh) return;
     if (fresh) {  // first update of a new block: its memory holds no prior state
         Dv = make_float4(0.f, 0.f, 0.f, 0.f);
         Wv = Dv;
@@ -475,7 +477,7 @@ __device__ __forceinline__ void nd_group(const DevVolume& V, const NdCam* cams, 
 // Work unit u = (union block u / 4, voxel group u % 4): one warp, 128 voxels, four
 // per lane.  Units come from a queue in chunks of `grab`.
 #ifndef SC_ND_MIN_BLOCKS
-#define SC_ND_MIN_BLOCKS 4  // CTAs of 256 threads per SM the register budget must allow
+#define SC_ND_MIN_BLOCKS 5  // CTAs of 256 threads per SM the register budget must allow (48 registers)
 #endif
 
 template <bool F32>
