@@ -14,7 +14,9 @@
 // a host synchronisation):
 //   1. H2D copy of the call's header and item table (one of two alternating pinned
 //      staging blocks; the node is pointed at it and resized per call)
-//   2. init: zero counters and the items' new block-list counts
+//   2. pack: zero the counters and the items' new block-list counts; pack the depth and
+//      colour of each item whose texel slot does not already hold its images into
+//      8-byte texels (one gather per sample in step 5)
 //   3. batched allocation of A(k, T_new) for all items (persistent over
 //      (item, pixel tile)); each item's new list is deduplicated with a per-slot
 //      item bit; every touched slot joins the batch's union list once
@@ -46,7 +48,7 @@ struct BatchItem {
     int32_t* old_count;
     int32_t* new_list;
     int32_t* new_count;
-    int32_t packed;  // the item's texel slot already holds its images (the pack skips it)
+    int32_t pack_item;  // items[r].pack_item, r < n_pack: the r-th item whose texels this call packs
 };
 
 struct BatchHeader {
@@ -54,6 +56,7 @@ struct BatchHeader {
     uint32_t call_id;
     int32_t tiles_x;
     int32_t tiles;
+    int32_t n_pack;  // items whose texel slot does not already hold their images
 };
 constexpr size_t STAGE_HDR = 256;  // header bytes ahead of the item table in a staging block
 
@@ -79,12 +82,6 @@ struct BatchSink {
     __device__ void mark_new(int32_t slot) { atomicOr(masks + (size_t)slot * mw, bit); }
     __device__ bool union_first(int32_t slot) { return atomicExch(&stamp[slot], call_id) != call_id; }
 };
-
-__global__ void batch_init_kernel(const BatchItem* items, const BatchHeader* hdr, int32_t* counters) {
-    const int n = hdr->n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) *items[i].new_count = 0;
-    if (blockIdx.x == 0 && threadIdx.x < 4) counters[threadIdx.x] = 0;
-}
 
 __global__ void __launch_bounds__(ALLOC_THREADS, SC_ALLOC_CTAS_PER_SM) batch_alloc_kernel(DevVolume V, const BatchItem* items,
                                                                     const BatchHeader* hdr, uint32_t* masks, int mw,
@@ -182,14 +179,21 @@ __device__ __forceinline__ uint2 pack_texel(float z, uint32_t c) {
     return make_uint2(z > 0.f ? __float_as_uint(z) : 0xff800000u, (c & 0x00ffffffu) | 0x01000000u);
 }
 
+// Only the header's n_pack listed items are packed: a slot that already holds its
+// item's images is skipped without a pass over its pixels.  The first kernel of the
+// batch graph, so it also zeroes the items' new-list counts and the batch counters.
 __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr, uint2* tex, uint32_t npx,
-                                  uint32_t stride) {
+                                  uint32_t stride, int32_t* counters) {
+    const int n = hdr->n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) *items[i].new_count = 0;
+    if (blockIdx.x == 0 && threadIdx.x < 4) counters[threadIdx.x] = 0;
     const uint32_t q = npx / 4;  // 640 x 480 and every width multiple of 4: float4 / uint4 loads
-    const size_t total = (size_t)hdr->n * q;
+    const int n_pack = hdr->n_pack;
+    const size_t total = (size_t)n_pack * q;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int it = (int)(i / q);
-        if (items[it].packed) continue;
-        const uint32_t p = (uint32_t)(i - (size_t)it * q) * 4;
+        const int r = (int)(i / q);
+        const int it = items[r].pack_item;
+        const uint32_t p = (uint32_t)(i - (size_t)r * q) * 4;
         const KfCam& k = items[it].newc;
         const float4 d = __ldg(reinterpret_cast<const float4*>(k.depth + p));
         const uint4 c = __ldg(reinterpret_cast<const uint4*>(k.rgba + p));
@@ -201,10 +205,9 @@ __global__ void batch_pack_kernel(const BatchItem* items, const BatchHeader* hdr
     }
     // remainder pixels (npx % 4) and each item's sentinel
     const uint32_t r0 = q * 4, nr = npx - r0 + 1;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)hdr->n * nr;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)n_pack * nr;
          i += (size_t)gridDim.x * blockDim.x) {
-        const int it = (int)(i / nr);
-        if (items[it].packed) continue;
+        const int it = items[i / nr].pack_item;
         const uint32_t p = r0 + (uint32_t)(i % nr);
         const KfCam& k = items[it].newc;
         tex[(size_t)it * stride + p] = p < npx ? pack_texel(k.depth[p], k.rgba[p]) : make_uint2(0xff800000u, 0u);
@@ -660,8 +663,8 @@ cudaError_t enqueue_batch(sc_volume* V, cudaStream_t s, cudaGraphNode_t* items_n
         if (ndeps != 1) return cudaErrorUnknown;
         *items_node = deps[0];
     }
-    batch_init_kernel<<<4, 256, 0, s>>>(B->items_d, B->hdr_d, B->counters);
-    batch_pack_kernel<<<V->num_sms * 8, 256, 0, s>>>(B->items_d, B->hdr_d, B->tex, B->tex_px, B->tex_stride);
+    batch_pack_kernel<<<V->num_sms * 8, 256, 0, s>>>(B->items_d, B->hdr_d, B->tex, B->tex_px, B->tex_stride,
+                                                     B->counters);
     if (V->prof_on) cudaEventRecordWithFlags(V->graph_ev[0], s, cudaEventRecordExternal);
     batch_alloc_kernel<<<V->num_sms * ALLOC_CTAS_PER_SM, ALLOC_THREADS, 0, s>>>(
         V->dv, B->items_d, B->hdr_d, B->masks, B->mw, B->ulist, B->counters, V->p.max_blocks_per_keyframe);
@@ -770,6 +773,7 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
     SC_CUDA(cudaEventSynchronize(B->staged[B->buf]));
     BatchHeader* hdr_h = reinterpret_cast<BatchHeader*>(B->stage_h[B->buf]);
     BatchItem* items_h = reinterpret_cast<BatchItem*>(B->stage_h[B->buf] + STAGE_HDR);
+    int n_pack = 0;
     for (int i = 0; i < n; ++i) {
         const ItemSpec& it = items[i];
         BatchItem& b = items_h[i];
@@ -786,8 +790,10 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
         // packed from the same pointers under the same binding still holds them
         if (!it.oldp) ++V->img_epoch[it.kf_id];
         BatchState::PackedSlot& ps = B->slots[i];
-        b.packed = it.oldp && ps.kf == it.kf_id && ps.depth == it.depth && ps.rgba == it.rgba &&
-                   ps.epoch == V->img_epoch[it.kf_id] && ps.px == B->tex_px;
+        const bool packed = it.oldp && ps.kf == it.kf_id && ps.depth == it.depth && ps.rgba == it.rgba &&
+                            ps.epoch == V->img_epoch[it.kf_id] && ps.px == B->tex_px;
+        // items are written in order, so entry n_pack <= i is already filled
+        if (!packed) items_h[n_pack++].pack_item = i;
         ps.kf = it.kf_id;
         ps.depth = it.depth;
         ps.rgba = it.rgba;
@@ -796,6 +802,7 @@ int prepare_specs(sc_volume* V, const ItemSpec* items, int32_t n, const sc_intri
     }
     if (++V->call_id == 0) V->call_id = 1;  // (plain calls reset stamps on wrap)
     hdr_h->n = n;
+    hdr_h->n_pack = n_pack;
     hdr_h->call_id = V->call_id;
     hdr_h->tiles_x = (K->width + ALLOC_TX - 1) / ALLOC_TX;
     hdr_h->tiles = hdr_h->tiles_x * ((K->height + ALLOC_TY - 1) / ALLOC_TY);
@@ -815,7 +822,7 @@ int prepare_items(sc_volume* V, const sc_reint_item* items, int32_t n, const sc_
     return prepare_specs(V, sp.data(), n, K);
 }
 
-constexpr int GRAPH_KERNELS = 6;  // init, pack, batched allocation, mark old, net-delta, clear
+constexpr int GRAPH_KERNELS = 5;  // pack (and counter reset), batched allocation, mark old, net-delta, clear
 
 // Launch the prepared graph.  Asynchronous: device errors stay in the volume's sticky
 // status word (sc_get_status); with profiling on, the call synchronises to read the
