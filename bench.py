@@ -59,7 +59,7 @@ IMG_BYTES = 640 * 480 * (4 + 4)  # keyframe depth f32 + RGBA8
 VOXEL_BYTES_RW = 24             # D, W, RGBA8: 12 B read + 12 B written per voxel
 
 # Instruction-issue roofline.  The step's largest kernels are bound by instruction
-# issue (ncu: issue active 65-77 %, DRAM < 12 % of peak), so the roofline is the issue
+# issue (ncu: issue active 70-72 %, DRAM < 20 % of peak), so the roofline is the issue
 # rate: 148 SMs x 4 schedulers x 1 warp instruction / cycle x 32 lanes x SM clock.
 # Warp instructions per unit of work and DRAM bytes per unit come from the ncu capture
 # of the 12-keyframe case (profiles/instructions_kinect_small.md); units are frames
