@@ -12,7 +12,8 @@ One step = one pass of the whole hot path over that input:
   fuse 600 frames into 60 keyframes (Eq. 1) -> reset the volume -> integrate the 60
   keyframes (allocation + running average) -> ONE batched pose update (de-integrate
   all 60 at the drifted poses, re-integrate at the true poses) -> SDF loss at 1 M
-  surface points + adjoint for all 60 keyframes -> extract the block list.
+  surface points + adjoint for all 60 keyframes, and beside them, on a second stream
+  (it reads only the hash table), extract the block list.
 value = 60 re-integrations / step time.  The JSON line also reports the update
 alone, batched (one graph) vs plain (120 per-keyframe calls), the roofline of the
 dominant kernel, the oracle on the host cores, clocks and the kernel count, and,
@@ -263,6 +264,8 @@ class Pipeline:
         self.loss_out = torch.empty(5, dtype=torch.float64, device=dev)
         self.gx = torch.empty((K, 6), dtype=torch.float64, device=dev)
         self.gd = torch.empty((K, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
+        self.side = torch.cuda.Stream(device=dev)  # the extraction's stream (see step)
+        self.ev_upd = torch.cuda.Event()
 
     def fuse(self):
         """Eq. 1 for all keyframes in one call (KF_CONST: frames k*10 .. k*10+9 -> keyframe k)."""
@@ -309,8 +312,14 @@ class Pipeline:
         self.fuse()
         self.integrate()
         self.update_batched()
+        # the block-list extraction reads only the hash table, which the loss and the
+        # adjoint leave as it is: it runs on a second stream beside them, so its count
+        # read-back waits for the extraction alone, and the next step's launches queue
+        # behind the adjoint instead of following a drained device
+        self.ev_upd.record()
         out, gx, gd = self.loss_adjoint()
-        ex = self.extract()
+        self.side.wait_event(self.ev_upd)
+        ex = self.V.extract(payload=False, capacity=self.capacity, stream=self.side)
         return out, ex
 
 
