@@ -19,9 +19,11 @@
 //
 // mc_kernel: one CTA of 128 threads per pool slot; the block's voxels and the faces
 // of its 7 upper neighbours (found in the hash) are staged in shared memory as a
-// 9 x 9 x 9 tile of D (NaN where unobserved); a thread owns 4 consecutive cubes;
+// 9 x 9 x 9 tile of D (NaN where unobserved); a thread classifies 4 consecutive cubes;
 // a CTA-wide scan of triangle counts and one atomic give each triangle its output
-// position.
+// position, and the block's triangles, listed in that order in shared memory, are
+// emitted by all threads (the surface crosses few cubes, so emitting each cube's
+// triangles from the thread that classified it left half the lanes idle).
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -169,6 +171,8 @@ __global__ void __launch_bounds__(MC_THREADS) mc_kernel(DevVolume V, const McTab
     __shared__ int32_t nslot[8];
     __shared__ int32_t scan[MC_THREADS / 32];
     __shared__ unsigned long long base_s;
+    __shared__ uint8_t cmask[NVOX];                // case of each of the block's 512 cubes
+    __shared__ uint16_t tri_ref[NVOX * MC_MAXT];   // (cube << 3 | t) of each triangle, in output order
     const uint32_t slot = blockIdx.x;
     if (slot >= n_slots) return;
     const int tid = threadIdx.x;
@@ -229,41 +233,48 @@ __global__ void __launch_bounds__(MC_THREADS) mc_kernel(DevVolume V, const McTab
         total += scan[w];
     }
     if (tid == 0) base_s = total ? atomicAdd(out.count, (unsigned long long)total) : 0ull;
-    __syncthreads();
-    if (cnt == 0) return;
-    unsigned long long k = base_s + (unsigned long long)(wbase + incl - cnt);
-    const float s = out.voxel_size;
+    // the block's triangles in output order, (cube, t) each, so that the emission below
+    // spreads them over all threads instead of leaving the threads of empty cubes idle
+    int loc = wbase + incl - cnt;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int m = masks[j];
+        cmask[4 * tid + j] = (uint8_t)m;
         const int nt = __ldg(&T->ntri[m]);
-        const int cx = lx0 + j;
-        const int vx = 8 * bc.x + cx, vy = 8 * bc.y + ly, vz = 8 * bc.z + lz;
-        for (int t = 0; t < nt; ++t, ++k) {
-            if (k >= out.cap) continue;
-            float* o = out.tri + 9 * k;
+        for (int t = 0; t < nt; ++t) tri_ref[loc++] = (uint16_t)(((4 * tid + j) << 3) | t);
+    }
+    __syncthreads();
+    const float s = out.voxel_size;
+    for (int i = tid; i < total; i += MC_THREADS) {
+        const unsigned long long k = base_s + (unsigned long long)i;
+        if (k >= out.cap) break;
+        const int r = tri_ref[i], cube = r >> 3, t = r & 7;
+        const int owner = cube >> 2;
+        const int cx = 4 * (owner & 1) + (cube & 3), cy = (owner >> 1) & 7, cz = owner >> 4;
+        const int m = cmask[cube];
+        const int vx = 8 * bc.x + cx, vy = 8 * bc.y + cy, vz = 8 * bc.z + cz;
+        float* o = out.tri + 9 * k;
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int e = __ldg(&T->edge[m][3 * t + q]);
-                const int a = e >> 2, r = e & 3;
-                const int o1 = (a == 0) ? 1 : 0, o2 = (a == 2) ? 1 : 2;
-                const int lo = ((r & 1) << o1) | (((r >> 1) & 1) << o2);
-                const int hi = lo | (1 << a);
-                const float d0 = tD[tile_at(cx + (lo & 1), ly + ((lo >> 1) & 1), lz + ((lo >> 2) & 1))];
-                const float d1 = tD[tile_at(cx + (hi & 1), ly + ((hi >> 1) & 1), lz + ((hi >> 2) & 1))];
-                const float tt = __fdiv_rn(d0, __fsub_rn(d0, d1));
-                const int vc[3] = {vx + (lo & 1), vy + ((lo >> 1) & 1), vz + ((lo >> 2) & 1)};
+        for (int q = 0; q < 3; ++q) {
+            const int e = __ldg(&T->edge[m][3 * t + q]);
+            const int a = e >> 2, rr = e & 3;
+            const int o1 = (a == 0) ? 1 : 0, o2 = (a == 2) ? 1 : 2;
+            const int lo = ((rr & 1) << o1) | (((rr >> 1) & 1) << o2);
+            const int hi = lo | (1 << a);
+            const float d0 = tD[tile_at(cx + (lo & 1), cy + ((lo >> 1) & 1), cz + ((lo >> 2) & 1))];
+            const float d1 = tD[tile_at(cx + (hi & 1), cy + ((hi >> 1) & 1), cz + ((hi >> 2) & 1))];
+            const float tt = __fdiv_rn(d0, __fsub_rn(d0, d1));
+            const int vc[3] = {vx + (lo & 1), vy + ((lo >> 1) & 1), vz + ((lo >> 2) & 1)};
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    o[3 * q + d] = __fmul_rn(s, d == a ? __fadd_rn((float)vc[d], tt) : (float)vc[d]);
-            }
-            if (out.cube) {
-                int32_t* c = out.cube + 4 * k;
-                c[0] = vx;
-                c[1] = vy;
-                c[2] = vz;
-                c[3] = t;
-            }
+            for (int d = 0; d < 3; ++d)
+                o[3 * q + d] = __fmul_rn(s, d == a ? __fadd_rn((float)vc[d], tt) : (float)vc[d]);
+        }
+        if (out.cube) {
+            int32_t* c = out.cube + 4 * k;
+            c[0] = vx;
+            c[1] = vy;
+            c[2] = vz;
+            c[3] = t;
         }
     }
 }
