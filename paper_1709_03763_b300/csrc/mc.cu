@@ -194,8 +194,10 @@ __global__ void __launch_bounds__(MC_THREADS) mc_kernel(DevVolume V, const McTab
         const int32_t s = nslot[nb];
         float d = __int_as_float(0x7fc00000);  // NaN: unobserved or missing
         if (s >= 0) {
+            // W and D requested together (one round trip, not two)
             const size_t v = (size_t)s * NVOX + (x & 7) + 8 * (y & 7) + 64 * (z & 7);
-            if (V.W[v] > 0.f) d = V.D[v];
+            const float w = V.W[v], dv = V.D[v];
+            if (w > 0.f) d = dv;
         }
         tD[i] = d;
     }
