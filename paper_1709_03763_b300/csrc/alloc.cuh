@@ -300,7 +300,9 @@ __device__ inline bool tile_collect(const KfCam& k, int tx, int ty, AllocShared&
     const int3 wo = sh.wo;
     unsigned char* bmap = reinterpret_cast<unsigned char*>(sh.bmap);
     bool my_ovf = false;
-#pragma unroll 1
+    // unrolled over the thread's pixels: their walks interleave (4.5 % faster than one
+    // pixel at a time, despite the longer code)
+#pragma unroll
     for (int r = 0; r < PPT; ++r) {
         const int v = v0 + r * (ALLOC_THREADS / ALLOC_TX);
         const float Z = Zp[r];
