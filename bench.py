@@ -66,8 +66,8 @@ VOXEL_BYTES_RW = 24             # D, W, RGBA8: 12 B read + 12 B written per voxe
 # of the 12-keyframe case (profiles/instructions_kinect_small.md); units are frames
 # (fusion) and keyframe images (batched allocation).
 SMS, SCHEDULERS, LANES = 148, 4, 32
-WINST_PER_UNIT = {"fuse_kernel": 895077.4, "batch_alloc_kernel": 3378779.8}
-DRAM_PER_UNIT = {"fuse_kernel": 1.5605e6, "batch_alloc_kernel": 1.285e6}
+WINST_PER_UNIT = {"fuse_kernel": 895077.4, "batch_alloc_kernel": 3241665.3}
+DRAM_PER_UNIT = {"fuse_kernel": 1.5641e6, "batch_alloc_kernel": 1.2865e6}
 
 
 def parse():
