@@ -9,8 +9,9 @@ depth, 737 MB of colour) are resident in HBM before the timed region, and they
 exceed the 126 MB L2, so no flush is needed between steps.
 
 One step = one pass of the whole hot path over that input:
-  fuse 600 frames into 60 keyframes (Eq. 1) -> reset the volume -> integrate the 60
-  keyframes (allocation + running average) -> ONE batched pose update (de-integrate
+  fuse 600 frames into 60 keyframes (Eq. 1), and beside it, on a second stream, reset
+  the volume -> integrate the 60 keyframes (allocation + running average) -> ONE
+  batched pose update (de-integrate
   all 60 at the drifted poses, re-integrate at the true poses) -> SDF loss at 1 M
   surface points + adjoint for all 60 keyframes, and beside them, on a second stream
   (it reads only the hash table), extract the block list.
@@ -264,8 +265,10 @@ class Pipeline:
         self.loss_out = torch.empty(5, dtype=torch.float64, device=dev)
         self.gx = torch.empty((K, 6), dtype=torch.float64, device=dev)
         self.gd = torch.empty((K, w.intr.height, w.intr.width), dtype=torch.float32, device=dev)
-        self.side = torch.cuda.Stream(device=dev)  # the extraction's stream (see step)
+        self.side = torch.cuda.Stream(device=dev)  # the reset's and the extraction's stream (see step)
         self.ev_upd = torch.cuda.Event()
+        self.ev_prev = torch.cuda.Event()
+        self.ev_reset = torch.cuda.Event()
 
     def fuse(self):
         """Eq. 1 for all keyframes in one call (KF_CONST: frames k*10 .. k*10+9 -> keyframe k)."""
@@ -309,8 +312,16 @@ class Pipeline:
         return self.V.extract(payload=False, capacity=self.capacity)
 
     def step(self):
+        import torch
+        # the reset touches only the volume, which the fusion leaves alone: it runs on a
+        # second stream beside the fusion, once the previous step's adjoint is done
+        self.ev_prev.record()
+        self.side.wait_event(self.ev_prev)
+        self.V.reset(stream=self.side)
+        self.ev_reset.record(self.side)
         self.fuse()
-        self.integrate()
+        torch.cuda.current_stream().wait_event(self.ev_reset)
+        self.V.integrate_many(intr=self.intr, prepared=self.prep_int)
         self.update_batched()
         # the block-list extraction reads only the hash table, which the loss and the
         # adjoint leave as it is: it runs on a second stream beside them, so its count
