@@ -191,7 +191,7 @@ int sc_fuse_frames_into_keyframe(const float* depths, const sc_pose* frame_poses
  * kf_weight are device [n_kf][H][W], overwritten.  Same per-keyframe result as
  * sc_fuse_frames_into_keyframe on each keyframe's frames (up to float summation
  * order).  Widths a multiple of 4: one launch initialises each keyframe's sums from
- * its first frame at the keyframe pose (no zeroing), then one scatter launch per 512
+ * its first frame at the keyframe pose (no zeroing), then one scatter launch per 576
  * other frames and one normalisation launch; other widths zero the sums and scatter
  * every frame. */
 int sc_fuse_keyframes(const float* depths, const sc_pose* frame_poses, const int32_t* frame_kf, int32_t n_frames,
